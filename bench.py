@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark of fast spectral clustering (Algorithm 2) on one GB300 per rank.
+
+A step is one pass of the hot path over the resident CSR graph:
+fsc_create_graph (validation + degrees) followed by fsc_cluster (Gaussian start
+block, t fused power iterations, D^-1/2, k-means++ seeding, Lloyd to
+convergence).  Default workload: SBM with n = 2^20 vertices, 16 equal blocks,
+expected intra-/inter-block degree 20/2 (~11.5M undirected edges, unit
+weights), k = 16, l = 4, t = 20, float32 storage.
+
+Prints one JSON line (rank 0).  `--impl reference` times the float64 CPU
+oracle on the same workload instead.  Under torchrun with N > 1 every rank
+runs its own replica (the method has no cross-GPU exchange for one graph in
+this library; see the design notes), value = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "sbm_n2p20_k16": dict(kind="sbm", n=2 ** 20, k=16, deg_in=20.0, deg_out=2.0, l=4, t=20, store="f32", seed=7,
+                          desc="SBM n=2^20, 16 equal blocks, intra-degree 20, inter-degree 2, unit weights; "
+                               "k=16, l=4, t=20, float32"),
+    "knn_2e5_k10": dict(kind="knn", npts=200_000, dim=32, ncomp=10, knn=10, k=10, l=4, t=20, store="f32", seed=5,
+                        desc="10-NN graph of 200,000 points in R^32 from a 10-component Gaussian mixture; "
+                             "k=10, l=4, t=20, float32"),
+    "image_481x321_bf16": dict(kind="image", k=8, l=3, t=30, store="bf16", seed=3,
+                               desc="481x321 Voronoi image graph, radius 3; k=8, l=3, t=30, bfloat16 storage"),
+}
+METRIC = "cluster ms & SpMM HBM GB/s (% peak) at matched ARI, learned/BF16 vs plain"
+
+
+def make_graph(w):
+    import workloads as W
+    if w["kind"] == "sbm":
+        return W.sbm_by_degree(w["n"], w["k"], w["deg_in"], w["deg_out"], seed=w["seed"])
+    if w["kind"] == "knn":
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        return W.knn_mixture(w["npts"], w["dim"], w["ncomp"], w["knn"], seed=w["seed"], device=dev)
+    if w["kind"] == "image":
+        return W.image_grid(321, 481, 8, seed=w["seed"])
+    raise ValueError(w["kind"])
+
+
+def spmm_bytes_per_launch(g, l, store):
+    """Algorithmic bytes of one fused power step: CSR once, X once, Y once, 1/d once."""
+    import paper_2310_10939_gb300 as fsc
+    lp = fsc.pad_l(l)
+    s = 4 if store == "f32" else 2
+    b = 4 * g.nnz + 8 * (g.n + 1) + 4 * g.n + 2 * g.n * lp * s
+    if g.w is not None:
+        b += 4 * g.nnz
+    return b
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def read_traffic(kernel_tag):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source has not changed since."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2310_10939_gb300", "csrc", "spmm.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    summ = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(summ):
+        return None
+    vals = {}
+    for line in open(summ):
+        if line.startswith("traffic_per_launch_bytes:") or line.startswith("kernel_source_sha:"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != sha or "traffic_per_launch_bytes" not in vals:
+        return None
+    return float(vals["traffic_per_launch_bytes"])
+
+
+def gpu_arm(args, w, rank, world, local_rank):
+    import torch
+    import paper_2310_10939_gb300 as fsc
+    from paper_2310_10939_gb300 import metrics as pm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    g = make_graph(w)
+    k, l, t, seed = w["k"], w["l"], w["t"], w["seed"]
+    store = fsc.BF16 if w["store"] == "bf16" else fsc.F32
+    rp = torch.as_tensor(g.row_ptr, device=dev)
+    col = torch.as_tensor(g.col, device=dev)
+    wt = None if g.w is None else torch.as_tensor(g.w, device=dev)
+    labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        G = fsc.Graph(rp, col, wt)
+        _, st = fsc.cluster(G, k, l, t, seed, store=store, labels=labels, rescale=True, events=evs)
+        G.close()
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    stats = None
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        stats = step(sp[i])
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    spmm_ms = [a.elapsed_time(b) for a, b in sp]
+    ms = float(np.mean(step_ms))
+    spmm_launch_ms = float(np.mean(spmm_ms)) / t
+    if world > 1:
+        x = torch.tensor([ms, spmm_launch_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        ms, spmm_launch_ms = float(x[0]), float(x[1])
+    ari = pm.ari(labels.cpu().numpy(), g.labels)
+
+    # end to end through the public API with host buffers: H2D of the CSR, create, cluster, D2H of labels
+    rp_h = torch.as_tensor(g.row_ptr).pin_memory()
+    col_h = torch.as_tensor(g.col).pin_memory()
+    w_h = None if g.w is None else torch.as_tensor(g.w).pin_memory()
+    lab_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    rp_d, col_d = torch.empty_like(rp), torch.empty_like(col)
+    w_d = None if wt is None else torch.empty_like(wt)
+    h2d = rp_h.numel() * 8 + col_h.numel() * 4 + (0 if w_h is None else w_h.numel() * 4)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rp_d.copy_(rp_h, non_blocking=True)
+        col_d.copy_(col_h, non_blocking=True)
+        if w_d is not None:
+            w_d.copy_(w_h, non_blocking=True)
+        G = fsc.Graph(rp_d, col_d, w_d)
+        lab_d, _ = fsc.cluster(G, k, l, t, seed, store=store, rescale=True)
+        lab_h.copy_(lab_d, non_blocking=True)
+        torch.cuda.synchronize()
+        G.close()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = float(np.mean(e2e_ms))
+    if world > 1:
+        x = torch.tensor([e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        e2e = float(x[0])
+
+    bytes_launch = spmm_bytes_per_launch(g, l, w["store"])
+    peak, peak_src = read_peaks()
+    achieved = bytes_launch / (spmm_launch_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC,
+        "value": round(ms, 4),
+        "unit": "ms per clustering (create_graph + cluster)",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if store == fsc.F32 else "bf16-store/f32-accumulate",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"{args.workload}: {w['desc']}", "n": g.n, "nnz": g.nnz, "k": k, "l": l, "t": t,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "512 MB buffer written between timed steps (flush)"},
+        "e2e": {"value": round(e2e, 4), "unit": "ms per clustering from pinned host CSR to host labels",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(g.n * 4)},
+        "roofline": {"kernel": "k_power_step (fused SpMM power iteration)", "bound": "hbm",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_src == "measured" else "fallback 6.8 TB/s",
+                     "traffic": read_traffic("spmm_sbm_n2p20_l4_f32") if args.workload == "sbm_n2p20_k16" else None,
+                     "bytes_per_launch": int(bytes_launch), "launch_ms": round(spmm_launch_ms, 5)},
+        "ari_vs_planted": round(ari, 4),
+        "lloyd_iterations": stats["iterations"] if stats else None,
+        "graphs_per_s": round(world * args.steps / (ms * args.steps * 1e-3), 3),
+        "wall_s": round(wall, 3),
+        "gpu_launches": args.steps * (1 + 1 + t + 2),
+        "clocks": clk,
+    }
+    return out, g
+
+
+def cpu_oracle_step(g, w):
+    from oracle import kmeans as km
+    from oracle import metrics, spectral
+    B = spectral.embed(g, w["l"], w["t"], w["seed"])
+    out = km.kmeans(B.astype(np.float32), w["k"], w["seed"])
+    spectral.degrees(g)
+    return metrics.ari(out["labels"], g.labels), out
+
+
+def cpu_cores_used():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max([1] + [int(i.get("num_threads", 1)) for i in threadpool_info()])
+        return n
+    except Exception:
+        return 1
+
+
+def reference_arm(args, w):
+    """The float64 CPU oracle, timed on the host cores (the comparison arm)."""
+    import workloads as W
+    tiny = W.sbm_by_degree(4096, 4, 20.0, 2.0, seed=1)
+    small_w = dict(w, k=4)
+    for _ in range(args.warmup):
+        cpu_oracle_step(tiny, small_w)
+    g = make_graph(w)
+    times = []
+    ari = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ari, _ = cpu_oracle_step(g, w)
+        times.append((time.perf_counter() - t0) * 1e3)
+    ms = float(np.mean(times))
+    cores = cpu_cores_used()
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(ms, 3),
+        "unit": "ms per clustering (create_graph + cluster)",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 (k-means decisions in f32)",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"{args.workload}: {w['desc']}", "n": g.n, "nnz": g.nnz},
+        "cpu_baseline": {"value": round(ms, 3), "unit": "ms per clustering", "cores": cores, "kind": "oracle",
+                         "sample": "the full workload per timed step (numpy/scipy float64 oracle); warm-up steps "
+                                   "on a 4096-vertex SBM"},
+        "e2e": {"value": round(ms, 3), "unit": "ms per clustering", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "ari_vs_planted": round(ari, 4) if ari is not None else None,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["fsc", "reference"], default="fsc")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sbm_n2p20_k16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(args, w)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out, g = gpu_arm(args, w, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        ari_cpu, _ = cpu_oracle_step(g, w)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        out["cpu_baseline"] = {"value": round(cpu_ms, 3), "unit": "ms per clustering", "cores": cpu_cores_used(),
+                               "kind": "oracle",
+                               "sample": "one full clustering of the same graph (float64 numpy/scipy oracle)",
+                               "ari_vs_planted": round(ari_cpu, 4)}
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

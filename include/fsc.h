@@ -1,0 +1,204 @@
+/*
+ * fsc.h - C ABI of the GB300 fast spectral clustering library (libfsc.so).
+ *
+ * The library implements Algorithm 2 (FastSpectralCluster) of Macgregor,
+ * "Fast and Simple Spectral Clustering in Theory and Practice" (NeurIPS 2023):
+ * l Gaussian vectors are pushed through t unnormalised power iterations
+ * (Algorithm 1) of the signless Laplacian M = I - N/2 = (I + D^-1/2 A D^-1/2)/2
+ * (Sec. 2), the result is scaled by D^-1/2, and its rows are clustered with
+ * k-means++ seeding and Lloyd iterations (Sec. 2.2).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers on the current CUDA device unless a
+ *    comment says "host".  `stream` is a cudaStream_t passed as void*
+ *    (NULL = the legacy default stream).
+ *  - Matrices are row-major.  An embedding of l columns is stored with
+ *    ld = fsc_pad_l(l) floats per row (1, 2, 4 or 8); columns l..ld-1 are
+ *    written as zero by fsc_embed and ignored by fsc_kmeans.
+ *  - No C++ exception crosses the ABI.  Every call returns an fsc_status;
+ *    outputs are defined only when it returns FSC_OK.  Calls marked
+ *    "asynchronous" only enqueue work on `stream`; errors detected on the
+ *    device during such work are reported by the next synchronous call that
+ *    reads them (fsc_kmeans with non-NULL stats, fsc_cluster) or by
+ *    fsc_sync_status().
+ *  - Thread safety: a graph handle may be used by one stream at a time.
+ */
+#ifndef FSC_H
+#define FSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fsc_status {
+    FSC_OK = 0,
+    FSC_ERR_INVALID_ARG = 1,    /* bad size, null pointer, unsupported l/k, ... */
+    FSC_ERR_INDEX_RANGE = 2,    /* column index outside [0, n) or row_ptr not monotone */
+    FSC_ERR_NOT_SYMMETRIC = 3,  /* edge (i,j,w) without its mirror (j,i,w) */
+    FSC_ERR_SELF_LOOP = 4,      /* an entry (i, i) */
+    FSC_ERR_BAD_WEIGHT = 5,     /* negative, NaN or infinite weight */
+    FSC_ERR_OOM = 6,            /* device allocation failed */
+    FSC_ERR_CUDA = 7,           /* a CUDA runtime call failed */
+    FSC_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up */
+    FSC_ERR_UNSORTED = 9        /* symmetry check asked for, but a row's columns are not increasing */
+} fsc_status;
+
+typedef enum fsc_dtype {
+    FSC_F32 = 0,                /* power-iteration block stored in float32 */
+    FSC_BF16 = 1                /* stored in bfloat16, accumulated in float32 */
+} fsc_dtype;
+
+/* fsc_create_graph flags */
+#define FSC_VALIDATE_SYMMETRY 0x1u  /* also check that A is symmetric (rows must be sorted) */
+
+/* fsc_embed_opts.flags */
+#define FSC_EMBED_RESCALE 0x1u      /* per-column power-of-two rescale every iteration */
+
+typedef struct fsc_graph fsc_graph;   /* opaque */
+
+typedef struct fsc_graph_info_t {
+    int64_t n;                  /* vertices */
+    int64_t nnz;                /* stored entries = 2m (both directions of each edge) */
+    int64_t n_isolated;         /* vertices with d(v) = 0 */
+    int32_t weighted;           /* 1 if the graph has a weight array */
+    double volume;              /* vol(V) = sum of degrees (Sec. 2) */
+    const double* deg;          /* device, n: d(v) = sum_{u != v} w(u, v), float64 */
+    const float* dinv;          /* device, n: d(v)^-1/2 rounded to float (0 if isolated) */
+    const float* invdeg;        /* device, n: 1/d(v) rounded to float (0 if isolated) */
+} fsc_graph_info_t;
+
+typedef struct fsc_embed_opts {
+    uint32_t flags;             /* FSC_EMBED_* */
+    int32_t threads_per_row;    /* 0 = choose automatically; else 4, 8, 16 or 32 */
+    void* ev_spmm_begin;        /* optional cudaEvent_t recorded on `stream` before the first power iteration */
+    void* ev_spmm_end;          /* optional cudaEvent_t recorded after the last power iteration */
+} fsc_embed_opts;
+
+typedef struct fsc_kmeans_stats {
+    int32_t iterations;         /* Lloyd assignment steps run */
+    int32_t changed;            /* labels changed in the last step (0 = converged) */
+    int32_t empty_events;       /* cluster-steps in which a cluster had no point */
+    int32_t device_status;      /* fsc_status of the device-side work */
+    double inertia;             /* float64 sum of the last step's float32 squared distances */
+    double seeding_potential;   /* sum of D^2 after the last k-means++ round */
+} fsc_kmeans_stats;
+
+/*
+ * fsc_create_graph - wrap a CSR graph and compute its degrees (Sec. 2).
+ *
+ * row_ptr: int64[n+1], row_ptr[0] = 0, row_ptr[n] = nnz, non-decreasing.
+ * col_idx: int32[nnz], each in [0, n), no (i, i) entries.
+ * w:       float[nnz] non-negative finite weights, or NULL for unit weights.
+ * The CSR must hold both directions of every undirected edge with equal
+ * weights (checked only with FSC_VALIDATE_SYMMETRY, which also requires
+ * increasing columns within each row).
+ * The graph BORROWS row_ptr, col_idx and w: the caller keeps them alive and
+ * unchanged until fsc_destroy_graph.  The library owns the degree arrays and
+ * the embedding workspace.  n must be in [1, 2^31 - 1].
+ * Degrees: d(v) = sum over u != v of w(u,v) in float64; D^-1/2 of an
+ * isolated vertex is taken as 0 (its embedding row is then 0).
+ * Synchronous: returns after validation; on error *out is left unchanged and
+ * nothing is allocated.
+ */
+fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                            const float* w, uint32_t flags, void* stream, fsc_graph** out);
+
+/* Frees the library-owned arrays of g (synchronises the device first). NULL is a no-op. */
+fsc_status fsc_destroy_graph(fsc_graph* g);
+
+/* Host call: fills *info (pointers stay valid until fsc_destroy_graph). */
+fsc_status fsc_graph_info(const fsc_graph* g, fsc_graph_info_t* info);
+
+/* Row stride of an l-column embedding: 1, 2, 4 or 8 (0 if l is not in [1, 8]). */
+int fsc_pad_l(int l);
+
+/*
+ * fsc_embed - Algorithm 2 up to k-means: B = D^-1/2 [PowerMethod(M, x_i, t)]_{i=1..l}.
+ *
+ * x_1..x_l are N(0, I) vectors drawn by Philox4x64-10 (key = (seed, 1)):
+ * element (i, c) of the n x l start block has index e = c*n + i; Philox
+ * counter (e/4, 0, 0, 0) gives four words; element slot j = e%4 takes the
+ * Box-Muller pair (u1, u2) = (U(w[2*(j/2)]), U(w[2*(j/2)+1])),
+ * U(w) = ((w >> 40) + 1) * 2^-24, cosine branch for even j, sine for odd.
+ * PowerMethod (Algorithm 1) applies M t times without normalisation.
+ * emb: float[n * fsc_pad_l(l)] output, pad columns set to 0.
+ * store: dtype of the iterated block (FSC_BF16 = bfloat16 storage with
+ * float32 accumulation; degrees and weights stay float32/float64).
+ * 1 <= l <= 8, t >= 0 (t = 0 returns D^-1/2 X0).  opts may be NULL.
+ * Asynchronous.
+ */
+fsc_status fsc_embed(const fsc_graph* g, int l, int t, uint64_t seed, fsc_dtype store, float* emb,
+                     const fsc_embed_opts* opts, void* stream);
+
+/*
+ * fsc_power_step - one power iteration (Algorithm 1 body) in embedding coordinates.
+ *
+ * With z = D^-1/2 x, computes z_out = D^-1/2 M D^1/2 z_in = (z_in + D^-1 A z_in) / 2,
+ * i.e. D^-1/2 of M x.  z_in/z_out: n * fsc_pad_l(l) elements of `store`
+ * type (float or bfloat16 bits), must not overlap.  Accumulation in float32.
+ * This is the kernel fsc_embed runs t times, with the same launch shape.
+ * Asynchronous.
+ */
+fsc_status fsc_power_step(const fsc_graph* g, int l, fsc_dtype store, const void* z_in, void* z_out,
+                          int threads_per_row, void* stream);
+
+/*
+ * fsc_kmeans - k-means++ seeding and Lloyd iterations on the rows of emb (Sec. 2.2).
+ *
+ * emb: float[n * ld], row i = point i, first l columns used (1 <= l <= ld, ld in {1,2,4,8}).
+ * Seeding: first centre floor(u_0 * n); round r picks the smallest i whose
+ * float64 prefix sum of D^2 (float32 squared distance to the nearest chosen
+ * centre) exceeds u_r * sum(D^2); u_r from Philox4x64-10 key (seed, 2),
+ * counter (r, 0, 0, 0), word 0, U(w) = (w >> 11) * 2^-53.  If sum(D^2) = 0,
+ * the lowest index not chosen yet.
+ * Lloyd: nearest centroid by float32 squared distance (ties -> lowest
+ * index), centroids are float64 means (an empty cluster keeps its centroid),
+ * stop when no label changes or after max_iter steps.
+ * labels: int32[n] output.  centroids: float64[k * l] output or NULL.
+ * seed_idx: int64[k] output (the k-means++ picks) or NULL.
+ * stats: host struct or NULL.  With stats != NULL the call synchronises
+ * `stream` and reports device-side errors (e.g. FSC_ERR_TIMEOUT) in its
+ * return value; with NULL it is asynchronous.
+ * Limits: 1 <= k <= n, k <= 1024, k * ld <= 4096, 1 <= max_iter.
+ * Workspace is allocated stream-ordered (cudaMallocAsync) and freed on return.
+ */
+fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int max_iter,
+                      int32_t* labels, double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats,
+                      void* stream);
+
+/*
+ * fsc_cluster - Algorithm 2 end to end: fsc_embed then fsc_kmeans on its output.
+ * labels: int32[n] output.  stats: host struct or NULL.  opts may be NULL.
+ * Synchronous (returns after the device work and reports its status).
+ */
+fsc_status fsc_cluster(const fsc_graph* g, int k, int l, int t, uint64_t seed, fsc_dtype store, int max_iter,
+                       int32_t* labels, fsc_kmeans_stats* stats, const fsc_embed_opts* opts, void* stream);
+
+/*
+ * fsc_default_params - l and t for n vertices and k clusters (host, no device work).
+ * mode 0: l = max(1, ceil(log2 k)), t = ceil(log2 n).
+ * mode 1: the paper's practical remark after Theorem 3.2, l = max(1, ceil(ln k)),
+ *         t = ceil(10 ln(n / k)).
+ */
+fsc_status fsc_default_params(int64_t n, int k, int mode, int* l, int* t);
+
+/* Synchronises `stream`, returns and clears the device-side error word of the current device. */
+fsc_status fsc_sync_status(void* stream);
+
+/* Testing hook: bound on every device-side wait, in nanoseconds (default 2e9). Host call. */
+void fsc_set_wait_limit_ns(int64_t ns);
+
+/* Static, human-readable name of a status code. */
+const char* fsc_status_string(fsc_status s);
+
+/* Library version, e.g. "0.1.0". */
+const char* fsc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSC_H */

@@ -1,0 +1,272 @@
+"""Python binding of libfsc.so, the GB300 fast spectral clustering library.
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors (PyTorch provides device memory and
+streams); the calls mirror the C ABI in ``include/fsc.h``:
+
+    g = Graph(row_ptr, col, w)                  # fsc_create_graph
+    emb = embed(g, l, t, seed)                  # fsc_embed
+    labels, st = kmeans(emb, l, k, seed)        # fsc_kmeans
+    labels, st = cluster(g, k, l, t, seed)      # fsc_cluster
+
+There is no CPU fallback: importing works without a GPU (so the library's
+exports can be inspected), but every call needs the built ``libfsc.so`` and a
+CUDA device, and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+__all__ = [
+    "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
+    "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "status_string", "LIB_PATH",
+    "F32", "BF16", "VALIDATE_SYMMETRY", "EMBED_RESCALE",
+]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
+
+F32, BF16 = 0, 1
+VALIDATE_SYMMETRY = 0x1
+EMBED_RESCALE = 0x1
+
+_STATUS = {
+    0: "FSC_OK", 1: "FSC_ERR_INVALID_ARG", 2: "FSC_ERR_INDEX_RANGE", 3: "FSC_ERR_NOT_SYMMETRIC",
+    4: "FSC_ERR_SELF_LOOP", 5: "FSC_ERR_BAD_WEIGHT", 6: "FSC_ERR_OOM", 7: "FSC_ERR_CUDA",
+    8: "FSC_ERR_TIMEOUT", 9: "FSC_ERR_UNSORTED",
+}
+
+
+class FscError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.name} ({status_string(status)})")
+
+
+class EmbedOpts(C.Structure):
+    _fields_ = [("flags", C.c_uint32), ("threads_per_row", C.c_int32),
+                ("ev_spmm_begin", C.c_void_p), ("ev_spmm_end", C.c_void_p)]
+
+
+class KmeansStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("changed", C.c_int32), ("empty_events", C.c_int32),
+                ("device_status", C.c_int32), ("inertia", C.c_double), ("seeding_potential", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class GraphInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("n_isolated", C.c_int64), ("weighted", C.c_int32),
+                ("volume", C.c_double), ("deg", C.c_void_p), ("dinv", C.c_void_p), ("invdeg", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libfsc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libfsc.so not built at {LIB_PATH}; run `python -m paper_2310_10939_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, u32, u64 = C.c_void_p, C.c_int64, C.c_int, C.c_uint32, C.c_uint64
+        L.fsc_create_graph.argtypes = [i64, i64, vp, vp, vp, u32, vp, C.POINTER(vp)]
+        L.fsc_destroy_graph.argtypes = [vp]
+        L.fsc_graph_info.argtypes = [vp, C.POINTER(GraphInfo)]
+        L.fsc_pad_l.argtypes = [i32]
+        L.fsc_pad_l.restype = i32
+        L.fsc_embed.argtypes = [vp, i32, i32, u64, i32, vp, C.POINTER(EmbedOpts), vp]
+        L.fsc_power_step.argtypes = [vp, i32, i32, vp, vp, i32, vp]
+        L.fsc_kmeans.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
+        L.fsc_cluster.argtypes = [vp, i32, i32, i32, u64, i32, i32, vp, C.POINTER(KmeansStats),
+                                  C.POINTER(EmbedOpts), vp]
+        L.fsc_default_params.argtypes = [i64, i32, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.fsc_sync_status.argtypes = [vp]
+        L.fsc_set_wait_limit_ns.argtypes = [i64]
+        L.fsc_set_wait_limit_ns.restype = None
+        L.fsc_status_string.argtypes = [i32]
+        L.fsc_status_string.restype = C.c_char_p
+        L.fsc_version.restype = C.c_char_p
+        for name in ("fsc_create_graph", "fsc_destroy_graph", "fsc_graph_info", "fsc_embed", "fsc_power_step",
+                     "fsc_kmeans", "fsc_cluster", "fsc_default_params", "fsc_sync_status"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().fsc_status_string(int(status)).decode()
+    except ImportError:
+        return _STATUS.get(status, "?")
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise FscError(rc, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _require_cuda(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
+
+
+def pad_l(l: int) -> int:
+    return int(lib().fsc_pad_l(int(l)))
+
+
+def default_params(n: int, k: int, mode: int = 0):
+    l, t = C.c_int(), C.c_int()
+    _check(lib().fsc_default_params(int(n), int(k), int(mode), C.byref(l), C.byref(t)), "fsc_default_params")
+    return l.value, t.value
+
+
+def sync_status(stream=None):
+    _check(lib().fsc_sync_status(_stream(stream)), "fsc_sync_status")
+
+
+def set_wait_limit_ns(ns: int):
+    lib().fsc_set_wait_limit_ns(int(ns))
+
+
+class Graph:
+    """A CSR graph on the GPU with its degrees (fsc_create_graph).  Keeps the CSR tensors alive."""
+
+    def __init__(self, row_ptr, col, w=None, validate_symmetry: bool = False, stream=None):
+        torch = _torch()
+        _require_cuda(row_ptr, torch.int64, "row_ptr")
+        _require_cuda(col, torch.int32, "col")
+        if w is not None:
+            _require_cuda(w, torch.float32, "w")
+        self.row_ptr, self.col, self.w = row_ptr, col, w
+        self.n = row_ptr.numel() - 1
+        self.nnz = col.numel()
+        h = C.c_void_p()
+        flags = VALIDATE_SYMMETRY if validate_symmetry else 0
+        _check(lib().fsc_create_graph(self.n, self.nnz, _ptr(row_ptr), _ptr(col), _ptr(w), flags,
+                                      _stream(stream), C.byref(h)), "fsc_create_graph")
+        self.handle = h
+
+    @classmethod
+    def from_workload(cls, g, device="cuda", **kw):
+        """Upload a ``workloads.Graph`` (numpy CSR) and wrap it."""
+        torch = _torch()
+        rp = torch.as_tensor(g.row_ptr, device=device)
+        col = torch.as_tensor(g.col, device=device)
+        w = None if g.w is None else torch.as_tensor(g.w, device=device)
+        return cls(rp, col, w, **kw)
+
+    def info(self) -> dict:
+        inf = GraphInfo()
+        _check(lib().fsc_graph_info(self.handle, C.byref(inf)), "fsc_graph_info")
+        return {f: getattr(inf, f) for f, _ in GraphInfo._fields_}
+
+    def degrees(self):
+        """Copy of the library's float64 degree array d(v) (device tensor)."""
+        return _wrap_device(self.info()["deg"], (self.n,), "<f8").clone()
+
+    def dinv(self):
+        """Copy of the library's float32 D^-1/2 diagonal (device tensor)."""
+        return _wrap_device(self.info()["dinv"], (self.n,), "<f4").clone()
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().fsc_destroy_graph(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr), True),
+                                         "version": 3, "strides": None}
+
+
+def _wrap_device(ptr: int, shape, typestr: str):
+    """Zero-copy torch view of library-owned device memory (valid while the owner lives)."""
+    return _torch().as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
+
+
+def _opts(rescale=False, threads_per_row=0, events=None):
+    o = EmbedOpts()
+    o.flags = EMBED_RESCALE if rescale else 0
+    o.threads_per_row = int(threads_per_row)
+    if events is not None:
+        o.ev_spmm_begin = events[0].cuda_event
+        o.ev_spmm_end = events[1].cuda_event
+    return o
+
+
+def embed(g: Graph, l: int, t: int, seed: int, store: int = F32, out=None, rescale: bool = False,
+          threads_per_row: int = 0, events=None, stream=None):
+    """fsc_embed: returns (or fills) an n x pad_l(l) float32 CUDA tensor = D^-1/2 M^t X0."""
+    torch = _torch()
+    lp = pad_l(l)
+    if out is None:
+        out = torch.empty((g.n, max(lp, 1)), dtype=torch.float32, device=g.row_ptr.device)
+    _require_cuda(out, torch.float32, "out")
+    o = _opts(rescale, threads_per_row, events)
+    _check(lib().fsc_embed(g.handle, int(l), int(t), int(seed) & (2**64 - 1), int(store), _ptr(out),
+                           C.byref(o), _stream(stream)), "fsc_embed")
+    return out
+
+
+def power_step(g: Graph, l: int, z_in, z_out, store: int = F32, threads_per_row: int = 0, stream=None):
+    """fsc_power_step: z_out = (z_in + D^-1 A z_in) / 2 (one iteration in embedding coordinates)."""
+    _check(lib().fsc_power_step(g.handle, int(l), int(store), _ptr(z_in), _ptr(z_out), int(threads_per_row),
+                                _stream(stream)), "fsc_power_step")
+    return z_out
+
+
+def kmeans(emb, l: int, k: int, seed: int, max_iter: int = 100, labels=None, want_centroids: bool = False,
+           want_seeds: bool = False, sync: bool = True, stream=None):
+    """fsc_kmeans on the rows of ``emb`` (n x ld float32).  Returns (labels, stats, centroids, seeds)."""
+    torch = _torch()
+    _require_cuda(emb, torch.float32, "emb")
+    n, ld = emb.shape
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=emb.device)
+    cen = torch.empty((k, l), dtype=torch.float64, device=emb.device) if want_centroids else None
+    sd = torch.empty(k, dtype=torch.int64, device=emb.device) if want_seeds else None
+    st = KmeansStats()
+    _check(lib().fsc_kmeans(_ptr(emb), n, int(l), int(ld), int(k), int(seed) & (2**64 - 1), int(max_iter),
+                            _ptr(labels), _ptr(cen), _ptr(sd), C.byref(st) if sync else None, _stream(stream)),
+           "fsc_kmeans")
+    return labels, (st.as_dict() if sync else None), cen, sd
+
+
+def cluster(g: Graph, k: int, l: int, t: int, seed: int, store: int = F32, max_iter: int = 100, labels=None,
+            rescale: bool = False, threads_per_row: int = 0, events=None, stream=None):
+    """fsc_cluster (Algorithm 2 end to end).  Returns (labels, stats)."""
+    torch = _torch()
+    if labels is None:
+        labels = torch.empty(g.n, dtype=torch.int32, device=g.row_ptr.device)
+    st = KmeansStats()
+    o = _opts(rescale, threads_per_row, events)
+    _check(lib().fsc_cluster(g.handle, int(k), int(l), int(t), int(seed) & (2**64 - 1), int(store), int(max_iter),
+                             _ptr(labels), C.byref(st), C.byref(o), _stream(stream)), "fsc_cluster")
+    return labels, st.as_dict()

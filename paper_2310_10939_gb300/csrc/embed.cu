@@ -1,0 +1,202 @@
+// Algorithm 2 up to k-means: Gaussian start block, t power iterations, D^-1/2 scaling.
+#include <string.h>
+
+#include "spmm.cuh"
+
+namespace fsc {
+
+// Z0 = D^-1/2 X0 with X0 ~ N(0, I) from Philox4x64-10 (key (seed, 1)) and Box-Muller.
+// Element (i, c) of X0 has index e = c*n + i; one thread per Philox block b = e/4 produces
+// the four elements 4b..4b+3.  Pad columns l..LP-1 are zeroed.  Optionally records the
+// per-column max |Z0| for the rescale protocol.
+template <int LP, typename TO>
+__global__ void __launch_bounds__(256) k_gauss_init(int n, int l, unsigned long long seed,
+                                                    const float* __restrict__ dinv, TO* __restrict__ out,
+                                                    unsigned* __restrict__ cm_out) {
+    __shared__ unsigned s_cm[LP];
+    if (threadIdx.x < LP) s_cm[threadIdx.x] = 0u;
+    __syncthreads();
+    const long long total = (long long)n * l;
+    const long long nblk = (total + 3) / 4;
+    const long long work = nblk > n ? nblk : n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < work; b += stride) {
+        if (b < nblk) {
+            const U64x4 r = philox4x64_10(U64x4{(unsigned long long)b, 0ull, 0ull, 0ull}, seed, STREAM_X0);
+            const unsigned long long wd[4] = {r.x, r.y, r.z, r.w};
+            float z[4];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const float u1 = uniform24(wd[2 * p]);
+                const float u2 = uniform24(wd[2 * p + 1]);
+                const float rad = sqrtf(-2.0f * logf(u1));
+                float sn, cs;
+                sincospif(2.0f * u2, &sn, &cs);
+                z[2 * p] = rad * cs;
+                z[2 * p + 1] = rad * sn;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long e = 4 * b + j;
+                if (e < total) {
+                    const int c = (int)(e / n);
+                    const long long i = e - (long long)c * n;
+                    const float v = dinv[i] * z[j];
+                    out[i * LP + c] = from_f32<TO>(v);
+                    if (cm_out) atomicMax(&s_cm[c], __float_as_uint(fabsf(v)));
+                }
+            }
+        }
+        if (b < n) {
+            for (int c = l; c < LP; ++c) out[b * LP + c] = from_f32<TO>(0.f);
+        }
+    }
+    if (cm_out) {
+        __syncthreads();
+        if (threadIdx.x < LP && s_cm[threadIdx.x]) atomicMax(cm_out + threadIdx.x, s_cm[threadIdx.x]);
+    }
+}
+
+template <typename TO>
+cudaError_t launch_init(int LP, int n, int l, unsigned long long seed, const float* dinv, TO* out,
+                        unsigned* cm_out, cudaStream_t s) {
+    const long long total = (long long)n * l;
+    const long long work = (total + 3) / 4 > n ? (total + 3) / 4 : n;
+    long long blocks = (work + 255) / 256;
+    const long long cap = (long long)device_props().num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    switch (LP) {
+        case 1: k_gauss_init<1, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+        case 2: k_gauss_init<2, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+        case 4: k_gauss_init<4, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+        case 8: k_gauss_init<8, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Lanes per row chosen from the average degree (overridable).
+int choose_threads_per_row(const fsc_graph* g, int requested) {
+    if (requested == 4 || requested == 8 || requested == 16 || requested == 32) return requested;
+    const double avg = g->n > 0 ? (double)g->nnz / (double)g->n : 0.0;
+    if (avg <= 6.0) return 4;
+    if (avg <= 24.0) return 8;
+    if (avg <= 64.0) return 16;
+    return 32;
+}
+
+fsc_status ensure_workspace(fsc_graph* g, size_t bytes) {
+    if (g->ws_bytes >= bytes) return FSC_OK;
+    if (g->ws) {
+        cudaError_t e = cudaFree(g->ws);
+        g->ws = nullptr;
+        g->ws_bytes = 0;
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    g->ws = p;
+    g->ws_bytes = bytes;
+    return FSC_OK;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace fsc
+
+using namespace fsc;
+
+extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed, fsc_dtype store, float* emb,
+                                const fsc_embed_opts* opts, void* stream) {
+    fsc_graph* g = const_cast<fsc_graph*>(gc);
+    if (!g || !emb || l < 1 || l > 8 || t < 0 || (store != FSC_F32 && store != FSC_BF16)) return FSC_ERR_INVALID_ARG;
+    const int LP = pad_l(l);
+    if (!aligned(emb, (size_t)(LP * 4 < 16 ? LP * 4 : 16))) return FSC_ERR_INVALID_ARG;
+    const uint32_t flags = opts ? opts->flags : 0u;
+    if (flags & ~FSC_EMBED_RESCALE) return FSC_ERR_INVALID_ARG;
+    const bool rescale = (flags & FSC_EMBED_RESCALE) != 0;
+    const int G = choose_threads_per_row(g, opts ? opts->threads_per_row : 0);
+    cudaStream_t s = as_stream(stream);
+    const int n = (int)g->n;
+    if (t == 0) {
+        FSC_CUDA(launch_init<float>(LP, n, l, seed, g->dinv, emb, nullptr, s));
+        if (opts && opts->ev_spmm_begin) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_begin, s));
+        if (opts && opts->ev_spmm_end) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_end, s));
+        return FSC_OK;
+    }
+    fsc_status rc = ensure_workspace(g, (size_t)n * LP * 4 + 256);
+    if (rc != FSC_OK) return rc;
+    unsigned* cm = g->colmax;   // three buffers of 8
+    int* expo = rescale ? g->expo : nullptr;
+    if (rescale) FSC_CUDA(cudaMemsetAsync(g->colmax, 0, 3 * 8 * sizeof(unsigned) + 8 * sizeof(int), s));
+
+    StepArgs a{};
+    a.n = n;
+    a.rp = g->row_ptr;
+    a.col = g->col;
+    a.w = g->w;
+    a.invdeg = g->invdeg;
+    a.expo = expo;
+    const bool weighted = g->w != nullptr;
+
+    if (store == FSC_F32) {
+        float* buf[2];
+        buf[t % 2] = emb;
+        buf[(t + 1) % 2] = static_cast<float*>(g->ws);
+        FSC_CUDA(launch_init<float>(LP, n, l, seed, g->dinv, buf[0], rescale ? cm : nullptr, s));
+        if (opts && opts->ev_spmm_begin) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_begin, s));
+        for (int it = 0; it < t; ++it) {
+            const bool last = it == t - 1;
+            a.zin = buf[it % 2];
+            a.zout = buf[(it + 1) % 2];
+            a.cm_in = (rescale && !last) ? cm + 8 * (it % 3) : nullptr;
+            a.cm_out = (rescale && it < t - 2) ? cm + 8 * ((it + 1) % 3) : nullptr;
+            a.cm_zero = (rescale && !last) ? cm + 8 * ((it + 2) % 3) : nullptr;
+            a.last = last ? 1 : 0;
+            FSC_CUDA(launch_step_f32(LP, G, weighted, a, s));
+        }
+    } else {
+        __nv_bfloat16* wb[2];
+        wb[0] = static_cast<__nv_bfloat16*>(g->ws);
+        wb[1] = wb[0] + (size_t)n * LP;
+        FSC_CUDA(launch_init<__nv_bfloat16>(LP, n, l, seed, g->dinv, wb[0], rescale ? cm : nullptr, s));
+        if (opts && opts->ev_spmm_begin) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_begin, s));
+        for (int it = 0; it < t; ++it) {
+            const bool last = it == t - 1;
+            a.zin = wb[it % 2];
+            a.zout = last ? static_cast<void*>(emb) : static_cast<void*>(wb[(it + 1) % 2]);
+            a.cm_in = (rescale && !last) ? cm + 8 * (it % 3) : nullptr;
+            a.cm_out = (rescale && it < t - 2) ? cm + 8 * ((it + 1) % 3) : nullptr;
+            a.cm_zero = (rescale && !last) ? cm + 8 * ((it + 2) % 3) : nullptr;
+            a.last = last ? 1 : 0;
+            if (last) FSC_CUDA(launch_step_bf16_to_f32(LP, G, weighted, a, s));
+            else FSC_CUDA(launch_step_bf16(LP, G, weighted, a, s));
+        }
+    }
+    if (opts && opts->ev_spmm_end) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_end, s));
+    return FSC_OK;
+}
+
+extern "C" fsc_status fsc_power_step(const fsc_graph* g, int l, fsc_dtype store, const void* z_in, void* z_out,
+                                     int threads_per_row, void* stream) {
+    if (!g || !z_in || !z_out || z_in == z_out || l < 1 || l > 8 || (store != FSC_F32 && store != FSC_BF16))
+        return FSC_ERR_INVALID_ARG;
+    const int LP = pad_l(l);
+    const size_t es = store == FSC_F32 ? 4 : 2;
+    const size_t al = LP * es < 16 ? LP * es : 16;
+    if (!aligned(z_in, al) || !aligned(z_out, al)) return FSC_ERR_INVALID_ARG;
+    StepArgs a{};
+    a.n = (int)g->n;
+    a.rp = g->row_ptr;
+    a.col = g->col;
+    a.w = g->w;
+    a.invdeg = g->invdeg;
+    a.zin = z_in;
+    a.zout = z_out;
+    const int G = choose_threads_per_row(g, threads_per_row);
+    cudaStream_t s = as_stream(stream);
+    if (store == FSC_F32) FSC_CUDA(launch_step_f32(LP, G, g->w != nullptr, a, s));
+    else FSC_CUDA(launch_step_bf16(LP, G, g->w != nullptr, a, s));
+    return FSC_OK;
+}

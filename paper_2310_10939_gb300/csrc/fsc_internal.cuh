@@ -1,0 +1,214 @@
+// Internal definitions shared by the libfsc translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cuda/atomic>
+
+#include "../../include/fsc.h"
+
+namespace fsc {
+
+// ---- device status word ---------------------------------------------------------------
+// Bits OR-ed into a device int by kernels; translated to fsc_status on the host.
+enum : int {
+    ST_INDEX_RANGE = 1 << 0,
+    ST_SELF_LOOP = 1 << 1,
+    ST_BAD_WEIGHT = 1 << 2,
+    ST_NOT_SYMMETRIC = 1 << 3,
+    ST_UNSORTED = 1 << 4,
+    ST_TIMEOUT = 1 << 5,
+    ST_BAD_ROWPTR = 1 << 6,
+};
+
+fsc_status status_from_bits(int bits);
+
+// ---- host helpers ---------------------------------------------------------------------
+struct DeviceProps {
+    int device;
+    int num_sms;
+};
+const DeviceProps& device_props();        // of the current device (cached per device)
+int* device_status_word();                // per-device error word (allocated once)
+long long wait_limit_ns();
+fsc_status cuda_status(cudaError_t e);    // records and maps a CUDA error
+
+#define FSC_CUDA(call)                                            \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ::fsc::cuda_status(e_);     \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---- row vectors: LP elements of type T, loaded/stored as aligned chunks ---------------
+template <int B> struct Chunk;
+template <> struct Chunk<2> { using type = unsigned short; };
+template <> struct Chunk<4> { using type = unsigned int; };
+template <> struct Chunk<8> { using type = uint2; };
+template <> struct Chunk<16> { using type = uint4; };
+
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <typename T> __device__ __forceinline__ T from_f32(float x);
+template <> __device__ __forceinline__ float from_f32<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float x) {
+    return __float2bfloat16_rn(x);
+}
+
+template <int LP, typename T>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, float (&v)[LP]) {
+    constexpr int BYTES = LP * (int)sizeof(T);
+    constexpr int CB = BYTES < 16 ? BYTES : 16;
+    using C = typename Chunk<CB>::type;
+    constexpr int NC = BYTES / CB;
+    C buf[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) buf[i] = __ldg(reinterpret_cast<const C*>(p) + i);
+    const T* e = reinterpret_cast<const T*>(buf);
+#pragma unroll
+    for (int c = 0; c < LP; ++c) v[c] = to_f32(e[c]);
+}
+
+// Same as load_row but through L2 only (data written by other blocks of the same launch).
+template <int LP>
+__device__ __forceinline__ void load_row_cg(const float* p, float (&v)[LP]) {
+#pragma unroll
+    for (int c = 0; c < LP; ++c) v[c] = __ldcg(p + c);
+}
+
+template <int LP, typename T>
+__device__ __forceinline__ void store_row(T* __restrict__ p, const float (&v)[LP]) {
+    constexpr int BYTES = LP * (int)sizeof(T);
+    constexpr int CB = BYTES < 16 ? BYTES : 16;
+    using C = typename Chunk<CB>::type;
+    constexpr int NC = BYTES / CB;
+    C buf[NC];
+    T* e = reinterpret_cast<T*>(buf);
+#pragma unroll
+    for (int c = 0; c < LP; ++c) e[c] = from_f32<T>(v[c]);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) reinterpret_cast<C*>(p)[i] = buf[i];
+}
+
+// ---- Philox4x64-10 (Salmon et al., SC'11) ----------------------------------------------
+struct U64x4 {
+    unsigned long long x, y, z, w;
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(U64x4 c, unsigned long long k0, unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long hi0 = __umul64hi(M0, c.x), lo0 = M0 * c.x;
+        const unsigned long long hi1 = __umul64hi(M1, c.z), lo1 = M1 * c.z;
+        c = U64x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += W0;
+        k1 += W1;
+    }
+    return c;
+}
+
+// uniform in (0, 1] from the top 24 bits (exact in float)
+__device__ __forceinline__ float uniform24(unsigned long long w) {
+    return (float)((unsigned)(w >> 40) + 1u) * 0x1p-24f;
+}
+// uniform in [0, 1) from the top 53 bits (exact in double)
+__device__ __forceinline__ double uniform53(unsigned long long w) { return (double)(w >> 11) * 0x1p-53; }
+
+constexpr unsigned long long STREAM_X0 = 1, STREAM_KMEANSPP = 2;
+
+// ---- bounded grid-wide barrier for cooperative launches --------------------------------
+struct GridBarrier {
+    unsigned int count;
+    unsigned int generation;
+};
+
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+// All blocks of a cooperative launch call this.  Returns false (for every thread of the block)
+// if the device error word is set or the wait exceeded `limit_ns`; the caller then returns.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, long long limit_ns) {
+    __shared__ int s_ok;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->generation);
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
+        cuda::atomic_ref<int, cuda::thread_scope_device> st(*status);
+        int ok = st.load(cuda::memory_order_relaxed) == 0;
+        if (ok) {
+            const unsigned int g = gen.load(cuda::memory_order_acquire);
+            const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+            if (arrived == gridDim.x - 1) {
+                cnt.store(0u, cuda::memory_order_relaxed);
+                gen.fetch_add(1u, cuda::memory_order_release);
+            } else {
+                const long long t0 = global_ns();
+                unsigned spins = 0;
+                while (gen.load(cuda::memory_order_acquire) == g) {
+                    if (st.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
+                    if (++spins > 32) __nanosleep(64);
+                    if ((spins & 63u) == 0 && global_ns() - t0 > limit_ns) {
+                        st.fetch_or(ST_TIMEOUT, cuda::memory_order_relaxed);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---- misc --------------------------------------------------------------------------------
+__device__ __forceinline__ int exponent_of(float m) {   // floor(log2 m) for normal m > 0, else 0
+    const unsigned b = __float_as_uint(m);
+    const int e = (int)((b >> 23) & 0xff);
+    return (e == 0 || e == 0xff) ? 0 : e - 127;
+}
+
+// float32 squared distance in a fixed order, no contraction (mirrors the oracle's decision rule)
+template <int LP>
+__device__ __forceinline__ float sqdist(const float (&x)[LP], const float* __restrict__ c) {
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
+        const float d = __fsub_rn(x[j], c[j]);
+        acc = __fadd_rn(acc, __fmul_rn(d, d));
+    }
+    return acc;
+}
+
+inline int pad_l(int l) { return l == 1 ? 1 : l == 2 ? 2 : l <= 4 ? 4 : l <= 8 ? 8 : 0; }
+
+}  // namespace fsc
+
+// The graph object behind the opaque handle.
+struct fsc_graph {
+    int device;
+    int64_t n, nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* w;
+    double* deg;
+    float* dinv;
+    float* invdeg;
+    int64_t n_isolated;
+    double volume;
+    // embedding workspace (grown on demand)
+    void* ws;
+    size_t ws_bytes;
+    unsigned* colmax;   // 3 x 8 unsigned
+    int* expo;          // 8 ints
+};

@@ -1,0 +1,294 @@
+// Graph ingest: validation and degrees d(v) = sum_{u != v} w(u, v) (Sec. 2), plus host utilities.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "fsc_internal.cuh"
+
+namespace fsc {
+
+namespace {
+constexpr int kMaxDevices = 64;
+DeviceProps g_props[kMaxDevices];
+int* g_status_word[kMaxDevices];
+std::once_flag g_props_once[kMaxDevices];
+std::mutex g_status_mu;
+std::atomic<long long> g_wait_limit{2000000000LL};
+}  // namespace
+
+const DeviceProps& device_props() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDevices) dev = 0;
+    std::call_once(g_props_once[dev], [dev] {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g_props[dev] = DeviceProps{dev, sms > 0 ? sms : 1};
+    });
+    return g_props[dev];
+}
+
+int* device_status_word() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    if (!g_status_word[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        g_status_word[dev] = p;
+    }
+    return g_status_word[dev];
+}
+
+long long wait_limit_ns() { return g_wait_limit.load(); }
+
+fsc_status cuda_status(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return FSC_ERR_OOM;
+    return FSC_ERR_CUDA;
+}
+
+fsc_status status_from_bits(int bits) {
+    if (bits == 0) return FSC_OK;
+    if (bits & (ST_INDEX_RANGE | ST_BAD_ROWPTR)) return FSC_ERR_INDEX_RANGE;
+    if (bits & ST_SELF_LOOP) return FSC_ERR_SELF_LOOP;
+    if (bits & ST_BAD_WEIGHT) return FSC_ERR_BAD_WEIGHT;
+    if (bits & ST_UNSORTED) return FSC_ERR_UNSORTED;
+    if (bits & ST_NOT_SYMMETRIC) return FSC_ERR_NOT_SYMMETRIC;
+    if (bits & ST_TIMEOUT) return FSC_ERR_TIMEOUT;
+    return FSC_ERR_CUDA;
+}
+
+// One warp per row: validates the row and sums its off-diagonal weights in float64
+// (row order within each lane, then a fixed shuffle tree).
+__global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, const float* __restrict__ w,
+                                                int check_sorted, double* __restrict__ deg,
+                                                float* __restrict__ dinv, float* __restrict__ invdeg,
+                                                unsigned long long* __restrict__ n_iso, double* __restrict__ vol,
+                                                int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (warp == 0 && lane == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
+    double vsum = 0.0;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int64_t s = rp[i], e = rp[i + 1];
+        int bad = 0;
+        double d = 0.0;
+        if (s < 0 || e < s || e > nnz) {
+            bad |= ST_BAD_ROWPTR;
+        } else {
+            for (int64_t p = s + lane; p < e; p += 32) {
+                const int j = col[p];
+                if (j < 0 || (int64_t)j >= n) { bad |= ST_INDEX_RANGE; continue; }
+                if ((int64_t)j == i) { bad |= ST_SELF_LOOP; continue; }
+                if (check_sorted && p > s && col[p - 1] >= j) bad |= ST_UNSORTED;
+                const float wv = w ? w[p] : 1.0f;
+                if (!(wv >= 0.0f) || isinf(wv)) { bad |= ST_BAD_WEIGHT; continue; }
+                d += (double)wv;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            d += __shfl_xor_sync(0xffffffffu, d, off);
+            bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+        }
+        if (lane == 0) {
+            if (bad) atomicOr(status, bad);
+            deg[i] = d;
+            if (d > 0.0) {
+                dinv[i] = (float)(1.0 / sqrt(d));
+                invdeg[i] = (float)(1.0 / d);
+            } else {
+                dinv[i] = 0.0f;
+                invdeg[i] = 0.0f;
+                atomicAdd(n_iso, 1ull);
+            }
+            vsum += d;
+        }
+    }
+    if (lane == 0 && vsum != 0.0) atomicAdd(vol, vsum);
+}
+
+// One warp per row: each entry (i, j, w) must have its mirror (j, i, w) (binary search, sorted rows).
+__global__ void __launch_bounds__(256) k_symmetry(int64_t n, const int64_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ col, const float* __restrict__ w,
+                                                  int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+            const int j = col[p];
+            int64_t lo = rp[j], hi = rp[j + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (col[mid] < (int)i) lo = mid + 1; else hi = mid;
+            }
+            const bool found = lo < rp[j + 1] && col[lo] == (int)i &&
+                               (w == nullptr || __float_as_uint(w[lo]) == __float_as_uint(w[p]));
+            if (!found) atomicOr(status, ST_NOT_SYMMETRIC);
+        }
+    }
+}
+
+}  // namespace fsc
+
+using namespace fsc;
+
+extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                       const float* w, uint32_t flags, void* stream, fsc_graph** out) {
+    if (!out || n < 1 || n > 2147483647LL || nnz < 0 || !row_ptr || (nnz > 0 && !col_idx))
+        return FSC_ERR_INVALID_ARG;
+    if (flags & ~FSC_VALIDATE_SYMMETRY) return FSC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    int dev = 0;
+    FSC_CUDA(cudaGetDevice(&dev));
+    fsc_graph* g = new (std::nothrow) fsc_graph();
+    if (!g) return FSC_ERR_OOM;
+    memset(g, 0, sizeof(*g));
+    g->device = dev;
+    g->n = n;
+    g->nnz = nnz;
+    g->row_ptr = row_ptr;
+    g->col = col_idx;
+    g->w = w;
+    // one allocation: deg (n doubles) | volume (1 double) | n_iso (1 u64) | status (int, padded) |
+    //                 dinv (n floats) | invdeg (n floats) | colmax 24 u32 | expo 8 int
+    const size_t n8 = (size_t)n * 8, n4 = ((size_t)n * 4 + 255) & ~(size_t)255;
+    const size_t bytes = n8 + 256 + 2 * n4 + 256;
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_status(e);
+    }
+    g->deg = reinterpret_cast<double*>(base);
+    double* vol = reinterpret_cast<double*>(base + n8);
+    unsigned long long* niso = reinterpret_cast<unsigned long long*>(base + n8 + 8);
+    int* status = reinterpret_cast<int*>(base + n8 + 16);
+    g->dinv = reinterpret_cast<float*>(base + n8 + 256);
+    g->invdeg = reinterpret_cast<float*>(base + n8 + 256 + n4);
+    g->colmax = reinterpret_cast<unsigned*>(base + n8 + 256 + 2 * n4);
+    g->expo = reinterpret_cast<int*>(base + n8 + 256 + 2 * n4 + 128);
+    fsc_status rc = FSC_OK;
+    do {
+        if ((e = cudaMemsetAsync(base + n8, 0, 256, s)) != cudaSuccess) break;
+        const int threads = 256;
+        const int64_t want = (n * 32 + threads - 1) / threads;
+        const int blocks = (int)(want < (int64_t)device_props().num_sms * 64 ? want : (int64_t)device_props().num_sms * 64);
+        const int check_sorted = (flags & FSC_VALIDATE_SYMMETRY) ? 1 : 0;
+        k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,
+                                            g->invdeg, niso, vol, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        int bits = 0;
+        if ((e = cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        if (bits == 0 && check_sorted) {
+            k_symmetry<<<blocks, threads, 0, s>>>(n, row_ptr, col_idx, w, status);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        }
+        if (bits) { rc = status_from_bits(bits); break; }
+        unsigned long long iso = 0;
+        double v = 0;
+        if ((e = cudaMemcpyAsync(&iso, niso, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(&v, vol, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        g->n_isolated = (int64_t)iso;
+        g->volume = v;
+    } while (0);
+    if (e != cudaSuccess) rc = cuda_status(e);
+    if (rc != FSC_OK) {
+        cudaFree(base);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return FSC_OK;
+}
+
+extern "C" fsc_status fsc_destroy_graph(fsc_graph* g) {
+    if (!g) return FSC_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    if (g->ws) cudaFree(g->ws);
+    cudaFree(g->deg);
+    cudaSetDevice(prev);
+    delete g;
+    return FSC_OK;
+}
+
+extern "C" fsc_status fsc_graph_info(const fsc_graph* g, fsc_graph_info_t* info) {
+    if (!g || !info) return FSC_ERR_INVALID_ARG;
+    info->n = g->n;
+    info->nnz = g->nnz;
+    info->n_isolated = g->n_isolated;
+    info->weighted = g->w != nullptr;
+    info->volume = g->volume;
+    info->deg = g->deg;
+    info->dinv = g->dinv;
+    info->invdeg = g->invdeg;
+    return FSC_OK;
+}
+
+extern "C" int fsc_pad_l(int l) { return (l >= 1 && l <= 8) ? pad_l(l) : 0; }
+
+extern "C" fsc_status fsc_default_params(int64_t n, int k, int mode, int* l, int* t) {
+    if (!l || !t || n < 1 || k < 1 || k > n || (mode != 0 && mode != 1)) return FSC_ERR_INVALID_ARG;
+    if (mode == 0) {
+        int lv = 0;
+        while ((1LL << lv) < k) ++lv;
+        int tv = 0;
+        while ((1LL << tv) < n) ++tv;
+        *l = lv < 1 ? 1 : lv;
+        *t = tv;
+    } else {
+        const double lk = k > 1 ? ceil(log((double)k)) : 1.0;
+        *l = lk < 1.0 ? 1 : (int)lk;
+        *t = n > k ? (int)ceil(10.0 * log((double)n / (double)k)) : 0;
+    }
+    return FSC_OK;
+}
+
+extern "C" fsc_status fsc_sync_status(void* stream) {
+    int* word = device_status_word();
+    if (!word) return FSC_ERR_CUDA;
+    cudaStream_t s = as_stream(stream);
+    int bits = 0;
+    FSC_CUDA(cudaMemcpyAsync(&bits, word, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FSC_CUDA(cudaStreamSynchronize(s));
+    if (bits) {
+        FSC_CUDA(cudaMemsetAsync(word, 0, sizeof(int), s));
+        FSC_CUDA(cudaStreamSynchronize(s));
+    }
+    return status_from_bits(bits);
+}
+
+extern "C" void fsc_set_wait_limit_ns(int64_t ns) { g_wait_limit.store(ns < 0 ? 0 : ns); }
+
+extern "C" const char* fsc_status_string(fsc_status s) {
+    switch (s) {
+        case FSC_OK: return "ok";
+        case FSC_ERR_INVALID_ARG: return "invalid argument";
+        case FSC_ERR_INDEX_RANGE: return "column index out of range or malformed row_ptr";
+        case FSC_ERR_NOT_SYMMETRIC: return "adjacency matrix is not symmetric";
+        case FSC_ERR_SELF_LOOP: return "self-loop in the graph";
+        case FSC_ERR_BAD_WEIGHT: return "negative, NaN or infinite edge weight";
+        case FSC_ERR_OOM: return "device out of memory";
+        case FSC_ERR_CUDA: return "CUDA runtime error";
+        case FSC_ERR_TIMEOUT: return "device-side wait timed out";
+        case FSC_ERR_UNSORTED: return "row columns not increasing (required by the symmetry check)";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* fsc_version(void) { return "0.1.0"; }

@@ -1,0 +1,185 @@
+// Fused power-iteration kernel (Algorithm 1 body with the operator M of Sec. 2).
+//
+// The iterate is kept in embedding coordinates z = D^-1/2 x.  Since
+// D^-1/2 M D^1/2 = (I + D^-1 A) / 2, one step is
+//     z_out[i] = (z_in[i] + (1/d_i) * sum_j w_ij z_in[j]) / 2,
+// which gathers only z rows (no per-neighbour degree load), and the final
+// D^-1/2 of Algorithm 2 comes for free: after t steps z_t = D^-1/2 M^t x_0.
+//
+// Layout: z is n x LP row-major (LP = padded l, rows of 4..64 bytes).  A group
+// of G lanes owns one row: lanes stride over the row's column indices
+// (coalesced int32 loads), unroll U independent gathers of LP-wide rows, then
+// a shuffle-xor tree reduces the group.  Accumulation is float32.
+//
+// Optional per-column power-of-two rescale: the previous launch's column
+// max-abs (cm_in, float bits) gives e_c = floor(log2 max); outputs are
+// multiplied by 2^-e_c (exact), block 0 adds e_c into expo[c], and the final
+// launch (last = 1) multiplies by 2^expo[c], so the result equals the
+// unscaled iteration except for under/overflow.
+#pragma once
+
+#include "fsc_internal.cuh"
+
+namespace fsc {
+
+__device__ __forceinline__ float pow2i(int e) {
+    e = e < -126 ? -126 : (e > 127 ? 127 : e);
+    return __int_as_float((e + 127) << 23);
+}
+
+template <int LP, typename TI, typename TO, int G, int U, bool W>
+__global__ void __launch_bounds__(256)
+k_power_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ w,
+             const float* __restrict__ invdeg, const TI* __restrict__ zin, TO* __restrict__ zout,
+             const unsigned* __restrict__ cm_in, unsigned* __restrict__ cm_out, unsigned* __restrict__ cm_zero,
+             int* __restrict__ expo, int last) {
+    static_assert(32 % G == 0, "G must divide the warp");
+    constexpr int RPW = 32 / G;
+    __shared__ unsigned s_cm[LP];
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    const int grp = lane / G;
+
+    float scale[LP];
+#pragma unroll
+    for (int c = 0; c < LP; ++c) {
+        if (last) scale[c] = expo ? pow2i(expo[c]) : 1.f;
+        else scale[c] = cm_in ? pow2i(-exponent_of(__uint_as_float(cm_in[c]))) : 1.f;
+    }
+    if (cm_out && threadIdx.x < LP) s_cm[threadIdx.x] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x < LP) {
+        if (cm_zero) cm_zero[threadIdx.x] = 0u;
+        if (!last && cm_in && expo) expo[threadIdx.x] += exponent_of(__uint_as_float(cm_in[threadIdx.x]));
+    }
+    __syncthreads();
+
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = warp * RPW; base < n; base += nwarps * RPW) {
+        const long long row = base + grp;
+        const bool active = row < n;
+        float acc[LP];
+#pragma unroll
+        for (int c = 0; c < LP; ++c) acc[c] = 0.f;
+        if (active) {
+            const int64_t s = rp[row], e = rp[row + 1];
+            for (int64_t p = s + sub; p < e; p += G * U) {
+                int j[U];
+                float wv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t q = p + (int64_t)u * G;
+                    const bool ok = q < e;
+                    j[u] = ok ? __ldg(col + q) : -1;
+                    if (W) wv[u] = ok ? __ldg(w + q) : 0.f;
+                }
+                float v[U][LP];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (j[u] >= 0) {
+                        load_row<LP, TI>(zin + (size_t)j[u] * LP, v[u]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < LP; ++c) v[u][c] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) acc[c] = W ? fmaf(wv[u], v[u][c], acc[c]) : acc[c] + v[u][c];
+            }
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < LP; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+        float y[LP];
+        if (active && sub == 0) {
+            float self[LP];
+            load_row<LP, TI>(zin + (size_t)row * LP, self);
+            const float id = invdeg[row];
+#pragma unroll
+            for (int c = 0; c < LP; ++c) y[c] = scale[c] * (0.5f * fmaf(id, acc[c], self[c]));
+            store_row<LP, TO>(zout + (size_t)row * LP, y);
+        } else {
+#pragma unroll
+            for (int c = 0; c < LP; ++c) y[c] = 0.f;
+        }
+        if (cm_out) {
+#pragma unroll
+            for (int c = 0; c < LP; ++c) {
+                float m = fabsf(y[c]);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                if (lane == 0 && m > 0.f) atomicMax(&s_cm[c], __float_as_uint(m));
+            }
+        }
+    }
+    if (cm_out) {
+        __syncthreads();
+        if (threadIdx.x < LP && s_cm[threadIdx.x]) atomicMax(cm_out + threadIdx.x, s_cm[threadIdx.x]);
+    }
+}
+
+struct StepArgs {
+    int n;
+    const int64_t* rp;
+    const int32_t* col;
+    const float* w;
+    const float* invdeg;
+    const void* zin;
+    void* zout;
+    const unsigned* cm_in;
+    unsigned* cm_out;
+    unsigned* cm_zero;
+    int* expo;
+    int last;
+};
+
+template <int LP, typename TI, typename TO, int G, int U, bool W>
+cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
+    auto kern = k_power_step<LP, TI, TO, G, U, W>;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 256, 0);
+        if (e != cudaSuccess || blocks_per_sm < 1) blocks_per_sm = 4;
+    }
+    constexpr int RPW = 32 / G;
+    const long long warps = ((long long)a.n + RPW - 1) / RPW;
+    long long blocks = (warps + 7) / 8;
+    const long long cap = (long long)device_props().num_sms * blocks_per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, 256, 0, s>>>(a.n, a.rp, a.col, a.w, a.invdeg, static_cast<const TI*>(a.zin),
+                                         static_cast<TO*>(a.zout), a.cm_in, a.cm_out, a.cm_zero, a.expo, a.last);
+    return cudaGetLastError();
+}
+
+template <int LP, typename TI, typename TO, bool W>
+cudaError_t launch_step_g(int G, const StepArgs& a, cudaStream_t s) {
+    switch (G) {
+        case 4: return launch_step<LP, TI, TO, 4, 4, W>(a, s);
+        case 8: return launch_step<LP, TI, TO, 8, 4, W>(a, s);
+        case 16: return launch_step<LP, TI, TO, 16, 2, W>(a, s);
+        case 32: return launch_step<LP, TI, TO, 32, 2, W>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_step_any(int LP, int G, bool weighted, const StepArgs& a, cudaStream_t s) {
+    switch (LP) {
+        case 1: return weighted ? launch_step_g<1, TI, TO, true>(G, a, s) : launch_step_g<1, TI, TO, false>(G, a, s);
+        case 2: return weighted ? launch_step_g<2, TI, TO, true>(G, a, s) : launch_step_g<2, TI, TO, false>(G, a, s);
+        case 4: return weighted ? launch_step_g<4, TI, TO, true>(G, a, s) : launch_step_g<4, TI, TO, false>(G, a, s);
+        case 8: return weighted ? launch_step_g<8, TI, TO, true>(G, a, s) : launch_step_g<8, TI, TO, false>(G, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Defined in spmm_f32.cu / spmm_bf16.cu (one instantiation set per translation unit).
+cudaError_t launch_step_f32(int LP, int G, bool weighted, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_bf16(int LP, int G, bool weighted, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_bf16_to_f32(int LP, int G, bool weighted, const StepArgs& a, cudaStream_t s);
+
+}  // namespace fsc

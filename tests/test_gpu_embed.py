@@ -1,0 +1,187 @@
+"""GPU parity of graph ingest, the power step and the embedding (Sec. 2, Algorithms 1-2).
+
+Every case compares the CUDA path (through the C ABI) with the float64 oracle on
+the same seeded inputs.  Tolerances: degrees exact (unit weights) or 1e-15
+relative (float64 sums in another order); one power step 2e-6 relative
+Frobenius (float32 accumulation of ~30 terms); the embedding 1e-5 relative
+Frobenius in float32 storage and 2e-2 in bfloat16 storage.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from _helpers import rel_fro, require_cuda
+from oracle import spectral
+
+pytestmark = pytest.mark.gpu
+
+GRAPHS = {
+    "sbm_1000_k4": lambda: W.sbm([250] * 4, 0.1, 0.002, 1),
+    "sbm_ragged": lambda: W.sbm([131, 77, 260], 0.08, 0.004, 2),
+    "knn_weighted": lambda: W.knn_mixture(3000, 16, 6, 10, seed=3),
+    "image_weighted": lambda: W.image_grid(40, 57, 5, seed=4),
+    "cycle": lambda: W.cycle(1001),
+    "cliques": lambda: W.disjoint_cliques(7, 23),
+    "isolated": lambda: W.with_isolated(W.sbm([200, 300], 0.05, 0.003, 5), 37),
+    "permuted_sbm": lambda: W.permuted(W.sbm([500] * 3, 0.04, 0.002, 6), 7),
+}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+def _graph(torch, g):
+    import paper_2310_10939_gb300 as fsc
+    return fsc.Graph.from_workload(g)
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_degrees_and_isolated_count(torch, name):
+    g = GRAPHS[name]()
+    G = _graph(torch, g)
+    d = G.degrees().cpu().numpy()
+    ref = spectral.degrees(g)
+    if g.w is None:
+        assert np.array_equal(d, ref)
+    else:
+        assert np.allclose(d, ref, rtol=1e-15, atol=0)
+    info = G.info()
+    assert info["n_isolated"] == int((ref == 0).sum())
+    assert np.isclose(info["volume"], ref.sum(), rtol=1e-12)
+    dinv = G.dinv().cpu().numpy()
+    assert np.array_equal(dinv, spectral.inv_sqrt_degrees(ref).astype(np.float32))
+
+
+@pytest.mark.parametrize("name", ["sbm_1000_k4", "knn_weighted", "image_weighted", "isolated"])
+@pytest.mark.parametrize("l", [1, 2, 3, 8])
+@pytest.mark.parametrize("tpr", [4, 8, 16, 32])
+def test_power_step_matches_oracle(torch, name, l, tpr):
+    import paper_2310_10939_gb300 as fsc
+    g = GRAPHS[name]()
+    G = _graph(torch, g)
+    lp = fsc.pad_l(l)
+    rng = np.random.default_rng(l * 100 + tpr)
+    z = np.zeros((g.n, lp), dtype=np.float32)
+    z[:, :l] = rng.normal(size=(g.n, l)).astype(np.float32)
+    zin = torch.as_tensor(z, device="cuda")
+    zout = torch.full_like(zin, float("nan"))
+    fsc.power_step(G, l, zin, zout, threads_per_row=tpr)
+    got = zout.cpu().numpy()
+    d = spectral.degrees(g)
+    dh = np.sqrt(d)
+    dm = spectral.inv_sqrt_degrees(d)
+    M = spectral.signless_laplacian(g)
+    ref = dm[:, None] * (M @ (dh[:, None] * z[:, :l].astype(np.float64)))
+    # isolated vertices: z = D^-1/2 x is 0 there; the step keeps z/2 (D^-1 A z = 0)
+    iso = d == 0
+    ref[iso] = 0.5 * z[iso, :l]
+    assert rel_fro(got[:, :l], ref) <= 2e-6
+    assert np.array_equal(got[:, l:], np.zeros((g.n, lp - l), dtype=np.float32))
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("l,t", [(2, 20), (3, 7), (1, 5), (5, 12), (8, 3)])
+def test_embed_f32_matches_oracle(torch, name, l, t):
+    import paper_2310_10939_gb300 as fsc
+    g = GRAPHS[name]()
+    G = _graph(torch, g)
+    seed = 1000 + 7 * l + t
+    emb = fsc.embed(G, l, t, seed).cpu().numpy()
+    ref = spectral.embed(g, l, t, seed)
+    assert rel_fro(emb[:, :l], ref) <= 1e-5
+    assert np.array_equal(emb[:, l:], np.zeros((g.n, emb.shape[1] - l), dtype=np.float32))
+
+
+@pytest.mark.parametrize("t", [0, 1, 2, 3])
+def test_embed_small_t_including_zero(torch, t):
+    import paper_2310_10939_gb300 as fsc
+    g = GRAPHS["isolated"]()
+    G = _graph(torch, g)
+    for store in (fsc.F32, fsc.BF16):
+        emb = fsc.embed(G, 3, t, 77, store=store, rescale=True).cpu().numpy()
+        ref = spectral.embed(g, 3, t, 77)
+        assert rel_fro(emb[:, :3], ref) <= (1e-5 if store == fsc.F32 or t == 0 else 2e-2)
+        assert np.array_equal(emb[-37:], np.zeros_like(emb[-37:]))   # isolated rows are zero
+
+
+@pytest.mark.parametrize("name", ["sbm_1000_k4", "knn_weighted", "image_weighted", "cliques"])
+@pytest.mark.parametrize("tpr", [4, 8, 16, 32])
+def test_rescale_is_exact_and_threads_per_row_agree(torch, name, tpr):
+    import paper_2310_10939_gb300 as fsc
+    g = GRAPHS[name]()
+    G = _graph(torch, g)
+    for store in (fsc.F32, fsc.BF16):
+        a = fsc.embed(G, 4, 25, 5, store=store, rescale=False, threads_per_row=tpr)
+        b = fsc.embed(G, 4, 25, 5, store=store, rescale=True, threads_per_row=tpr)
+        assert torch.equal(a, b), "power-of-two rescale must not change the result"
+
+
+@pytest.mark.parametrize("name", ["sbm_1000_k4", "knn_weighted", "image_weighted", "cycle", "isolated"])
+def test_embed_bf16_within_tolerance(torch, name):
+    import paper_2310_10939_gb300 as fsc
+    g = GRAPHS[name]()
+    G = _graph(torch, g)
+    l, t = 3, 30
+    emb = fsc.embed(G, l, t, 11, store=fsc.BF16, rescale=True).cpu().numpy()
+    ref = spectral.embed(g, l, t, 11)
+    err = rel_fro(emb[:, :l], ref)
+    assert err <= 2e-2
+    emb32 = fsc.embed(G, l, t, 11).cpu().numpy()
+    assert rel_fro(emb32[:, :l], ref) <= 1e-5
+
+
+def test_embed_eigenvalue_one_direction(torch):
+    """P-a through the GPU: x = D^1/2 1 is fixed by M, so z = D^-1/2 x = 1 is fixed by the step."""
+    import paper_2310_10939_gb300 as fsc
+    g = GRAPHS["knn_weighted"]()
+    G = _graph(torch, g)
+    z = torch.zeros((g.n, 4), dtype=torch.float32, device="cuda")
+    z[:, 0] = 1.0
+    out = torch.empty_like(z)
+    fsc.power_step(G, 4, z, out)
+    assert torch.allclose(out[:, 0], torch.ones_like(out[:, 0]), rtol=0, atol=1e-6)
+
+
+def test_graph_validation_errors(torch):
+    import paper_2310_10939_gb300 as fsc
+    g = W.sbm([30, 30], 0.2, 0.05, 9)
+
+    def make(rp, col, w=None, **kw):
+        return fsc.Graph(torch.as_tensor(rp, device="cuda"), torch.as_tensor(col, device="cuda"),
+                         None if w is None else torch.as_tensor(w, device="cuda"), **kw)
+
+    col = g.col.copy()
+    col[5] = g.n + 3
+    with pytest.raises(fsc.FscError) as e:
+        make(g.row_ptr, col)
+    assert e.value.name == "FSC_ERR_INDEX_RANGE"
+    col = g.col.copy()
+    r0 = np.searchsorted(g.row_ptr, 10, side="right") - 1
+    col[g.row_ptr[10]] = 10
+    with pytest.raises(fsc.FscError) as e:
+        make(g.row_ptr, col)
+    assert e.value.name == "FSC_ERR_SELF_LOOP"
+    w = np.ones(g.nnz, dtype=np.float32)
+    w[3] = np.nan
+    with pytest.raises(fsc.FscError) as e:
+        make(g.row_ptr, g.col, w)
+    assert e.value.name == "FSC_ERR_BAD_WEIGHT"
+    w[3] = -1.0
+    with pytest.raises(fsc.FscError) as e:
+        make(g.row_ptr, g.col, w)
+    assert e.value.name == "FSC_ERR_BAD_WEIGHT"
+    w = np.ones(g.nnz, dtype=np.float32)
+    w[7] = 2.0                                   # mirror entry keeps weight 1
+    make(g.row_ptr, g.col, w)                    # accepted without the symmetry check
+    with pytest.raises(fsc.FscError) as e:
+        make(g.row_ptr, g.col, w, validate_symmetry=True)
+    assert e.value.name == "FSC_ERR_NOT_SYMMETRIC"
+    rp = g.row_ptr.copy()
+    rp[-1] += 1
+    with pytest.raises(fsc.FscError) as e:
+        make(rp, np.concatenate([g.col, [0]]).astype(np.int32)[:g.nnz])
+    assert e.value.name == "FSC_ERR_INDEX_RANGE"
+    make(g.row_ptr, g.col, validate_symmetry=True)   # the valid graph passes
+    del r0

@@ -233,15 +233,15 @@ def _knn_indices(x: np.ndarray, knn: int, device: str) -> np.ndarray:
     npts = x.shape[0]
     if device != "cpu":
         import torch
-        xt = torch.as_tensor(x, dtype=torch.float64, device=device)
+        xt = torch.as_tensor(x, dtype=torch.float32, device=device)
         sq = (xt * xt).sum(1)
         out = torch.empty((npts, knn), dtype=torch.int64, device=device)
-        for s in range(0, npts, 8192):
-            blk = xt[s:s + 8192]
-            d = sq[s:s + 8192, None] + sq[None, :] - 2.0 * (blk @ xt.T)
-            idx = torch.arange(s, min(s + 8192, npts), device=device)
+        for s in range(0, npts, 2048):
+            blk = xt[s:s + 2048]
+            d = sq[s:s + 2048, None] + sq[None, :] - 2.0 * (blk @ xt.T)
+            idx = torch.arange(s, min(s + 2048, npts), device=device)
             d[idx - s, idx] = float("inf")
-            out[s:s + 8192] = torch.topk(d, knn, dim=1, largest=False).indices
+            out[s:s + 2048] = torch.topk(d, knn, dim=1, largest=False).indices
         return out.cpu().numpy()
     sq = (x * x).sum(1)
     out = np.empty((npts, knn), dtype=np.int64)
