@@ -191,6 +191,11 @@ fsc_status fsc_sync_status(void* stream);
 /* Testing hook: bound on every device-side wait, in nanoseconds (default 2e9). Host call. */
 void fsc_set_wait_limit_ns(int64_t ns);
 
+/* Testing hook (failure injection without a GPU fault): with enable != 0, kernels launched
+ * afterwards never release their grid barriers, so every wait runs into the limit above and
+ * the call reports FSC_ERR_TIMEOUT.  Host call; 0 restores normal operation. */
+void fsc_inject_barrier_stall(int enable);
+
 /* Static, human-readable name of a status code. */
 const char* fsc_status_string(fsc_status s);
 

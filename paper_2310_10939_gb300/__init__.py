@@ -20,7 +20,7 @@ import os
 
 __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
-    "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "status_string", "LIB_PATH",
+    "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
     "F32", "BF16", "VALIDATE_SYMMETRY", "EMBED_RESCALE",
 ]
 
@@ -87,6 +87,8 @@ def lib() -> C.CDLL:
         L.fsc_sync_status.argtypes = [vp]
         L.fsc_set_wait_limit_ns.argtypes = [i64]
         L.fsc_set_wait_limit_ns.restype = None
+        L.fsc_inject_barrier_stall.argtypes = [i32]
+        L.fsc_inject_barrier_stall.restype = None
         L.fsc_status_string.argtypes = [i32]
         L.fsc_status_string.restype = C.c_char_p
         L.fsc_version.restype = C.c_char_p
@@ -148,6 +150,11 @@ def set_wait_limit_ns(ns: int):
     lib().fsc_set_wait_limit_ns(int(ns))
 
 
+def inject_barrier_stall(enable: bool):
+    """Testing hook: grid barriers are never released, so every wait runs into its limit."""
+    lib().fsc_inject_barrier_stall(1 if enable else 0)
+
+
 class Graph:
     """A CSR graph on the GPU with its degrees (fsc_create_graph).  Keeps the CSR tensors alive."""
 
@@ -202,7 +209,7 @@ class Graph:
 
 class _DeviceArray:
     def __init__(self, ptr, shape, typestr):
-        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
 
@@ -216,6 +223,9 @@ def _opts(rescale=False, threads_per_row=0, events=None):
     o.flags = EMBED_RESCALE if rescale else 0
     o.threads_per_row = int(threads_per_row)
     if events is not None:
+        for ev in events:
+            if not ev.cuda_event:          # torch creates the CUDA event lazily on first record
+                ev.record()
         o.ev_spmm_begin = events[0].cuda_event
         o.ev_spmm_end = events[1].cuda_event
     return o

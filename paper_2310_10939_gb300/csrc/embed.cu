@@ -129,7 +129,7 @@ extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed
     if (rc != FSC_OK) return rc;
     unsigned* cm = g->colmax;   // three buffers of 8
     int* expo = rescale ? g->expo : nullptr;
-    if (rescale) FSC_CUDA(cudaMemsetAsync(g->colmax, 0, 3 * 8 * sizeof(unsigned) + 8 * sizeof(int), s));
+    if (rescale) FSC_CUDA(cudaMemsetAsync(g->colmax, 0, 256, s));   // 3 x 8 column maxima + 8 exponents
 
     StepArgs a{};
     a.n = n;

@@ -33,6 +33,7 @@ struct DeviceProps {
 const DeviceProps& device_props();        // of the current device (cached per device)
 int* device_status_word();                // per-device error word (allocated once)
 long long wait_limit_ns();
+int barrier_stall();                      // testing hook: nonzero = never release grid barriers
 fsc_status cuda_status(cudaError_t e);    // records and maps a CUDA error
 
 #define FSC_CUDA(call)                                            \
@@ -135,7 +136,7 @@ __device__ __forceinline__ long long global_ns() {
 
 // All blocks of a cooperative launch call this.  Returns false (for every thread of the block)
 // if the device error word is set or the wait exceeded `limit_ns`; the caller then returns.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, long long limit_ns) {
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, long long limit_ns, int stall = 0) {
     __shared__ int s_ok;
     __threadfence();
     __syncthreads();
@@ -147,9 +148,13 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, long lo
         if (ok) {
             const unsigned int g = gen.load(cuda::memory_order_acquire);
             const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-            if (arrived == gridDim.x - 1) {
+            if (arrived == gridDim.x - 1 && !stall) {
                 cnt.store(0u, cuda::memory_order_relaxed);
                 gen.fetch_add(1u, cuda::memory_order_release);
+            } else if (arrived == gridDim.x - 1 && stall) {
+                // injected failure: the barrier is never released; this block records a timeout
+                st.fetch_or(ST_TIMEOUT, cuda::memory_order_relaxed);
+                ok = 0;
             } else {
                 const long long t0 = global_ns();
                 unsigned spins = 0;

@@ -17,6 +17,7 @@ int* g_status_word[kMaxDevices];
 std::once_flag g_props_once[kMaxDevices];
 std::mutex g_status_mu;
 std::atomic<long long> g_wait_limit{2000000000LL};
+std::atomic<int> g_stall{0};
 }  // namespace
 
 const DeviceProps& device_props() {
@@ -46,6 +47,7 @@ int* device_status_word() {
 }
 
 long long wait_limit_ns() { return g_wait_limit.load(); }
+int barrier_stall() { return g_stall.load(); }
 
 fsc_status cuda_status(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return FSC_ERR_OOM;
@@ -63,56 +65,78 @@ fsc_status status_from_bits(int bits) {
     return FSC_ERR_CUDA;
 }
 
-// One warp per row: validates the row and sums its off-diagonal weights in float64
-// (row order within each lane, then a fixed shuffle tree).
+// One thread per row: validates the row and forms d(v) = sum_{u != v} w(u, v).  Unit weights:
+// an exact integer count.  Weighted: a float64 sum in row order (the order of the definition).
+// D^-1/2 and 1/d are formed in float32 from the float64 degree (correctly rounded sqrt and
+// division, so within 1-2 ulp of the exact values); float64 arithmetic is kept out of the
+// unit-weight path because it runs at a small fraction of the float32 rate on this GPU.
 __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                                 const int32_t* __restrict__ col, const float* __restrict__ w,
                                                 int check_sorted, double* __restrict__ deg,
                                                 float* __restrict__ dinv, float* __restrict__ invdeg,
                                                 unsigned long long* __restrict__ n_iso, double* __restrict__ vol,
                                                 int* __restrict__ status) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    if (warp == 0 && lane == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (tid == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
+    int bad = 0;
+    unsigned iso = 0;
     double vsum = 0.0;
-    for (int64_t i = warp; i < n; i += nwarps) {
+    long long cnt_total = 0;
+    for (int64_t i = tid; i < n; i += stride) {
         const int64_t s = rp[i], e = rp[i + 1];
-        int bad = 0;
         double d = 0.0;
+        long long cnt = 0;
         if (s < 0 || e < s || e > nnz) {
             bad |= ST_BAD_ROWPTR;
         } else {
-            for (int64_t p = s + lane; p < e; p += 32) {
+            int prev = -1;
+            for (int64_t p = s; p < e; ++p) {
                 const int j = col[p];
                 if (j < 0 || (int64_t)j >= n) { bad |= ST_INDEX_RANGE; continue; }
                 if ((int64_t)j == i) { bad |= ST_SELF_LOOP; continue; }
-                if (check_sorted && p > s && col[p - 1] >= j) bad |= ST_UNSORTED;
-                const float wv = w ? w[p] : 1.0f;
-                if (!(wv >= 0.0f) || isinf(wv)) { bad |= ST_BAD_WEIGHT; continue; }
-                d += (double)wv;
+                if (check_sorted && j <= prev) bad |= ST_UNSORTED;
+                prev = j;
+                if (w) {
+                    const float wv = w[p];
+                    if (!(wv >= 0.0f) || isinf(wv)) { bad |= ST_BAD_WEIGHT; continue; }
+                    d += (double)wv;
+                } else {
+                    ++cnt;
+                }
             }
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            d += __shfl_xor_sync(0xffffffffu, d, off);
-            bad |= __shfl_xor_sync(0xffffffffu, bad, off);
-        }
-        if (lane == 0) {
-            if (bad) atomicOr(status, bad);
-            deg[i] = d;
-            if (d > 0.0) {
-                dinv[i] = (float)(1.0 / sqrt(d));
-                invdeg[i] = (float)(1.0 / d);
-            } else {
-                dinv[i] = 0.0f;
-                invdeg[i] = 0.0f;
-                atomicAdd(n_iso, 1ull);
-            }
+        if (!w) {
+            d = (double)cnt;
+            cnt_total += cnt;
+        } else {
             vsum += d;
         }
+        deg[i] = d;
+        if (d > 0.0) {
+            const float df = (float)d;
+            dinv[i] = 1.0f / sqrtf(df);
+            invdeg[i] = 1.0f / df;
+        } else {
+            dinv[i] = 0.0f;
+            invdeg[i] = 0.0f;
+            ++iso;
+        }
     }
-    if (lane == 0 && vsum != 0.0) atomicAdd(vol, vsum);
+    for (int off = 16; off > 0; off >>= 1) {
+        bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+        iso += __shfl_xor_sync(0xffffffffu, iso, off);
+        cnt_total += __shfl_xor_sync(0xffffffffu, cnt_total, off);
+    }
+    if (w) {
+        for (int off = 16; off > 0; off >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(status, bad);
+        if (iso) atomicAdd(n_iso, (unsigned long long)iso);
+        const double v = w ? vsum : (double)cnt_total;
+        if (v != 0.0) atomicAdd(vol, v);
+    }
 }
 
 // One warp per row: each entry (i, j, w) must have its mirror (j, i, w) (binary search, sorted rows).
@@ -180,7 +204,7 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     do {
         if ((e = cudaMemsetAsync(base + n8, 0, 256, s)) != cudaSuccess) break;
         const int threads = 256;
-        const int64_t want = (n * 32 + threads - 1) / threads;
+        const int64_t want = (n + threads - 1) / threads;
         const int blocks = (int)(want < (int64_t)device_props().num_sms * 64 ? want : (int64_t)device_props().num_sms * 64);
         const int check_sorted = (flags & FSC_VALIDATE_SYMMETRY) ? 1 : 0;
         k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,
@@ -274,6 +298,8 @@ extern "C" fsc_status fsc_sync_status(void* stream) {
 }
 
 extern "C" void fsc_set_wait_limit_ns(int64_t ns) { g_wait_limit.store(ns < 0 ? 0 : ns); }
+
+extern "C" void fsc_inject_barrier_stall(int enable) { g_stall.store(enable ? 1 : 0); }
 
 extern "C" const char* fsc_status_string(fsc_status s) {
     switch (s) {

@@ -1,19 +1,28 @@
-// k-means++ seeding and Lloyd iterations on the embedding rows (Sec. 2.2, Algorithm 2 last step).
+// k-means++ seeding and Lloyd iterations on the embedding rows (Sec. 2.2, last step of Algorithm 2).
 //
 // Both phases run as one cooperative (co-resident) persistent launch each.  Blocks own
 // contiguous chunks of points; cross-block steps are separated by a bounded grid barrier
 // (grid_sync), after which every block reads the other blocks' partial results through L2.
 //
-// Decisions follow fixed rules so that a float64 CPU restatement can reproduce them:
+// Decisions follow fixed rules that a float64 CPU restatement reproduces:
 //  * squared distances: float32, columns in order, no fused multiply-add;
-//  * k-means++: first centre floor(u0 * n); round r picks the smallest index whose float64
-//    prefix of D^2 exceeds u_r * sum(D^2) (prefix taken over block chunks, then 512-point
-//    tiles, then a block scan - the same index order as a sequential scan); sum(D^2) = 0
-//    picks the lowest index not chosen yet; a target beyond the computed prefix (rounding)
-//    picks the last index with D^2 > 0;
-//  * Lloyd: strict '<' over centroids in index order (ties -> lowest index); float64 sums
-//    per block, reduced over blocks in a fixed order; an empty cluster keeps its centroid;
-//    stop when no label changes or after max_iter steps.
+//  * k-means++: first centre floor(u0 * n); round r picks the smallest index whose prefix sum
+//    of D^2 exceeds u_r * sum(D^2); sum(D^2) = 0 picks the lowest index not chosen yet;
+//  * Lloyd: strict '<' over centroids in index order (ties -> lowest index); centroids are
+//    means; an empty cluster keeps its centroid; stop when no label changes or after max_iter.
+//
+// High-precision sums without float64 arithmetic in the loops: float64 runs at a small
+// fraction of the float32 rate on this GPU, so centroid sums, D^2 prefix sums and the
+// inertia are accumulated EXACTLY as 64-bit fixed-point integers (order independent,
+// deterministic).  With A = max |x| over the used columns, 2^Ex > A and 2^N >= n:
+//    coordinates:  q(x) = trunc(x * 2^Sx),  Sx = 62 - Ex - N
+//    distances:    q(d) = trunc(d * 2^Sd),  Sd = 62 - Ed - N,  Ed = 2 Ex + ceil(log2 l) + 3
+// so no sum of n terms can exceed 2^62.  Each term loses less than one unit 2^-S, i.e. the
+// sums carry an absolute error below n 2^-S (about 1e-13 A for the centroid means at
+// n = 2^20), smaller than the rounding of a sequential float64 sum.  Means and inertia are
+// formed in float64 from the exact integer sums.  The k-means++ target is compared exactly:
+// with U = w >> 11 (53 bits), index i qualifies iff P_i > floor(U * P_total / 2^53), which is
+// the same as P_i > u * P_total for u = U / 2^53.
 #include <limits.h>
 #include <math.h>
 
@@ -24,6 +33,8 @@ namespace fsc {
 constexpr int KM_THREADS = 512;
 constexpr int KM_WARPS = KM_THREADS / 32;
 constexpr int KM_MAX_BLOCKS = 1024;
+constexpr int KM_PPT = 4;                          // consecutive points per thread per tile
+constexpr int KM_TILE = KM_THREADS * KM_PPT;       // points per tile (chunks are multiples of it)
 
 struct KmDevStats {
     int iterations;
@@ -34,7 +45,40 @@ struct KmDevStats {
     double potential;
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+// ---- fixed-point helpers ---------------------------------------------------------------
+__device__ __forceinline__ long long fixq(float x, int S) {
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0 || e == 0xff) return 0;                     // zero / subnormal (below resolution)
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);   // |x| = m * 2^(e - 150)
+    const int sh = e - 150 + S;
+    long long v;
+    if (sh >= 0) v = sh < 39 ? (m << sh) : (m << 38);      // sh < 39 whenever |x| < 2^(62-S)
+    else v = sh > -25 ? (m >> -sh) : 0;
+    return (b >> 31) ? -v : v;
+}
+__device__ __forceinline__ double pow2d(int e) {          // 2^e as a double, e in [-1022, 1023]
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+__device__ __forceinline__ int ceil_log2(long long v) {    // smallest c with 2^c >= v (v >= 1)
+    int c = 0;
+    while ((1LL << c) < v) ++c;
+    return c;
+}
+struct Scales {
+    int Sx, Sd;
+};
+__device__ __forceinline__ Scales scales_for(float A, long long n, int l) {
+    const int N = ceil_log2(n < 2 ? 2 : n);
+    const int Ex = A > 0.f ? exponent_of(A) + 1 : 0;
+    const int Ed = 2 * Ex + ceil_log2(l) + 3;
+    Scales s;
+    s.Sx = 62 - Ex - N;
+    s.Sd = 62 - Ed - N;
+    return s;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
@@ -44,17 +88,14 @@ __device__ __forceinline__ int warp_sum_i(int v) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
 }
-
-// Block-wide sum with a fixed reduction tree; result valid in every thread.
-__device__ double block_sum_d(double v, double* s_red) {
+__device__ long long block_sum_ll(long long v, long long* s_red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum_d(v);
+    v = warp_sum_ll(v);
     __syncthreads();
     if (lane == 0) s_red[wid] = v;
     __syncthreads();
-    double t = lane < KM_WARPS ? s_red[lane] : 0.0;
-    t = warp_sum_d(t);
-    return t;
+    long long t = lane < KM_WARPS ? s_red[lane] : 0;
+    return warp_sum_ll(t);
 }
 __device__ int block_sum_i(int v, int* s_red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -65,23 +106,22 @@ __device__ int block_sum_i(int v, int* s_red) {
     int t = lane < KM_WARPS ? s_red[lane] : 0;
     return warp_sum_i(t);
 }
-
-// Inclusive block scan (fixed tree) of one double per thread.
-__device__ double block_scan_incl(double v, double* s_red) {
+// inclusive block scan of one int64 per thread
+__device__ long long block_scan_ll(long long v, long long* s_red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const double u = __shfl_up_sync(0xffffffffu, v, off);
+        const long long u = __shfl_up_sync(0xffffffffu, v, off);
         if (lane >= off) v += u;
     }
     __syncthreads();
     if (lane == 31) s_red[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        double t = lane < KM_WARPS ? s_red[lane] : 0.0;
+        long long t = lane < KM_WARPS ? s_red[lane] : 0;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const double u = __shfl_up_sync(0xffffffffu, t, off);
+            const long long u = __shfl_up_sync(0xffffffffu, t, off);
             if (lane >= off) t += u;
         }
         if (lane < KM_WARPS) s_red[lane] = t;
@@ -104,29 +144,64 @@ struct KppArgs {
     int n, l, k;
     unsigned long long seed;
     float* d2[2];
-    double* bsum[2];
-    double* tsum[2];
+    long long* bsum[2];
+    long long* tsum[2];
     int max_tiles;
+    long long chunk;     // points per block, a multiple of KM_TILE
+    unsigned* amax;      // max |x| (float bits), output for the Lloyd launch
     int64_t* seeds;
     float* c32;
-    double* c64;
     GridBarrier* bar;
     int* status;
     long long limit;
+    int stall;
 };
+
+__device__ int lowest_unchosen(const int* chosen, int r) {
+    int cand = 0;
+    for (;; ++cand) {
+        bool taken = false;
+        for (int q = 0; q < r; ++q)
+            if (chosen[q] == cand) { taken = true; break; }
+        if (!taken) return cand;
+    }
+}
 
 template <int LP>
 __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     extern __shared__ int s_chosen[];   // k entries
     __shared__ float s_c[LP];
-    __shared__ double s_red[KM_WARPS];
-    __shared__ double s_pref[KM_MAX_BLOCKS];
-    __shared__ double s_T, s_base;
-    __shared__ int s_bstar, s_tile, s_idx, s_fallback;
+    __shared__ long long s_red[KM_WARPS];
+    __shared__ long long s_pref[KM_MAX_BLOCKS];
+    __shared__ long long s_tiles[KM_THREADS];
+    __shared__ long long s_T, s_base;
+    __shared__ unsigned s_amax;
+    __shared__ int s_bstar, s_tile, s_idx;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
-    const long long chunk = (n + G - 1) / G;
+    const long long chunk = a.chunk;                 // multiple of KM_TILE
     const long long lo = min(n, (long long)b * chunk), hi = min(n, lo + chunk);
+
+    // ---- phase 0: A = max |x| over the used columns (sets the fixed-point scales)
+    if (tid == 0) s_amax = 0u;
+    __syncthreads();
+    {
+        float m = 0.f;
+        for (long long i = lo + tid; i < hi; i += KM_THREADS) {
+            float x[LP];
+            load_point<LP>(a.X, i, a.l, x);
+#pragma unroll
+            for (int c = 0; c < LP; ++c) m = fmaxf(m, fabsf(x[c]));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (lane == 0 && m > 0.f) atomicMax(&s_amax, __float_as_uint(m));
+        __syncthreads();
+        if (tid == 0 && s_amax) atomicMax(a.amax, s_amax);
+    }
+    if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
+    const float A = __uint_as_float(__ldcg(a.amax));
+    const Scales sc = scales_for(A, n, a.l);
 
     if (tid == 0) {
         const U64x4 r = philox4x64_10(U64x4{0ull, 0ull, 0ull, 0ull}, a.seed, STREAM_KMEANSPP);
@@ -143,150 +218,128 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         __syncthreads();
         float* d2n = a.d2[r & 1];
         const float* d2o = a.d2[(r - 1) & 1];
-        double* bs = a.bsum[r & 1];
-        double* ts = a.tsum[r & 1] + (size_t)b * a.max_tiles;
-        // ---- phase A: D^2 update over this block's chunk, in 512-point tiles
-        double bacc = 0.0;
+        long long* bs = a.bsum[r & 1];
+        long long* ts = a.tsum[r & 1] + (size_t)b * a.max_tiles;
+        // ---- phase A: D^2 update, KM_PPT consecutive points per thread, exact tile sums
+        long long bacc = 0;
         int tile = 0;
-        for (long long t0 = lo; t0 < hi; t0 += KM_THREADS, ++tile) {
-            const long long i = t0 + tid;
-            double v = 0.0;
-            if (i < hi) {
-                float x[LP];
-                load_point<LP>(a.X, i, a.l, x);
-                float dd = sqdist<LP>(x, s_c);
-                if (r > 1) dd = fminf(dd, d2o[i]);
-                d2n[i] = dd;
-                v = (double)dd;
+        for (long long t0 = lo; t0 < hi; t0 += KM_TILE, ++tile) {
+            const long long i0 = t0 + (long long)KM_PPT * tid;
+            float x[KM_PPT][LP];
+            float old[KM_PPT];
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                if (i0 + u < hi) load_point<LP>(a.X, i0 + u, a.l, x[u]);
+                old[u] = (r > 1 && i0 + u < hi) ? d2o[i0 + u] : 0.f;
             }
-            const double tsv = block_sum_d(v, s_red);
+            long long v = 0;
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                if (i0 + u < hi) {
+                    float dd = sqdist<LP>(x[u], s_c);
+                    if (r > 1) dd = fminf(dd, old[u]);
+                    d2n[i0 + u] = dd;
+                    v += fixq(dd, sc.Sd);
+                }
+            }
+            const long long tsv = block_sum_ll(v, s_red);
             if (tid == 0) {
                 ts[tile] = tsv;
                 bacc += tsv;
             }
         }
         if (tid == 0) bs[b] = bacc;
-        if (!grid_sync(a.bar, a.status, a.limit)) return;
+        if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
 
-        // ---- selection (identical in every block)
+        // ---- selection (identical in every block, exact integer arithmetic)
+        for (int q = tid; q < G; q += KM_THREADS) s_pref[q] = __ldcg(bs + q);
+        __syncthreads();
         if (wid == 0) {
             const int per = (G + 31) / 32;
             const int q0 = min(G, lane * per), q1 = min(G, q0 + per);
-            double seg = 0.0;
-            for (int q = q0; q < q1; ++q) seg += __ldcg(bs + q);
-            double incl = seg;
+            long long seg = 0;
+            for (int q = q0; q < q1; ++q) seg += s_pref[q];
+            long long incl = seg;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                const double u = __shfl_up_sync(0xffffffffu, incl, off);
+                const long long u = __shfl_up_sync(0xffffffffu, incl, off);
                 if (lane >= off) incl += u;
             }
-            double run = __shfl_up_sync(0xffffffffu, incl, 1);
-            if (lane == 0) run = 0.0;
+            long long run = incl - seg;
             for (int q = q0; q < q1; ++q) {
-                run += __ldcg(bs + q);
+                run += s_pref[q];
                 s_pref[q] = run;
             }
-        }
-        __syncthreads();
-        if (wid == 0) {
-            const double total = s_pref[G - 1];
-            if (!(total > 0.0)) {
-                if (lane == 0) {
-                    s_bstar = -1;
-                    s_fallback = 0;
-                    s_idx = -1;
-                }
+            __syncwarp();
+            const long long total = s_pref[G - 1];
+            if (total <= 0) {
+                if (lane == 0) s_bstar = -1;
             } else {
                 const U64x4 rr = philox4x64_10(U64x4{(unsigned long long)r, 0ull, 0ull, 0ull}, a.seed, STREAM_KMEANSPP);
-                const double T = uniform53(rr.x) * total;
-                const int per = (G + 31) / 32;
-                const int q0 = min(G, lane * per), q1 = min(G, q0 + per);
+                const unsigned long long U = rr.x >> 11, P = (unsigned long long)total;
+                const unsigned long long hi64 = __umul64hi(U, P), lo64 = U * P;
+                const long long T = (long long)((hi64 << 11) | (lo64 >> 53));   // floor(U * P / 2^53) < P
                 int found = -1;
                 for (int q = q0; q < q1; ++q)
                     if (s_pref[q] > T) { found = q; break; }
                 const unsigned m = __ballot_sync(0xffffffffu, found >= 0);
-                int bstar, fb = 0;
-                if (m) {
-                    bstar = __shfl_sync(0xffffffffu, found, __ffs(m) - 1);
-                } else {
-                    int lastpos = -1;
-                    for (int q = q1 - 1; q >= q0; --q)
-                        if (__ldcg(bs + q) > 0.0) { lastpos = q; break; }
-                    const unsigned m2 = __ballot_sync(0xffffffffu, lastpos >= 0);
-                    bstar = m2 ? __shfl_sync(0xffffffffu, lastpos, 31 - __clz(m2)) : 0;
-                    fb = 1;
-                }
+                const int bstar = m ? __shfl_sync(0xffffffffu, found, __ffs(m) - 1) : G - 1;
                 if (lane == 0) {
                     s_bstar = bstar;
-                    s_fallback = fb;
-                    s_idx = -1;
-                    s_base = bstar > 0 ? s_pref[bstar - 1] : 0.0;
+                    s_base = bstar > 0 ? s_pref[bstar - 1] : 0;
                     s_T = T;
                 }
             }
         }
         __syncthreads();
         if (s_bstar < 0) {
-            // sum(D^2) = 0: the lowest index not chosen yet
-            if (tid == 0) {
-                int cand = 0;
-                for (;; ++cand) {
-                    bool taken = false;
-                    for (int q = 0; q < r; ++q)
-                        if (s_chosen[q] == cand) { taken = true; break; }
-                    if (!taken) break;
-                }
-                s_idx = cand;
-            }
+            if (tid == 0) s_idx = lowest_unchosen(s_chosen, r);   // sum(D^2) = 0
         } else {
-            const int bs_ = s_bstar;
-            const long long blo = min(n, (long long)bs_ * chunk), bhi = min(n, blo + chunk);
-            const double* tsb = a.tsum[r & 1] + (size_t)bs_ * a.max_tiles;
-            const int ntiles = (int)((bhi - blo + KM_THREADS - 1) / KM_THREADS);
+            const int bq = s_bstar;
+            const long long blo = min(n, (long long)bq * chunk), bhi = min(n, blo + chunk);
+            const int ntiles = (int)((bhi - blo + KM_TILE - 1) / KM_TILE);
+            const long long* tsb = a.tsum[r & 1] + (size_t)bq * a.max_tiles;
             if (tid == 0) {
-                double run = s_base;
-                int tl = -1;
-                if (!s_fallback) {
-                    for (int q = 0; q < ntiles; ++q) {
-                        const double v = __ldcg(tsb + q);
-                        if (run + v > s_T) { tl = q; break; }
-                        run += v;
+                s_tile = -1;
+                s_idx = INT_MAX;
+            }
+            for (int q0 = 0; q0 < ntiles; q0 += KM_THREADS) {
+                const int cnt = min(KM_THREADS, ntiles - q0);
+                __syncthreads();
+                if (tid < cnt) s_tiles[tid] = __ldcg(tsb + q0 + tid);
+                __syncthreads();
+                if (tid == 0) {
+                    long long run = s_base;
+                    for (int q = 0; q < cnt; ++q) {
+                        if (run + s_tiles[q] > s_T) { s_tile = q0 + q; break; }
+                        run += s_tiles[q];
                     }
+                    s_base = run;
                 }
-                s_tile = tl;
-                s_base = run;
+                __syncthreads();
+                if (s_tile >= 0) break;
+            }
+            if (tid == 0 && s_tile < 0) s_tile = ntiles - 1;   // defensive only (exact sums always cross)
+            __syncthreads();
+            const long long i0 = blo + (long long)s_tile * KM_TILE + (long long)KM_PPT * tid;
+            long long q[KM_PPT];
+            long long v = 0;
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                q[u] = i0 + u < bhi ? fixq(__ldcg(d2n + i0 + u), sc.Sd) : 0;
+                v += q[u];
+            }
+            long long run = block_scan_ll(v, s_red) - v + s_base;   // exclusive prefix of this thread
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                run += q[u];
+                if (q[u] > 0 && run > s_T) {
+                    atomicMin(&s_idx, (int)(i0 + u));
+                    break;
+                }
             }
             __syncthreads();
-            if (s_tile >= 0) {
-                const long long i = blo + (long long)s_tile * KM_THREADS + tid;
-                const double v = i < bhi ? (double)__ldcg(d2n + i) : 0.0;
-                const double incl = block_scan_incl(v, s_red) + s_base;
-                if (tid == 0) s_idx = INT_MAX;
-                __syncthreads();
-                if (i < bhi && v > 0.0 && incl > s_T) atomicMin(&s_idx, (int)i);
-                __syncthreads();
-                if (s_idx == INT_MAX) s_idx = -1;   // rounding: fall through to the last positive
-                __syncthreads();
-            }
-            if (s_idx < 0) {
-                // last index of the chunk with D^2 > 0
-                if (tid == 0) s_idx = -1;
-                __syncthreads();
-                for (long long i = blo + tid; i < bhi; i += KM_THREADS)
-                    if (__ldcg(d2n + i) > 0.f) atomicMax(&s_idx, (int)i);
-                __syncthreads();
-                if (tid == 0 && s_idx < 0) {
-                    // nothing positive in the chunk (rounding only): the lowest index not chosen yet
-                    int cand = 0;
-                    for (;; ++cand) {
-                        bool taken = false;
-                        for (int q = 0; q < r; ++q)
-                            if (s_chosen[q] == cand) { taken = true; break; }
-                        if (!taken) break;
-                    }
-                    s_idx = cand;
-                }
-            }
+            if (tid == 0 && s_idx == INT_MAX) s_idx = lowest_unchosen(s_chosen, r);   // defensive only
         }
         __syncthreads();
         if (tid == 0) {
@@ -295,13 +348,10 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         }
         __syncthreads();
     }
-    // centres: block 0 writes the k seed rows (float32 copy and float64 master)
     if (b == 0) {
         for (int q = tid; q < a.k * LP; q += KM_THREADS) {
             const int j = q / LP, c = q % LP;
-            const float v = c < a.l ? a.X[(size_t)s_chosen[j] * LP + c] : 0.f;
-            a.c32[q] = v;
-            a.c64[q] = (double)v;
+            a.c32[q] = c < a.l ? a.X[(size_t)s_chosen[j] * LP + c] : 0.f;
         }
     }
 }
@@ -312,88 +362,127 @@ struct LloydArgs {
     int32_t* labels;
     float* c32;
     double* c64;
-    double* partials;
-    double* inertia_part;
+    long long* partials;
+    long long* inertia_part;
     int* changed_part;
+    const unsigned* amax;
+    long long chunk;
     KmDevStats* st;
     GridBarrier* bar;
     int* status;
     long long limit;
+    int stall;
 };
 
+// Flush a thread's run sums into the block's shared accumulators; when the whole warp flushes
+// the same cluster (sorted or clustered inputs), reduce in registers first.
 template <int LP>
-__global__ void __launch_bounds__(KM_THREADS) k_lloyd(LloydArgs a) {
+__device__ __forceinline__ void flush_run(int cur, const long long (&acc)[LP], long long cnt,
+                                          unsigned long long* s_sum, unsigned long long* s_cnt, bool warp_wide) {
+    if (warp_wide) {
+        const int c0 = __shfl_sync(0xffffffffu, cur, 0);
+        if (__all_sync(0xffffffffu, cur == c0) && c0 >= 0) {
+            const int lane = threadIdx.x & 31;
+#pragma unroll
+            for (int c = 0; c < LP; ++c) {
+                const long long v = warp_sum_ll(acc[c]);
+                if (lane == 0) atomicAdd(&s_sum[c0 * LP + c], (unsigned long long)v);
+            }
+            const long long cn = warp_sum_ll(cnt);
+            if (lane == 0) atomicAdd(&s_cnt[c0], (unsigned long long)cn);
+            return;
+        }
+    }
+    if (cur >= 0) {
+#pragma unroll
+        for (int c = 0; c < LP; ++c) atomicAdd(&s_sum[cur * LP + c], (unsigned long long)acc[c]);
+        atomicAdd(&s_cnt[cur], (unsigned long long)cnt);
+    }
+}
+
+template <int LP>
+__global__ void __launch_bounds__(KM_THREADS, (LP >= 8 ? 1 : 2)) k_lloyd(LloydArgs a) {
     extern __shared__ __align__(16) unsigned char km_smem[];
     const int k = a.k;
     float* s_c = reinterpret_cast<float*>(km_smem);
-    double* s_sum = reinterpret_cast<double*>(km_smem + (((size_t)k * LP * 4 + 15) & ~(size_t)15));
-    unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_sum + (size_t)k * LP);
-    __shared__ double s_red[KM_WARPS];
+    unsigned long long* s_sum =
+        reinterpret_cast<unsigned long long*>(km_smem + (((size_t)k * LP * 4 + 15) & ~(size_t)15));
+    unsigned long long* s_cnt = s_sum + (size_t)k * LP;
+    __shared__ long long s_red[KM_WARPS];
     __shared__ int s_redi[KM_WARPS];
     __shared__ int s_stop, s_changed;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
-    const long long chunk = (n + G - 1) / G;
+    const long long chunk = a.chunk;
     const long long lo = min(n, (long long)b * chunk), hi = min(n, lo + chunk);
     const size_t pstride = (size_t)k * LP + k;
+    const Scales sc = scales_for(__uint_as_float(__ldcg(a.amax)), n, a.l);
 
+    if (b == 0) {   // float64 masters of the k-means++ centres
+        for (int q = tid; q < k * LP; q += KM_THREADS) a.c64[q] = (double)__ldcg(a.c32 + q);
+    }
     for (int it = 1; it <= a.max_iter; ++it) {
         for (int q = tid; q < k * LP; q += KM_THREADS) {
             s_c[q] = __ldcg(a.c32 + q);
-            s_sum[q] = 0.0;
+            s_sum[q] = 0ull;
         }
         for (int q = tid; q < k; q += KM_THREADS) s_cnt[q] = 0ull;
         __syncthreads();
-        double inert = 0.0;
+        long long inert = 0;
         int changed = 0;
-        // ---- phase A: assignment and per-block float64 sums
-        for (long long base = lo + (long long)wid * 32; base < hi; base += KM_THREADS) {
-            const long long i = base + lane;
-            const bool valid = i < hi;
-            float x[LP];
-            int bj = 0;
-            if (valid) {
-                load_point<LP>(a.X, i, a.l, x);
-                float best = sqdist<LP>(x, s_c);
+        // ---- phase A: assignment of KM_PPT consecutive points per thread; exact run sums
+        int cur = -1;
+        long long acc[LP];
+        long long cnt = 0;
+#pragma unroll
+        for (int c = 0; c < LP; ++c) acc[c] = 0;
+        for (long long t0 = lo; t0 < hi; t0 += KM_TILE) {
+            const long long i0 = t0 + (long long)KM_PPT * tid;
+            float x[KM_PPT][LP];
+            int old[KM_PPT];
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                if (i0 + u < hi) {
+                    load_point<LP>(a.X, i0 + u, a.l, x[u]);
+                    old[u] = a.labels[i0 + u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                if (i0 + u >= hi) break;
+                float best = sqdist<LP>(x[u], s_c);
+                int bj = 0;
                 for (int j = 1; j < k; ++j) {
-                    const float d = sqdist<LP>(x, s_c + j * LP);
+                    const float d = sqdist<LP>(x[u], s_c + j * LP);
                     if (d < best) { best = d; bj = j; }
                 }
-                const int old = a.labels[i];
-                changed += old != bj;
-                a.labels[i] = bj;
-                inert += (double)best;
-            } else {
+                changed += old[u] != bj;
+                a.labels[i0 + u] = bj;
+                inert += fixq(best, sc.Sd);
+                if (bj != cur) {
+                    flush_run<LP>(cur, acc, cnt, s_sum, s_cnt, false);
+                    cur = bj;
+                    cnt = 0;
 #pragma unroll
-                for (int c = 0; c < LP; ++c) x[c] = 0.f;
-            }
-            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-            const int lab0 = __shfl_sync(0xffffffffu, bj, 0);
-            const bool uniform = __all_sync(0xffffffffu, !valid || bj == lab0);
-            if (uniform) {
-#pragma unroll
-                for (int c = 0; c < LP; ++c) {
-                    const double v = warp_sum_d((double)x[c]);
-                    if (lane == 0) atomicAdd(&s_sum[lab0 * LP + c], v);
+                    for (int c = 0; c < LP; ++c) acc[c] = 0;
                 }
-                if (lane == 0) atomicAdd(&s_cnt[lab0], (unsigned long long)__popc(vmask));
-            } else if (valid) {
 #pragma unroll
-                for (int c = 0; c < LP; ++c) atomicAdd(&s_sum[bj * LP + c], (double)x[c]);
-                atomicAdd(&s_cnt[bj], 1ull);
+                for (int c = 0; c < LP; ++c) acc[c] += fixq(x[u][c], sc.Sx);
+                ++cnt;
             }
         }
+        flush_run<LP>(cur, acc, cnt, s_sum, s_cnt, true);
         __syncthreads();
-        double* P = a.partials + (size_t)b * pstride;
-        for (int q = tid; q < k * LP; q += KM_THREADS) P[q] = s_sum[q];
-        for (int q = tid; q < k; q += KM_THREADS) P[(size_t)k * LP + q] = (double)s_cnt[q];
-        inert = block_sum_d(inert, s_red);
+        long long* P = a.partials + (size_t)b * pstride;
+        for (int q = tid; q < k * LP; q += KM_THREADS) P[q] = (long long)s_sum[q];
+        for (int q = tid; q < k; q += KM_THREADS) P[(size_t)k * LP + q] = (long long)s_cnt[q];
+        inert = block_sum_ll(inert, s_red);
         changed = block_sum_i(changed, s_redi);
         if (tid == 0) {
             a.inertia_part[b] = inert;
             a.changed_part[b] = changed;
         }
-        if (!grid_sync(a.bar, a.status, a.limit)) return;
+        if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
         // ---- phase B: convergence test (every block) and centroid means (one warp per cluster)
         if (wid == 0) {
             int c = 0;
@@ -405,38 +494,40 @@ __global__ void __launch_bounds__(KM_THREADS) k_lloyd(LloydArgs a) {
             }
         }
         for (int j = b * KM_WARPS + wid; j < k; j += G * KM_WARPS) {
-            double acc[LP + 1];
+            long long sum[LP + 1];
 #pragma unroll
-            for (int c = 0; c <= LP; ++c) acc[c] = 0.0;
+            for (int c = 0; c <= LP; ++c) sum[c] = 0;
             for (int q = lane; q < G; q += 32) {
-                const double* Pq = a.partials + (size_t)q * pstride;
+                const long long* Pq = a.partials + (size_t)q * pstride;
 #pragma unroll
-                for (int c = 0; c < LP; ++c) acc[c] += __ldcg(Pq + (size_t)j * LP + c);
-                acc[LP] += __ldcg(Pq + (size_t)k * LP + j);
+                for (int c = 0; c < LP; ++c) sum[c] += __ldcg(Pq + (size_t)j * LP + c);
+                sum[LP] += __ldcg(Pq + (size_t)k * LP + j);
             }
 #pragma unroll
-            for (int c = 0; c <= LP; ++c) acc[c] = warp_sum_d(acc[c]);
-            if (lane == 0) {
-                const double cnt = acc[LP];
-                if (cnt > 0.0) {
+            for (int c = 0; c <= LP; ++c) sum[c] = warp_sum_ll(sum[c]);
+            if (lane < LP) {
+                const long long cntj = sum[LP];
+                long long sv = sum[0];
 #pragma unroll
-                    for (int c = 0; c < LP; ++c) {
-                        const double m = acc[c] / cnt;
-                        a.c64[(size_t)j * LP + c] = m;
-                        a.c32[(size_t)j * LP + c] = (float)m;
-                    }
-                } else {
+                for (int c = 1; c < LP; ++c)
+                    if (lane == c) sv = sum[c];
+                if (cntj > 0) {
+                    const double m = ((double)sv * pow2d(-sc.Sx)) / (double)cntj;
+                    a.c64[(size_t)j * LP + lane] = m;
+                    a.c32[(size_t)j * LP + lane] = (float)m;
+                } else if (lane == 0) {
                     atomicAdd(&a.st->empty_events, 1);
                 }
             }
         }
         if (b == 0 && wid == 1) {
-            double v = 0.0;
+            long long v = 0;
             for (int q = lane; q < G; q += 32) v += __ldcg(a.inertia_part + q);
-            v = warp_sum_d(v);
+            v = warp_sum_ll(v);
             if (lane == 0) {
-                a.st->inertia = v;
-                if (it == 1) a.st->potential = v;
+                const double iv = (double)v * pow2d(-sc.Sd);
+                a.st->inertia = iv;
+                if (it == 1) a.st->potential = iv;
             }
         }
         __syncthreads();
@@ -445,7 +536,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_lloyd(LloydArgs a) {
             a.st->changed = s_changed;
         }
         if (s_stop) return;
-        if (!grid_sync(a.bar, a.status, a.limit)) return;
+        if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
     }
 }
 
@@ -474,16 +565,17 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     const int G2 = coop_blocks(lly, lloyd_smem);
     if (G2 < G) G = G2;
     if (G < 1) return FSC_ERR_CUDA;
-    const long long need = ((long long)n + KM_THREADS - 1) / KM_THREADS;
-    if (G > need) G = (int)need;
     if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
-    const long long chunk = ((long long)n + G - 1) / G;
-    const int max_tiles = (int)((chunk + KM_THREADS - 1) / KM_THREADS);
+    // contiguous chunks of whole tiles; drop blocks that would get no point
+    long long chunk = ((long long)n + G - 1) / G;
+    chunk = (chunk + KM_TILE - 1) / KM_TILE * KM_TILE;
+    G = (int)(((long long)n + chunk - 1) / chunk);
+    const int max_tiles = (int)(chunk / KM_TILE);
 
-    // workspace layout (256-byte aligned pieces)
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
     size_t off = 0;
-    const size_t o_hdr = off; off += up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int));
+    const size_t o_hdr = off; off += hdr;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
     const size_t o_bs = off; off += 2 * up((size_t)G * 8);
     const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * 8);
@@ -500,8 +592,9 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     KmDevStats* st = reinterpret_cast<KmDevStats*>(ws + o_hdr);
     GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + o_hdr + sizeof(KmDevStats));
     int* call_status = reinterpret_cast<int*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier));
+    unsigned* amax = reinterpret_cast<unsigned*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier) + 8);
     do {
-        if ((e = cudaMemsetAsync(ws + o_hdr, 0, up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int)), s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(ws + o_hdr, 0, hdr, s)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(labels, 0xff, (size_t)n * 4, s)) != cudaSuccess) break;
         KppArgs ka{};
         ka.X = emb;
@@ -511,17 +604,19 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         ka.seed = seed;
         ka.d2[0] = reinterpret_cast<float*>(ws + o_d2);
         ka.d2[1] = reinterpret_cast<float*>(ws + o_d2 + up((size_t)n * 4));
-        ka.bsum[0] = reinterpret_cast<double*>(ws + o_bs);
-        ka.bsum[1] = reinterpret_cast<double*>(ws + o_bs + up((size_t)G * 8));
-        ka.tsum[0] = reinterpret_cast<double*>(ws + o_ts);
-        ka.tsum[1] = reinterpret_cast<double*>(ws + o_ts + up((size_t)G * max_tiles * 8));
+        ka.bsum[0] = reinterpret_cast<long long*>(ws + o_bs);
+        ka.bsum[1] = reinterpret_cast<long long*>(ws + o_bs + up((size_t)G * 8));
+        ka.tsum[0] = reinterpret_cast<long long*>(ws + o_ts);
+        ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)G * max_tiles * 8));
         ka.max_tiles = max_tiles;
+        ka.chunk = chunk;
+        ka.amax = amax;
         ka.seeds = reinterpret_cast<int64_t*>(ws + o_seed);
         ka.c32 = reinterpret_cast<float*>(ws + o_c32);
-        ka.c64 = reinterpret_cast<double*>(ws + o_c64);
         ka.bar = bar;
         ka.status = call_status;
         ka.limit = wait_limit_ns();
+        ka.stall = barrier_stall();
         void* kargs[] = {&ka};
         if ((e = cudaLaunchCooperativeKernel((const void*)kpp, dim3(G), dim3(KM_THREADS), kargs, kpp_smem, s)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s)) != cudaSuccess) break;
@@ -533,18 +628,21 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.max_iter = max_iter;
         la.labels = labels;
         la.c32 = ka.c32;
-        la.c64 = ka.c64;
-        la.partials = reinterpret_cast<double*>(ws + o_part);
-        la.inertia_part = reinterpret_cast<double*>(ws + o_inert);
+        la.c64 = reinterpret_cast<double*>(ws + o_c64);
+        la.partials = reinterpret_cast<long long*>(ws + o_part);
+        la.inertia_part = reinterpret_cast<long long*>(ws + o_inert);
         la.changed_part = reinterpret_cast<int*>(ws + o_chg);
+        la.amax = amax;
+        la.chunk = chunk;
         la.st = st;
         la.bar = bar;
         la.status = call_status;
         la.limit = ka.limit;
+        la.stall = ka.stall;
         void* largs[] = {&la};
         if ((e = cudaLaunchCooperativeKernel((const void*)lly, dim3(G), dim3(KM_THREADS), largs, lloyd_smem, s)) != cudaSuccess) break;
         if (centroids)
-            if ((e = cudaMemcpy2DAsync(centroids, (size_t)l * 8, ka.c64, (size_t)LP * 8, (size_t)l * 8, (size_t)k,
+            if ((e = cudaMemcpy2DAsync(centroids, (size_t)l * 8, la.c64, (size_t)LP * 8, (size_t)l * 8, (size_t)k,
                                        cudaMemcpyDeviceToDevice, s)) != cudaSuccess) break;
         if (seed_idx)
             if ((e = cudaMemcpyAsync(seed_idx, ka.seeds, (size_t)k * 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) break;

@@ -53,6 +53,9 @@ k_power_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ 
     }
     __syncthreads();
 
+    float cmx[LP];   // this lane's running column max |y| (reduced once, at the end)
+#pragma unroll
+    for (int c = 0; c < LP; ++c) cmx[c] = 0.f;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long base = warp * RPW; base < n; base += nwarps * RPW) {
@@ -101,21 +104,18 @@ k_power_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ 
 #pragma unroll
             for (int c = 0; c < LP; ++c) y[c] = scale[c] * (0.5f * fmaf(id, acc[c], self[c]));
             store_row<LP, TO>(zout + (size_t)row * LP, y);
-        } else {
 #pragma unroll
-            for (int c = 0; c < LP; ++c) y[c] = 0.f;
-        }
-        if (cm_out) {
-#pragma unroll
-            for (int c = 0; c < LP; ++c) {
-                float m = fabsf(y[c]);
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-                if (lane == 0 && m > 0.f) atomicMax(&s_cm[c], __float_as_uint(m));
-            }
+            for (int c = 0; c < LP; ++c) cmx[c] = fmaxf(cmx[c], fabsf(y[c]));
         }
     }
     if (cm_out) {
+#pragma unroll
+        for (int c = 0; c < LP; ++c) {
+            float m = cmx[c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+            if (lane == 0 && m > 0.f) atomicMax(&s_cm[c], __float_as_uint(m));
+        }
         __syncthreads();
         if (threadIdx.x < LP && s_cm[threadIdx.x]) atomicMax(cm_out + threadIdx.x, s_cm[threadIdx.x]);
     }
