@@ -147,7 +147,7 @@ struct KppArgs {
     long long* bsum[2];
     long long* tsum[2];
     int max_tiles;
-    long long chunk;     // points per block, a multiple of KM_TILE
+    long long chunk;     // points per block, a multiple of KM_PPT
     unsigned* amax;      // max |x| (float bits), output for the Lloyd launch
     int64_t* seeds;
     float* c32;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     __shared__ int s_bstar, s_tile, s_idx;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
-    const long long chunk = a.chunk;                 // multiple of KM_TILE
+    const long long chunk = a.chunk;                 // multiple of KM_PPT
     const long long lo = min(n, (long long)b * chunk), hi = min(n, lo + chunk);
 
     // ---- phase 0: A = max |x| over the used columns (sets the fixed-point scales)
@@ -367,6 +367,7 @@ struct LloydArgs {
     int* changed_part;
     const unsigned* amax;
     long long chunk;
+    int ntab;
     KmDevStats* st;
     GridBarrier* bar;
     int* status;
@@ -374,68 +375,83 @@ struct LloydArgs {
     int stall;
 };
 
-// Flush a thread's run sums into the block's shared accumulators; when the whole warp flushes
-// the same cluster (sorted or clustered inputs), reduce in registers first.
+// Per-thread accumulation: two register slots (cluster id, exact coordinate sums, count) absorb
+// runs of one label and alternation between two labels; a third label evicts the older slot
+// into the warp's private shared table (no contention between warps).  At the end of the
+// phase a slot that every lane of the warp holds for the same cluster is reduced in registers.
 template <int LP>
-__device__ __forceinline__ void flush_run(int cur, const long long (&acc)[LP], long long cnt,
-                                          unsigned long long* s_sum, unsigned long long* s_cnt, bool warp_wide) {
-    if (warp_wide) {
-        const int c0 = __shfl_sync(0xffffffffu, cur, 0);
-        if (__all_sync(0xffffffffu, cur == c0) && c0 >= 0) {
-            const int lane = threadIdx.x & 31;
+struct Slot {
+    int j;
+    long long cnt;
+    long long s[LP];
+};
+
+template <int LP>
+__device__ __forceinline__ void slot_flush(const Slot<LP>& sl, unsigned long long* tab) {
+    if (sl.j < 0 || sl.cnt == 0) return;
+    unsigned long long* row = tab + (size_t)sl.j * (LP + 1);
 #pragma unroll
-            for (int c = 0; c < LP; ++c) {
-                const long long v = warp_sum_ll(acc[c]);
-                if (lane == 0) atomicAdd(&s_sum[c0 * LP + c], (unsigned long long)v);
-            }
-            const long long cn = warp_sum_ll(cnt);
-            if (lane == 0) atomicAdd(&s_cnt[c0], (unsigned long long)cn);
-            return;
-        }
-    }
-    if (cur >= 0) {
-#pragma unroll
-        for (int c = 0; c < LP; ++c) atomicAdd(&s_sum[cur * LP + c], (unsigned long long)acc[c]);
-        atomicAdd(&s_cnt[cur], (unsigned long long)cnt);
-    }
+    for (int c = 0; c < LP; ++c) atomicAdd(row + c, (unsigned long long)sl.s[c]);
+    atomicAdd(row + LP, (unsigned long long)sl.cnt);
 }
 
 template <int LP>
-__global__ void __launch_bounds__(KM_THREADS, (LP >= 8 ? 1 : 2)) k_lloyd(LloydArgs a) {
+__device__ __forceinline__ void slot_flush_warp(const Slot<LP>& sl, unsigned long long* tab) {
+    const int j0 = __shfl_sync(0xffffffffu, sl.j, 0);
+    if (__all_sync(0xffffffffu, sl.j == j0)) {
+        if (j0 < 0) return;
+        const int lane = threadIdx.x & 31;
+        unsigned long long* row = tab + (size_t)j0 * (LP + 1);
+#pragma unroll
+        for (int c = 0; c < LP; ++c) {
+            const long long v = warp_sum_ll(sl.s[c]);
+            if (lane == 0) atomicAdd(row + c, (unsigned long long)v);
+        }
+        const long long cn = warp_sum_ll(sl.cnt);
+        if (lane == 0) atomicAdd(row + LP, (unsigned long long)cn);
+        return;
+    }
+    slot_flush<LP>(sl, tab);
+}
+
+template <int LP>
+__global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydArgs a) {
     extern __shared__ __align__(16) unsigned char km_smem[];
     const int k = a.k;
+    const int ntab = a.ntab;                              // private tables (warp w uses w % ntab)
+    const size_t rowlen = (size_t)k * (LP + 1);
     float* s_c = reinterpret_cast<float*>(km_smem);
-    unsigned long long* s_sum =
+    unsigned long long* s_tab =
         reinterpret_cast<unsigned long long*>(km_smem + (((size_t)k * LP * 4 + 15) & ~(size_t)15));
-    unsigned long long* s_cnt = s_sum + (size_t)k * LP;
     __shared__ long long s_red[KM_WARPS];
     __shared__ int s_redi[KM_WARPS];
+    __shared__ long long s_tot[LP + 1];
     __shared__ int s_stop, s_changed;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
     const long long chunk = a.chunk;
     const long long lo = min(n, (long long)b * chunk), hi = min(n, lo + chunk);
-    const size_t pstride = (size_t)k * LP + k;
     const Scales sc = scales_for(__uint_as_float(__ldcg(a.amax)), n, a.l);
+    unsigned long long* my_tab = s_tab + (size_t)(wid % ntab) * rowlen;
 
     if (b == 0) {   // float64 masters of the k-means++ centres
         for (int q = tid; q < k * LP; q += KM_THREADS) a.c64[q] = (double)__ldcg(a.c32 + q);
     }
     for (int it = 1; it <= a.max_iter; ++it) {
-        for (int q = tid; q < k * LP; q += KM_THREADS) {
-            s_c[q] = __ldcg(a.c32 + q);
-            s_sum[q] = 0ull;
-        }
-        for (int q = tid; q < k; q += KM_THREADS) s_cnt[q] = 0ull;
+        for (int q = tid; q < k * LP; q += KM_THREADS) s_c[q] = __ldcg(a.c32 + q);
+        for (size_t q = tid; q < (size_t)ntab * rowlen; q += KM_THREADS) s_tab[q] = 0ull;
         __syncthreads();
         long long inert = 0;
         int changed = 0;
-        // ---- phase A: assignment of KM_PPT consecutive points per thread; exact run sums
-        int cur = -1;
-        long long acc[LP];
-        long long cnt = 0;
+        // ---- phase A: assignment of KM_PPT consecutive points per thread
+        Slot<LP> sl[2];
 #pragma unroll
-        for (int c = 0; c < LP; ++c) acc[c] = 0;
+        for (int q = 0; q < 2; ++q) {
+            sl[q].j = -1;
+            sl[q].cnt = 0;
+#pragma unroll
+            for (int c = 0; c < LP; ++c) sl[q].s[c] = 0;
+        }
         for (long long t0 = lo; t0 < hi; t0 += KM_TILE) {
             const long long i0 = t0 + (long long)KM_PPT * tid;
             float x[KM_PPT][LP];
@@ -445,37 +461,68 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 8 ? 1 : 2)) k_lloyd(LloydAr
                 if (i0 + u < hi) {
                     load_point<LP>(a.X, i0 + u, a.l, x[u]);
                     old[u] = a.labels[i0 + u];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) x[u][c] = 0.f;
+                    old[u] = 0;
+                }
+            }
+            float best[KM_PPT];
+            int bj[KM_PPT];
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                best[u] = __int_as_float(0x7f800000);   // +inf
+                bj[u] = 0;
+            }
+            for (int j = 0; j < k; ++j) {
+                float cj[LP];
+#pragma unroll
+                for (int c = 0; c < LP; ++c) cj[c] = s_c[j * LP + c];
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    const float d = sqdist<LP>(x[u], cj);
+                    if (d < best[u]) { best[u] = d; bj[u] = j; }
                 }
             }
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
                 if (i0 + u >= hi) break;
-                float best = sqdist<LP>(x[u], s_c);
-                int bj = 0;
-                for (int j = 1; j < k; ++j) {
-                    const float d = sqdist<LP>(x[u], s_c + j * LP);
-                    if (d < best) { best = d; bj = j; }
-                }
-                changed += old[u] != bj;
-                a.labels[i0 + u] = bj;
-                inert += fixq(best, sc.Sd);
-                if (bj != cur) {
-                    flush_run<LP>(cur, acc, cnt, s_sum, s_cnt, false);
-                    cur = bj;
-                    cnt = 0;
+                const int lab = bj[u];
+                changed += old[u] != lab;
+                a.labels[i0 + u] = lab;
+                inert += fixq(best[u], sc.Sd);
+                int q;
+                if (sl[0].j == lab) q = 0;
+                else if (sl[1].j == lab) q = 1;
+                else {
+                    // evict the slot that was not used last (slot 1 holds the older run)
+                    slot_flush<LP>(sl[1], my_tab);
+                    sl[1] = sl[0];
+                    sl[0].j = lab;
+                    sl[0].cnt = 0;
 #pragma unroll
-                    for (int c = 0; c < LP; ++c) acc[c] = 0;
+                    for (int c = 0; c < LP; ++c) sl[0].s[c] = 0;
+                    q = 0;
+                }
+                if (q == 1) {   // keep the most recent label in slot 0
+                    const Slot<LP> t = sl[0];
+                    sl[0] = sl[1];
+                    sl[1] = t;
                 }
 #pragma unroll
-                for (int c = 0; c < LP; ++c) acc[c] += fixq(x[u][c], sc.Sx);
-                ++cnt;
+                for (int c = 0; c < LP; ++c) sl[0].s[c] += fixq(x[u][c], sc.Sx);
+                ++sl[0].cnt;
             }
         }
-        flush_run<LP>(cur, acc, cnt, s_sum, s_cnt, true);
+        slot_flush_warp<LP>(sl[0], my_tab);
+        slot_flush_warp<LP>(sl[1], my_tab);
         __syncthreads();
-        long long* P = a.partials + (size_t)b * pstride;
-        for (int q = tid; q < k * LP; q += KM_THREADS) P[q] = (long long)s_sum[q];
-        for (int q = tid; q < k; q += KM_THREADS) P[(size_t)k * LP + q] = (long long)s_cnt[q];
+        // block totals -> transposed partials[(j*(LP+1) + c) * G + b]
+        for (size_t q = tid; q < rowlen; q += KM_THREADS) {
+            unsigned long long v = 0;
+            for (int t = 0; t < ntab; ++t) v += s_tab[(size_t)t * rowlen + q];
+            a.partials[q * G + b] = (long long)v;
+        }
         inert = block_sum_ll(inert, s_red);
         changed = block_sum_i(changed, s_redi);
         if (tid == 0) {
@@ -483,52 +530,73 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 8 ? 1 : 2)) k_lloyd(LloydAr
             a.changed_part[b] = changed;
         }
         if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
-        // ---- phase B: convergence test (every block) and centroid means (one warp per cluster)
-        if (wid == 0) {
+        // ---- phase B: every block reads the changed total; block b updates clusters j = b, b+G, ...
+        if (wid == KM_WARPS - 1) {
             int c = 0;
-            for (int q = lane; q < G; q += 32) c += __ldcg(a.changed_part + q);
+            for (int q0 = 0; q0 < G; q0 += 256) {
+                int v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int q = q0 + u * 32 + lane;
+                    v[u] = q < G ? __ldcg(a.changed_part + q) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) c += v[u];
+            }
             c = warp_sum_i(c);
             if (lane == 0) {
                 s_changed = c;
                 s_stop = (c == 0 || it == a.max_iter) ? 1 : 0;
             }
         }
-        for (int j = b * KM_WARPS + wid; j < k; j += G * KM_WARPS) {
-            long long sum[LP + 1];
+        if (b == 0 && wid == KM_WARPS - 2) {
+            long long tot = 0;
+            for (int q0 = 0; q0 < G; q0 += 256) {
+                long long v[8];
 #pragma unroll
-            for (int c = 0; c <= LP; ++c) sum[c] = 0;
-            for (int q = lane; q < G; q += 32) {
-                const long long* Pq = a.partials + (size_t)q * pstride;
-#pragma unroll
-                for (int c = 0; c < LP; ++c) sum[c] += __ldcg(Pq + (size_t)j * LP + c);
-                sum[LP] += __ldcg(Pq + (size_t)k * LP + j);
-            }
-#pragma unroll
-            for (int c = 0; c <= LP; ++c) sum[c] = warp_sum_ll(sum[c]);
-            if (lane < LP) {
-                const long long cntj = sum[LP];
-                long long sv = sum[0];
-#pragma unroll
-                for (int c = 1; c < LP; ++c)
-                    if (lane == c) sv = sum[c];
-                if (cntj > 0) {
-                    const double m = ((double)sv * pow2d(-sc.Sx)) / (double)cntj;
-                    a.c64[(size_t)j * LP + lane] = m;
-                    a.c32[(size_t)j * LP + lane] = (float)m;
-                } else if (lane == 0) {
-                    atomicAdd(&a.st->empty_events, 1);
+                for (int u = 0; u < 8; ++u) {
+                    const int q = q0 + u * 32 + lane;
+                    v[u] = q < G ? __ldcg(a.inertia_part + q) : 0;
                 }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) tot += v[u];
             }
-        }
-        if (b == 0 && wid == 1) {
-            long long v = 0;
-            for (int q = lane; q < G; q += 32) v += __ldcg(a.inertia_part + q);
-            v = warp_sum_ll(v);
+            tot = warp_sum_ll(tot);
             if (lane == 0) {
-                const double iv = (double)v * pow2d(-sc.Sd);
+                const double iv = (double)tot * pow2d(-sc.Sd);
                 a.st->inertia = iv;
                 if (it == 1) a.st->potential = iv;
             }
+        }
+        for (int j = b; j < k; j += G) {
+            if (wid <= LP) {   // warp c sums component c (c = LP: the count) over the G blocks
+                const long long* src = a.partials + ((size_t)j * (LP + 1) + wid) * G;
+                long long tot = 0;
+                for (int q0 = 0; q0 < G; q0 += 256) {
+                    long long v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int q = q0 + u * 32 + lane;
+                        v[u] = q < G ? __ldcg(src + q) : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) tot += v[u];
+                }
+                tot = warp_sum_ll(tot);
+                if (lane == 0) s_tot[wid] = tot;
+            }
+            __syncthreads();
+            if (tid < LP) {
+                const long long cntj = s_tot[LP];
+                if (cntj > 0) {
+                    const double m = ((double)s_tot[tid] * pow2d(-sc.Sx)) / (double)cntj;
+                    a.c64[(size_t)j * LP + tid] = m;
+                    a.c32[(size_t)j * LP + tid] = (float)m;
+                } else if (tid == 0) {
+                    atomicAdd(&a.st->empty_events, 1);
+                }
+            }
+            __syncthreads();
         }
         __syncthreads();
         if (b == 0 && tid == 0) {
@@ -556,7 +624,12 @@ template <int LP>
 static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed, int max_iter, int32_t* labels,
                             double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats, cudaStream_t s) {
     const size_t kpp_smem = (size_t)k * sizeof(int);
-    const size_t lloyd_smem = (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)k * LP * 8 + (size_t)k * 8;
+    // private accumulation tables: as many as fit in 64 KB (at least one, at most one per warp)
+    const size_t tab_bytes = (size_t)k * (LP + 1) * 8;
+    int ntab = (int)(65536 / tab_bytes);
+    if (ntab > KM_WARPS) ntab = KM_WARPS;
+    if (ntab < 1) ntab = 1;
+    const size_t lloyd_smem = (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes;
     auto kpp = k_kmeanspp<LP>;
     auto lly = k_lloyd<LP>;
     FSC_CUDA(cudaFuncSetAttribute(kpp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kpp_smem));
@@ -566,11 +639,11 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     if (G2 < G) G = G2;
     if (G < 1) return FSC_ERR_CUDA;
     if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
-    // contiguous chunks of whole tiles; drop blocks that would get no point
+    // contiguous chunks (multiples of KM_PPT points); drop blocks that would get no point
     long long chunk = ((long long)n + G - 1) / G;
-    chunk = (chunk + KM_TILE - 1) / KM_TILE * KM_TILE;
+    chunk = (chunk + KM_PPT - 1) / KM_PPT * KM_PPT;
     G = (int)(((long long)n + chunk - 1) / chunk);
-    const int max_tiles = (int)(chunk / KM_TILE);
+    const int max_tiles = (int)((chunk + KM_TILE - 1) / KM_TILE);
 
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
@@ -634,6 +707,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.changed_part = reinterpret_cast<int*>(ws + o_chg);
         la.amax = amax;
         la.chunk = chunk;
+        la.ntab = ntab;
         la.st = st;
         la.bar = bar;
         la.status = call_status;
