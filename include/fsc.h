@@ -43,7 +43,8 @@ typedef enum fsc_status {
     FSC_ERR_OOM = 6,            /* device allocation failed */
     FSC_ERR_CUDA = 7,           /* a CUDA runtime call failed */
     FSC_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up */
-    FSC_ERR_UNSORTED = 9        /* symmetry check asked for, but a row's columns are not increasing */
+    FSC_ERR_UNSORTED = 9,       /* symmetry check asked for, but a row's columns are not increasing */
+    FSC_ERR_TOO_LARGE = 10      /* problem needs more scratch than fsc_kmeans_static's fixed array */
 } fsc_status;
 
 typedef enum fsc_dtype {
@@ -168,6 +169,29 @@ fsc_status fsc_power_step(const fsc_graph* g, int l, fsc_dtype store, const void
 fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int max_iter,
                       int32_t* labels, double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats,
                       void* stream);
+
+/*
+ * fsc_kmeans_static - fsc_kmeans without any device allocation.
+ *
+ * No counterpart in the paper: an engineering variant for callers that cannot allocate
+ * device memory once they are running, e.g. code inside a runtime that hands out a fixed
+ * memory budget up front, or a latency-critical loop where an allocation could block or
+ * fail.  Same arguments, same kernels and same results as fsc_kmeans; the scratch space
+ * (about 8 bytes per point plus per-block partial sums) lives in one fixed array of
+ * FSC_KMEANS_STATIC_SCRATCH_BYTES compiled into the library, which every GPU that loads the
+ * library keeps reserved until the process exits.
+ *  - Problems whose scratch does not fit return FSC_ERR_TOO_LARGE (with 152 SMs this admits,
+ *    for example, n = 1,048,576 points with k = 64 and ld = 8).
+ *  - All calls on a device share the one array: calls that may run at the same time on the
+ *    GPU (different streams, threads or processes sharing the context) race; serialise them.
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *    with that device current); make that first call before any stream capture.
+ *  - Always synchronous: it waits for `stream` and reports device-side errors; stats may be NULL.
+ */
+#define FSC_KMEANS_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+fsc_status fsc_kmeans_static(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int max_iter,
+                             int32_t* labels, double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats,
+                             void* stream);
 
 /*
  * fsc_cluster - Algorithm 2 end to end: fsc_embed then fsc_kmeans on its output.

@@ -33,7 +33,7 @@ EMBED_RESCALE = 0x1
 _STATUS = {
     0: "FSC_OK", 1: "FSC_ERR_INVALID_ARG", 2: "FSC_ERR_INDEX_RANGE", 3: "FSC_ERR_NOT_SYMMETRIC",
     4: "FSC_ERR_SELF_LOOP", 5: "FSC_ERR_BAD_WEIGHT", 6: "FSC_ERR_OOM", 7: "FSC_ERR_CUDA",
-    8: "FSC_ERR_TIMEOUT", 9: "FSC_ERR_UNSORTED",
+    8: "FSC_ERR_TIMEOUT", 9: "FSC_ERR_UNSORTED", 10: "FSC_ERR_TOO_LARGE",
 }
 
 
@@ -81,6 +81,8 @@ def lib() -> C.CDLL:
         L.fsc_embed.argtypes = [vp, i32, i32, u64, i32, vp, C.POINTER(EmbedOpts), vp]
         L.fsc_power_step.argtypes = [vp, i32, i32, vp, vp, i32, vp]
         L.fsc_kmeans.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
+        L.fsc_kmeans_static.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
+        L.fsc_kmeans_static.restype = i32
         L.fsc_cluster.argtypes = [vp, i32, i32, i32, u64, i32, i32, vp, C.POINTER(KmeansStats),
                                   C.POINTER(EmbedOpts), vp]
         L.fsc_default_params.argtypes = [i64, i32, i32, C.POINTER(i32), C.POINTER(i32)]

@@ -313,6 +313,7 @@ extern "C" const char* fsc_status_string(fsc_status s) {
         case FSC_ERR_CUDA: return "CUDA runtime error";
         case FSC_ERR_TIMEOUT: return "device-side wait timed out";
         case FSC_ERR_UNSORTED: return "row columns not increasing (required by the symmetry check)";
+        case FSC_ERR_TOO_LARGE: return "problem exceeds the fixed scratch array of fsc_kmeans_static";
     }
     return "unknown status";
 }

@@ -26,6 +26,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "fsc_internal.cuh"
 
 namespace fsc {
@@ -790,4 +792,178 @@ extern "C" fsc_status fsc_cluster(const fsc_graph* g, int k, int l, int t, uint6
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_status(e);
     }
     return rc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// fsc_kmeans_static: the same k-means++ and Lloyd kernels, with every scratch buffer carved out
+// of one fixed device array instead of a stream-ordered allocation.  For callers that must not
+// allocate device memory while they run (code inside a memory-capped or pre-sized runtime, or a
+// real-time loop whose memory is reserved up front): the array below is part of the library's
+// device image, so it exists on every GPU that loads the library and stays reserved until the
+// process exits.
+// ---------------------------------------------------------------------------------------------
+namespace fsc {
+
+static __device__ __align__(256) unsigned char g_kmeans_static_scratch[FSC_KMEANS_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kStaticMaxDevices = 64;
+void* g_static_base[kStaticMaxDevices];
+std::once_flag g_static_once[kStaticMaxDevices];
+cudaError_t g_static_err[kStaticMaxDevices];
+
+// Host code cannot use the array's name as a device address; look the address up once per device
+// (with that device current) and keep it.
+cudaError_t static_scratch(int dev, void** out) {
+    std::call_once(g_static_once[dev], [dev] {
+        void* p = nullptr;
+        g_static_err[dev] = cudaGetSymbolAddress(&p, g_kmeans_static_scratch);
+        g_static_base[dev] = (g_static_err[dev] == cudaSuccess) ? p : nullptr;
+    });
+    *out = g_static_base[dev];
+    return g_static_err[dev];
+}
+}  // namespace
+
+template <int LP>
+static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64_t seed, int max_iter,
+                                   int32_t* labels, double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats,
+                                   cudaStream_t s) {
+    int dev = 0;
+    FSC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) return FSC_ERR_INVALID_ARG;
+    void* basep = nullptr;
+    FSC_CUDA(static_scratch(dev, &basep));
+    char* ws = static_cast<char*>(basep);
+    if (!ws) return FSC_ERR_CUDA;
+
+    const size_t kpp_smem = (size_t)k * sizeof(int);
+    const size_t tab_bytes = (size_t)k * (LP + 1) * 8;
+    int ntab = (int)(65536 / tab_bytes);
+    if (ntab > KM_WARPS) ntab = KM_WARPS;
+    if (ntab < 1) ntab = 1;
+    const size_t lloyd_smem = (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes;
+    auto kpp = k_kmeanspp<LP>;
+    auto lly = k_lloyd<LP>;
+    FSC_CUDA(cudaFuncSetAttribute(kpp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kpp_smem));
+    FSC_CUDA(cudaFuncSetAttribute(lly, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lloyd_smem));
+    int G = coop_blocks(kpp, kpp_smem);
+    const int G2 = coop_blocks(lly, lloyd_smem);
+    if (G2 < G) G = G2;
+    if (G < 1) return FSC_ERR_CUDA;
+    if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
+    long long chunk = ((long long)n + G - 1) / G;
+    chunk = (chunk + KM_PPT - 1) / KM_PPT * KM_PPT;
+    G = (int)(((long long)n + chunk - 1) / chunk);
+    const int max_tiles = (int)((chunk + KM_TILE - 1) / KM_TILE);
+
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
+    size_t off = 0;
+    const size_t o_hdr = off; off += hdr;
+    const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
+    const size_t o_bs = off; off += 2 * up((size_t)G * 8);
+    const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * 8);
+    const size_t o_part = off; off += up((size_t)G * ((size_t)k * LP + k) * 8);
+    const size_t o_inert = off; off += up((size_t)G * 8);
+    const size_t o_chg = off; off += up((size_t)G * 4);
+    const size_t o_c64 = off; off += up((size_t)k * LP * 8);
+    const size_t o_c32 = off; off += up((size_t)k * LP * 4);
+    const size_t o_seed = off; off += up((size_t)k * 8);
+    if (off > (size_t)FSC_KMEANS_STATIC_SCRATCH_BYTES) return FSC_ERR_TOO_LARGE;
+
+    KmDevStats* st = reinterpret_cast<KmDevStats*>(ws + o_hdr);
+    GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + o_hdr + sizeof(KmDevStats));
+    int* call_status = reinterpret_cast<int*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier));
+    unsigned* amax = reinterpret_cast<unsigned*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier) + 8);
+    // the array keeps the previous call's contents: clear what the kernels expect to start at zero
+    FSC_CUDA(cudaMemsetAsync(ws + o_hdr, 0, hdr, s));
+    FSC_CUDA(cudaMemsetAsync(labels, 0xff, (size_t)n * 4, s));
+    KppArgs ka{};
+    ka.X = emb;
+    ka.n = n;
+    ka.l = l;
+    ka.k = k;
+    ka.seed = seed;
+    ka.d2[0] = reinterpret_cast<float*>(ws + o_d2);
+    ka.d2[1] = reinterpret_cast<float*>(ws + o_d2 + up((size_t)n * 4));
+    ka.bsum[0] = reinterpret_cast<long long*>(ws + o_bs);
+    ka.bsum[1] = reinterpret_cast<long long*>(ws + o_bs + up((size_t)G * 8));
+    ka.tsum[0] = reinterpret_cast<long long*>(ws + o_ts);
+    ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)G * max_tiles * 8));
+    ka.max_tiles = max_tiles;
+    ka.chunk = chunk;
+    ka.amax = amax;
+    ka.seeds = reinterpret_cast<int64_t*>(ws + o_seed);
+    ka.c32 = reinterpret_cast<float*>(ws + o_c32);
+    ka.bar = bar;
+    ka.status = call_status;
+    ka.limit = wait_limit_ns();
+    ka.stall = barrier_stall();
+    void* kargs[] = {&ka};
+    FSC_CUDA(cudaLaunchCooperativeKernel((const void*)kpp, dim3(G), dim3(KM_THREADS), kargs, kpp_smem, s));
+    FSC_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
+    LloydArgs la{};
+    la.X = emb;
+    la.n = n;
+    la.l = l;
+    la.k = k;
+    la.max_iter = max_iter;
+    la.labels = labels;
+    la.c32 = ka.c32;
+    la.c64 = reinterpret_cast<double*>(ws + o_c64);
+    la.partials = reinterpret_cast<long long*>(ws + o_part);
+    la.inertia_part = reinterpret_cast<long long*>(ws + o_inert);
+    la.changed_part = reinterpret_cast<int*>(ws + o_chg);
+    la.amax = amax;
+    la.chunk = chunk;
+    la.ntab = ntab;
+    la.st = st;
+    la.bar = bar;
+    la.status = call_status;
+    la.limit = ka.limit;
+    la.stall = ka.stall;
+    void* largs[] = {&la};
+    FSC_CUDA(cudaLaunchCooperativeKernel((const void*)lly, dim3(G), dim3(KM_THREADS), largs, lloyd_smem, s));
+    if (centroids)
+        FSC_CUDA(cudaMemcpy2DAsync(centroids, (size_t)l * 8, la.c64, (size_t)LP * 8, (size_t)l * 8, (size_t)k,
+                                   cudaMemcpyDeviceToDevice, s));
+    if (seed_idx) FSC_CUDA(cudaMemcpyAsync(seed_idx, ka.seeds, (size_t)k * 8, cudaMemcpyDeviceToDevice, s));
+    KmDevStats hst{};
+    int hstatus = 0;
+    FSC_CUDA(cudaMemcpyAsync(&hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+    FSC_CUDA(cudaMemcpyAsync(&hstatus, call_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FSC_CUDA(cudaStreamSynchronize(s));
+    const fsc_status rc = status_from_bits(hstatus);
+    if (stats) {
+        stats->iterations = hst.iterations;
+        stats->changed = hst.changed;
+        stats->empty_events = hst.empty_events;
+        stats->device_status = (int32_t)rc;
+        stats->inertia = hst.inertia;
+        stats->seeding_potential = hst.potential;
+    }
+    return rc;
+}
+
+}  // namespace fsc
+
+extern "C" fsc_status fsc_kmeans_static(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed,
+                                        int max_iter, int32_t* labels, double* centroids, int64_t* seed_idx,
+                                        fsc_kmeans_stats* stats, void* stream) {
+    if (!emb || !labels || n < 1 || n > 2147483647LL || l < 1 || l > ld || k < 1 || (int64_t)k > n || k > 1024 ||
+        max_iter < 1)
+        return FSC_ERR_INVALID_ARG;
+    if (ld != 1 && ld != 2 && ld != 4 && ld != 8) return FSC_ERR_INVALID_ARG;
+    if ((int64_t)k * ld > 4096) return FSC_ERR_INVALID_ARG;
+    const size_t al = (size_t)ld * 4 < 16 ? (size_t)ld * 4 : 16;
+    if (reinterpret_cast<uintptr_t>(emb) % al) return FSC_ERR_INVALID_ARG;
+    cudaStream_t s = fsc::as_stream(stream);
+    switch (ld) {
+        case 1: return fsc::kmeans_lp_static<1>(emb, (int)n, l, k, seed, max_iter, labels, centroids, seed_idx, stats, s);
+        case 2: return fsc::kmeans_lp_static<2>(emb, (int)n, l, k, seed, max_iter, labels, centroids, seed_idx, stats, s);
+        case 4: return fsc::kmeans_lp_static<4>(emb, (int)n, l, k, seed, max_iter, labels, centroids, seed_idx, stats, s);
+        case 8: return fsc::kmeans_lp_static<8>(emb, (int)n, l, k, seed, max_iter, labels, centroids, seed_idx, stats, s);
+    }
+    return FSC_ERR_INVALID_ARG;
 }
