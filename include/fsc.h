@@ -202,6 +202,62 @@ fsc_status fsc_cluster(const fsc_graph* g, int k, int l, int t, uint64_t seed, f
                        int32_t* labels, fsc_kmeans_stats* stats, const fsc_embed_opts* opts, void* stream);
 
 /*
+ * fsc_autotune - time the lane counts of the power step (4, 8, 16, 32 lanes per row) on g.
+ *
+ * No counterpart in the paper (a tuning aid).  Runs one warm-up and five timed power steps per
+ * candidate on scratch iterates, records the fastest in a process-wide table keyed by (row
+ * width fsc_pad_l(l), storage type, weighted or not, half-octave bucket of the average degree)
+ * and returns it.  Later fsc_embed / fsc_cluster calls with threads_per_row = 0, and batch
+ * plans, use the table for graphs in the same bucket.  Synchronous; allocates its scratch.
+ */
+fsc_status fsc_autotune(const fsc_graph* g, int l, fsc_dtype store, int* best_threads_per_row, float* best_us,
+                        void* stream);
+
+/*
+ * Batched Algorithm 2 (no counterpart in the paper: many independent graphs at once).
+ *
+ * The batch is the disjoint union of num_graphs graphs in one CSR with global vertex ids:
+ * graph g owns vertices [vertex_offset[g], vertex_offset[g+1]) and every edge of its rows must
+ * stay inside that range (checked).  Each graph gets its own k, l, t and seed; l or t NULL
+ * (or l[g] = 0, t[g] < 0) take fsc_default_params mode 0.  fsc_batch_create validates the
+ * union, computes degrees, assigns lanes per row (autotuned with FSC_BATCH_AUTOTUNE), orders
+ * the graphs largest first, allocates the per-graph workspace and captures the work (a queue
+ * reset and one persistent kernel in which one CTA runs one whole graph) into a CUDA graph.
+ * fsc_batch_run replays that graph on `stream` (asynchronous); labels[v] receives the local
+ * cluster id (0..k_g-1) of global vertex v.  Per graph the result equals fsc_cluster with the
+ * same parameters and lanes per row.  The plan borrows row_ptr, col_idx, w and labels.
+ * Limits: k_g <= 256, l_g <= 8, total vertices < 2^31.
+ */
+#define FSC_BATCH_AUTOTUNE 0x2u
+typedef struct fsc_batch fsc_batch;   /* opaque */
+typedef struct fsc_batch_desc {
+    int32_t num_graphs;
+    const int64_t* vertex_offset;   /* host, num_graphs + 1, vertex_offset[0] = 0 */
+    const int64_t* row_ptr;         /* device, vertex_offset[num_graphs] + 1 entries */
+    const int32_t* col_idx;         /* device, global vertex ids */
+    const float* w;                 /* device or NULL (unit weights) */
+    const int32_t* k;               /* host, clusters per graph */
+    const int32_t* l;               /* host or NULL */
+    const int32_t* t;               /* host or NULL */
+    const uint64_t* seed;           /* host */
+    int32_t* labels;                /* device output, vertex_offset[num_graphs] entries */
+    int32_t store;                  /* fsc_dtype of the iterates */
+    int32_t max_iter;               /* Lloyd iteration cap per graph */
+    uint32_t flags;                 /* FSC_BATCH_AUTOTUNE | FSC_VALIDATE_SYMMETRY */
+} fsc_batch_desc;
+
+fsc_status fsc_batch_create(const fsc_batch_desc* desc, void* stream, fsc_batch** out);
+fsc_status fsc_batch_run(fsc_batch* batch, void* stream);
+/* Synchronises `stream`; any output may be NULL.  stats: host, num_graphs entries.
+ * seed_idx: host, sum of k_g (graph by graph).  centroids: host, sum of k_g * l_g doubles. */
+fsc_status fsc_batch_results(fsc_batch* batch, fsc_kmeans_stats* stats, int64_t* seed_idx, double* centroids,
+                             void* stream);
+/* Copies graph `graph`'s float32 embedding D^-1/2 M^t X0 of the last run into out (device,
+ * n_g * fsc_pad_l(l_g) floats).  Asynchronous on `stream`. */
+fsc_status fsc_batch_embedding(fsc_batch* batch, int graph, float* out, void* stream);
+fsc_status fsc_batch_destroy(fsc_batch* batch);
+
+/*
  * fsc_default_params - l and t for n vertices and k clusters (host, no device work).
  * mode 0: l = max(1, ceil(log2 k)), t = ceil(log2 n).
  * mode 1: the paper's practical remark after Theorem 3.2, l = max(1, ceil(ln k)),

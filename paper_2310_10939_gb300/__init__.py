@@ -21,7 +21,7 @@ import os
 __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
     "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
-    "F32", "BF16", "VALIDATE_SYMMETRY", "EMBED_RESCALE",
+    "F32", "BF16", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
@@ -29,6 +29,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
 F32, BF16 = 0, 1
 VALIDATE_SYMMETRY = 0x1
 EMBED_RESCALE = 0x1
+BATCH_AUTOTUNE = 0x2
 
 _STATUS = {
     0: "FSC_OK", 1: "FSC_ERR_INVALID_ARG", 2: "FSC_ERR_INDEX_RANGE", 3: "FSC_ERR_NOT_SYMMETRIC",
@@ -55,6 +56,13 @@ class KmeansStats(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [("num_graphs", C.c_int32), ("vertex_offset", C.c_void_p), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("w", C.c_void_p), ("k", C.c_void_p), ("l", C.c_void_p),
+                ("t", C.c_void_p), ("seed", C.c_void_p), ("labels", C.c_void_p), ("store", C.c_int32),
+                ("max_iter", C.c_int32), ("flags", C.c_uint32)]
 
 
 class GraphInfo(C.Structure):
@@ -85,6 +93,15 @@ def lib() -> C.CDLL:
         L.fsc_kmeans_static.restype = i32
         L.fsc_cluster.argtypes = [vp, i32, i32, i32, u64, i32, i32, vp, C.POINTER(KmeansStats),
                                   C.POINTER(EmbedOpts), vp]
+        L.fsc_autotune.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float), vp]
+        L.fsc_batch_create.argtypes = [C.POINTER(BatchDesc), vp, C.POINTER(vp)]
+        L.fsc_batch_run.argtypes = [vp, vp]
+        L.fsc_batch_results.argtypes = [vp, vp, vp, vp, vp]
+        L.fsc_batch_destroy.argtypes = [vp]
+        L.fsc_batch_embedding.argtypes = [vp, i32, vp, vp]
+        for name in ("fsc_autotune", "fsc_batch_create", "fsc_batch_run", "fsc_batch_results", "fsc_batch_destroy",
+                     "fsc_batch_embedding"):
+            getattr(L, name).restype = i32
         L.fsc_default_params.argtypes = [i64, i32, i32, C.POINTER(i32), C.POINTER(i32)]
         L.fsc_sync_status.argtypes = [vp]
         L.fsc_set_wait_limit_ns.argtypes = [i64]
@@ -282,3 +299,104 @@ def cluster(g: Graph, k: int, l: int, t: int, seed: int, store: int = F32, max_i
     _check(lib().fsc_cluster(g.handle, int(k), int(l), int(t), int(seed) & (2**64 - 1), int(store), int(max_iter),
                              _ptr(labels), C.byref(st), C.byref(o), _stream(stream)), "fsc_cluster")
     return labels, st.as_dict()
+
+
+def autotune(g: Graph, l: int, store: int = F32, stream=None):
+    """fsc_autotune: returns (best lanes per row, microseconds per power step)."""
+    best, us = C.c_int(), C.c_float()
+    _check(lib().fsc_autotune(g.handle, int(l), int(store), C.byref(best), C.byref(us), _stream(stream)),
+           "fsc_autotune")
+    return best.value, us.value
+
+
+class Batch:
+    """A batched clustering plan over the disjoint union of many graphs (fsc_batch_create).
+
+    ``row_ptr``/``col`` (and ``w``) are the union CSR on the device with global vertex ids;
+    ``vertex_offset`` (host, int64, G+1) delimits the graphs; ``k``, ``l``, ``t``, ``seed`` are
+    per-graph host arrays (``l``/``t`` may be None for the defaults).  ``run()`` replays the
+    captured CUDA graph; ``labels`` (device, int32) receives local cluster ids.
+    """
+
+    def __init__(self, vertex_offset, row_ptr, col, k, seed, w=None, l=None, t=None, store: int = F32,
+                 max_iter: int = 100, autotune: bool = False, validate_symmetry: bool = False, stream=None):
+        import numpy as np
+        torch = _torch()
+        _require_cuda(row_ptr, torch.int64, "row_ptr")
+        _require_cuda(col, torch.int32, "col")
+        if w is not None:
+            _require_cuda(w, torch.float32, "w")
+        self._host = {
+            "voff": np.ascontiguousarray(vertex_offset, dtype=np.int64),
+            "k": np.ascontiguousarray(k, dtype=np.int32),
+            "seed": np.ascontiguousarray(seed, dtype=np.uint64),
+            "l": None if l is None else np.ascontiguousarray(l, dtype=np.int32),
+            "t": None if t is None else np.ascontiguousarray(t, dtype=np.int32),
+        }
+        self.num_graphs = len(self._host["k"])
+        self.row_ptr, self.col, self.w = row_ptr, col, w
+        nv = int(self._host["voff"][-1])
+        self.labels = torch.empty(nv, dtype=torch.int32, device=row_ptr.device)
+        d = BatchDesc()
+        d.num_graphs = self.num_graphs
+        d.vertex_offset = self._host["voff"].ctypes.data
+        d.row_ptr = row_ptr.data_ptr()
+        d.col_idx = col.data_ptr()
+        d.w = None if w is None else w.data_ptr()
+        d.k = self._host["k"].ctypes.data
+        d.l = None if self._host["l"] is None else self._host["l"].ctypes.data
+        d.t = None if self._host["t"] is None else self._host["t"].ctypes.data
+        d.seed = self._host["seed"].ctypes.data
+        d.labels = self.labels.data_ptr()
+        d.store = int(store)
+        d.max_iter = int(max_iter)
+        d.flags = (BATCH_AUTOTUNE if autotune else 0) | (VALIDATE_SYMMETRY if validate_symmetry else 0)
+        h = C.c_void_p()
+        _check(lib().fsc_batch_create(C.byref(d), _stream(stream), C.byref(h)), "fsc_batch_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(lib().fsc_batch_run(self.handle, _stream(stream)), "fsc_batch_run")
+        return self.labels
+
+    def results(self, stream=None):
+        """(stats list, k-means++ picks per graph, centroids per graph) after a run (synchronises)."""
+        import numpy as np
+        G = self.num_graphs
+        st = (KmeansStats * G)()
+        k = self._host["k"]
+        total_k = int(k.sum())
+        seeds = np.zeros(total_k, dtype=np.int64)
+        ls = self._host["l"]
+        if ls is None or (ls == 0).any():
+            ls = np.array([default_params(int(self._host["voff"][g + 1] - self._host["voff"][g]), int(k[g]))[0]
+                           if ls is None or ls[g] == 0 else int(ls[g]) for g in range(G)], dtype=np.int64)
+        cents = np.zeros(int((k.astype(np.int64) * ls).sum()), dtype=np.float64)
+        _check(lib().fsc_batch_results(self.handle, C.cast(st, C.c_void_p), seeds.ctypes.data, cents.ctypes.data,
+                                       _stream(stream)), "fsc_batch_results")
+        so = co = 0
+        seed_list, cent_list = [], []
+        for g in range(G):
+            seed_list.append(seeds[so:so + k[g]])
+            cent_list.append(cents[co:co + k[g] * ls[g]].reshape(k[g], ls[g]))
+            so += k[g]
+            co += k[g] * ls[g]
+        return [s.as_dict() for s in st], seed_list, cent_list
+
+    def embedding(self, g: int, n: int, l: int, stream=None):
+        """Graph g's float32 embedding (n x pad_l(l)) from the last run (device tensor)."""
+        torch = _torch()
+        out = torch.empty((n, pad_l(l)), dtype=torch.float32, device=self.row_ptr.device)
+        _check(lib().fsc_batch_embedding(self.handle, int(g), _ptr(out), _stream(stream)), "fsc_batch_embedding")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().fsc_batch_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,5 +1,10 @@
 // Algorithm 2 up to k-means: Gaussian start block, t power iterations, D^-1/2 scaling.
+#include <math.h>
 #include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "spmm.cuh"
 
@@ -75,14 +80,86 @@ cudaError_t launch_init(int LP, int n, int l, unsigned long long seed, const flo
     return cudaGetLastError();
 }
 
-// Lanes per row chosen from the average degree (overridable).
-int choose_threads_per_row(const fsc_graph* g, int requested) {
+// ---- lanes per row: explicit request > autotuned table > degree heuristic ------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;   // (LP, store, weighted, degree bucket) -> lanes
+int degree_bucket(double avg) { return (int)floor(2.0 * log2(avg < 1.0 ? 1.0 : avg)); }   // half octaves
+}  // namespace
+
+int tuned_threads_per_row(double avg_degree, int LP, int store, bool weighted) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(LP, store, weighted ? 1 : 0, degree_bucket(avg_degree)));
+    return it == g_tune.end() ? 0 : it->second;
+}
+
+int choose_threads_per_row(const fsc_graph* g, int requested, int LP, int store) {
     if (requested == 4 || requested == 8 || requested == 16 || requested == 32) return requested;
     const double avg = g->n > 0 ? (double)g->nnz / (double)g->n : 0.0;
+    const int tuned = tuned_threads_per_row(avg, LP, store, g->w != nullptr);
+    if (tuned) return tuned;
     if (avg <= 40.0) return 4;      // measured fastest at average degree ~22 (random 16-byte row gathers)
     if (avg <= 96.0) return 8;
     if (avg <= 256.0) return 16;
     return 32;
+}
+
+int choose_threads_per_row(const fsc_graph* g, int requested) { return choose_threads_per_row(g, requested, 4, 0); }
+
+// Times one power step for each lane count on scratch iterates and records the fastest for the
+// graph's (row width, storage type, weighting, degree bucket).
+fsc_status autotune_graph(fsc_graph* g, int l, fsc_dtype store, int* best, float* best_us, cudaStream_t s) {
+    const int LP = pad_l(l);
+    const size_t es = store == FSC_F32 ? 4 : 2;
+    const size_t bytes = (size_t)g->n * LP * es;
+    void* buf = nullptr;
+    FSC_CUDA(cudaMalloc(&buf, 2 * bytes + 256));
+    char* zin = static_cast<char*>(buf);
+    char* zout = zin + ((bytes + 255) & ~(size_t)255);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemsetAsync(zin, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int bestG = 0;
+    float bestT = 1e30f;
+    const int cands[4] = {4, 8, 16, 32};
+    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
+        StepArgs a{};
+        a.n = (int)g->n;
+        a.rp = g->row_ptr;
+        a.col = g->col;
+        a.w = g->w;
+        a.invdeg = g->invdeg;
+        a.zin = zin;
+        a.zout = zout;
+        a.col_off = g->col_off;
+        auto launch = [&]() {
+            return store == FSC_F32 ? launch_step_f32(LP, cands[ci], g->w != nullptr, a, s)
+                                    : launch_step_bf16(LP, cands[ci], g->w != nullptr, a, s);
+        };
+        if ((e = launch()) != cudaSuccess) break;
+        if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch();
+        if (e != cudaSuccess) break;
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+        if (ms < bestT) { bestT = ms; bestG = cands[ci]; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_status(e);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        const double avg = g->n > 0 ? (double)g->nnz / (double)g->n : 0.0;
+        g_tune[std::make_tuple(LP, (int)store, g->w ? 1 : 0, degree_bucket(avg))] = bestG;
+    }
+    if (best) *best = bestG;
+    if (best_us) *best_us = bestT * 1000.f / 5.f;
+    return FSC_OK;
 }
 
 fsc_status ensure_workspace(fsc_graph* g, size_t bytes) {
@@ -116,7 +193,7 @@ extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed
     const uint32_t flags = opts ? opts->flags : 0u;
     if (flags & ~FSC_EMBED_RESCALE) return FSC_ERR_INVALID_ARG;
     const bool rescale = (flags & FSC_EMBED_RESCALE) != 0;
-    const int G = choose_threads_per_row(g, opts ? opts->threads_per_row : 0);
+    const int G = choose_threads_per_row(g, opts ? opts->threads_per_row : 0, LP, (int)store);
     cudaStream_t s = as_stream(stream);
     const int n = (int)g->n;
     if (t == 0) {
@@ -138,6 +215,7 @@ extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed
     a.w = g->w;
     a.invdeg = g->invdeg;
     a.expo = expo;
+    a.col_off = g->col_off;
     const bool weighted = g->w != nullptr;
 
     if (store == FSC_F32) {
@@ -194,9 +272,16 @@ extern "C" fsc_status fsc_power_step(const fsc_graph* g, int l, fsc_dtype store,
     a.invdeg = g->invdeg;
     a.zin = z_in;
     a.zout = z_out;
-    const int G = choose_threads_per_row(g, threads_per_row);
+    a.col_off = g->col_off;
+    const int G = choose_threads_per_row(g, threads_per_row, LP, (int)store);
     cudaStream_t s = as_stream(stream);
     if (store == FSC_F32) FSC_CUDA(launch_step_f32(LP, G, g->w != nullptr, a, s));
     else FSC_CUDA(launch_step_bf16(LP, G, g->w != nullptr, a, s));
     return FSC_OK;
+}
+
+extern "C" fsc_status fsc_autotune(const fsc_graph* g, int l, fsc_dtype store, int* best_threads_per_row,
+                                   float* best_us, void* stream) {
+    if (!g || l < 1 || l > 8 || (store != FSC_F32 && store != FSC_BF16)) return FSC_ERR_INVALID_ARG;
+    return autotune_graph(const_cast<fsc_graph*>(g), l, store, best_threads_per_row, best_us, as_stream(stream));
 }

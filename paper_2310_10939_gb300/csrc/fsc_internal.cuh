@@ -216,4 +216,5 @@ struct fsc_graph {
     size_t ws_bytes;
     unsigned* colmax;   // 3 x 8 unsigned
     int* expo;          // 8 ints
+    long long col_off;  // subtracted from column ids (0, or the first vertex of a graph inside a batch)
 };

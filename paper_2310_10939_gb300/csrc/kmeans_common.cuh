@@ -1,0 +1,170 @@
+// Helpers shared by the k-means kernels: fixed-point scales and conversions, block
+// reductions and scans, point loads, and the per-thread run accumulators of Lloyd.
+// The fixed-point scheme is described in kmeans.cu.
+#pragma once
+
+#include <limits.h>
+
+#include "fsc_internal.cuh"
+
+namespace fsc {
+
+constexpr int KM_THREADS = 512;
+constexpr int KM_WARPS = KM_THREADS / 32;
+constexpr int KM_MAX_BLOCKS = 1024;
+constexpr int KM_PPT = 4;                          // consecutive points per thread per tile
+constexpr int KM_TILE = KM_THREADS * KM_PPT;       // points per tile (chunks are multiples of it)
+
+struct KmDevStats {
+    int iterations;
+    int changed;
+    int empty_events;
+    int status;
+    double inertia;
+    double potential;
+};
+
+// ---- fixed-point helpers ---------------------------------------------------------------
+__device__ __forceinline__ long long fixq(float x, int S) {
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0 || e == 0xff) return 0;                     // zero / subnormal (below resolution)
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);   // |x| = m * 2^(e - 150)
+    const int sh = e - 150 + S;
+    long long v;
+    if (sh >= 0) v = sh < 39 ? (m << sh) : (m << 38);      // sh < 39 whenever |x| < 2^(62-S)
+    else v = sh > -25 ? (m >> -sh) : 0;
+    return (b >> 31) ? -v : v;
+}
+__device__ __forceinline__ double pow2d(int e) {          // 2^e as a double, e in [-1022, 1023]
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+__device__ __forceinline__ int ceil_log2(long long v) {    // smallest c with 2^c >= v (v >= 1)
+    int c = 0;
+    while ((1LL << c) < v) ++c;
+    return c;
+}
+struct Scales {
+    int Sx, Sd;
+};
+__device__ __forceinline__ Scales scales_for(float A, long long n, int l) {
+    const int N = ceil_log2(n < 2 ? 2 : n);
+    const int Ex = A > 0.f ? exponent_of(A) + 1 : 0;
+    const int Ed = 2 * Ex + ceil_log2(l) + 3;
+    Scales s;
+    s.Sx = 62 - Ex - N;
+    s.Sd = 62 - Ed - N;
+    return s;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* s_red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum_ll(v);
+    __syncthreads();
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    long long t = lane < KM_WARPS ? s_red[lane] : 0;
+    return warp_sum_ll(t);
+}
+__device__ __forceinline__ int block_sum_i(int v, int* s_red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum_i(v);
+    __syncthreads();
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    int t = lane < KM_WARPS ? s_red[lane] : 0;
+    return warp_sum_i(t);
+}
+// inclusive block scan of one int64 per thread
+__device__ __forceinline__ long long block_scan_ll(long long v, long long* s_red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += u;
+    }
+    __syncthreads();
+    if (lane == 31) s_red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        long long t = lane < KM_WARPS ? s_red[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += u;
+        }
+        if (lane < KM_WARPS) s_red[lane] = t;
+    }
+    __syncthreads();
+    if (wid > 0) v += s_red[wid - 1];
+    return v;
+}
+
+template <int LP>
+__device__ __forceinline__ void load_point(const float* __restrict__ X, long long i, int l, float (&x)[LP]) {
+    load_row<LP, float>(X + (size_t)i * LP, x);
+#pragma unroll
+    for (int c = 0; c < LP; ++c)
+        if (c >= l) x[c] = 0.f;
+}
+
+__device__ __forceinline__ int lowest_unchosen(const int* chosen, int r) {
+    int cand = 0;
+    for (;; ++cand) {
+        bool taken = false;
+        for (int q = 0; q < r; ++q)
+            if (chosen[q] == cand) { taken = true; break; }
+        if (!taken) return cand;
+    }
+}
+
+// Per-thread accumulation: two register slots (cluster id, exact coordinate sums, count) absorb
+// runs of one label and alternation between two labels; a third label evicts the older slot
+// into the warp's private shared table (no contention between warps).  At the end of the
+// phase a slot that every lane of the warp holds for the same cluster is reduced in registers.
+template <int LP>
+struct Slot {
+    int j;
+    long long cnt;
+    long long s[LP];
+};
+
+template <int LP>
+__device__ __forceinline__ void slot_flush(const Slot<LP>& sl, unsigned long long* tab) {
+    if (sl.j < 0 || sl.cnt == 0) return;
+    unsigned long long* row = tab + (size_t)sl.j * (LP + 1);
+#pragma unroll
+    for (int c = 0; c < LP; ++c) atomicAdd(row + c, (unsigned long long)sl.s[c]);
+    atomicAdd(row + LP, (unsigned long long)sl.cnt);
+}
+
+template <int LP>
+__device__ __forceinline__ void slot_flush_warp(const Slot<LP>& sl, unsigned long long* tab) {
+    const int j0 = __shfl_sync(0xffffffffu, sl.j, 0);
+    if (__all_sync(0xffffffffu, sl.j == j0)) {
+        if (j0 < 0) return;
+        const int lane = threadIdx.x & 31;
+        unsigned long long* row = tab + (size_t)j0 * (LP + 1);
+#pragma unroll
+        for (int c = 0; c < LP; ++c) {
+            const long long v = warp_sum_ll(sl.s[c]);
+            if (lane == 0) atomicAdd(row + c, (unsigned long long)v);
+        }
+        const long long cn = warp_sum_ll(sl.cnt);
+        if (lane == 0) atomicAdd(row + LP, (unsigned long long)cn);
+        return;
+    }
+    slot_flush<LP>(sl, tab);
+}
+
+}  // namespace fsc

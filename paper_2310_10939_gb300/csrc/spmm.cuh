@@ -27,12 +27,88 @@ __device__ __forceinline__ float pow2i(int e) {
     return __int_as_float((e + 127) << 23);
 }
 
+// Loads of the iterate: through the read-only path when it is not written during the launch
+// (NC = true), else through L2 only (the batch kernel rewrites it between block barriers).
+template <int LP, typename T, bool NC>
+__device__ __forceinline__ void load_z(const T* p, float (&v)[LP]) {
+    if (NC) {
+        load_row<LP, T>(p, v);
+    } else {
+        constexpr int BYTES = LP * (int)sizeof(T);
+        constexpr int CB = BYTES < 16 ? BYTES : 16;
+        using C = typename Chunk<CB>::type;
+        constexpr int NCH = BYTES / CB;
+        C buf[NCH];
+#pragma unroll
+        for (int i = 0; i < NCH; ++i) buf[i] = __ldcg(reinterpret_cast<const C*>(p) + i);
+        const T* e = reinterpret_cast<const T*>(buf);
+#pragma unroll
+        for (int c = 0; c < LP; ++c) v[c] = to_f32(e[c]);
+    }
+}
+
+// One output row of the power step, computed by the G lanes `sub` = 0..G-1 of a group; every
+// lane of the warp must call it (the group reduction uses full-warp shuffles).  `row` indexes
+// rp/invdeg/zout; column ids are shifted by col_off to index zin.  Returns true on the lane
+// that wrote the row (sub == 0), with the row in y.
+template <int LP, typename TI, typename TO, int G, int U, bool W, bool NC>
+__device__ __forceinline__ bool power_row(bool active, long long row, int sub, const int64_t* __restrict__ rp,
+                                          const int32_t* __restrict__ col, const float* __restrict__ w,
+                                          const float* __restrict__ invdeg, const TI* zin, TO* zout,
+                                          long long col_off, const float (&scale)[LP], float (&y)[LP]) {
+    float acc[LP];
+#pragma unroll
+    for (int c = 0; c < LP; ++c) acc[c] = 0.f;
+    if (active) {
+        const int64_t s = rp[row], e = rp[row + 1];
+        for (int64_t p = s + sub; p < e; p += G * U) {
+            long long j[U];
+            float wv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t q = p + (int64_t)u * G;
+                const bool ok = q < e;
+                j[u] = ok ? (long long)__ldg(col + q) - col_off : -1;
+                if (W) wv[u] = ok ? __ldg(w + q) : 0.f;
+            }
+            float v[U][LP];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j[u] >= 0) {
+                    load_z<LP, TI, NC>(zin + (size_t)j[u] * LP, v[u]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) v[u][c] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int c = 0; c < LP; ++c) acc[c] = W ? fmaf(wv[u], v[u][c], acc[c]) : acc[c] + v[u][c];
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int c = 0; c < LP; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    if (active && sub == 0) {
+        float self[LP];
+        load_z<LP, TI, NC>(zin + (size_t)row * LP, self);
+        const float id = invdeg[row];
+#pragma unroll
+        for (int c = 0; c < LP; ++c) y[c] = scale[c] * (0.5f * fmaf(id, acc[c], self[c]));
+        store_row<LP, TO>(zout + (size_t)row * LP, y);
+        return true;
+    }
+    return false;
+}
+
 template <int LP, typename TI, typename TO, int G, int U, bool W>
 __global__ void __launch_bounds__(256)
 k_power_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ w,
              const float* __restrict__ invdeg, const TI* __restrict__ zin, TO* __restrict__ zout,
              const unsigned* __restrict__ cm_in, unsigned* __restrict__ cm_out, unsigned* __restrict__ cm_zero,
-             int* __restrict__ expo, int last) {
+             int* __restrict__ expo, int last, long long col_off) {
     static_assert(32 % G == 0, "G must divide the warp");
     constexpr int RPW = 32 / G;
     __shared__ unsigned s_cm[LP];
@@ -60,50 +136,8 @@ k_power_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ 
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long base = warp * RPW; base < n; base += nwarps * RPW) {
         const long long row = base + grp;
-        const bool active = row < n;
-        float acc[LP];
-#pragma unroll
-        for (int c = 0; c < LP; ++c) acc[c] = 0.f;
-        if (active) {
-            const int64_t s = rp[row], e = rp[row + 1];
-            for (int64_t p = s + sub; p < e; p += G * U) {
-                int j[U];
-                float wv[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t q = p + (int64_t)u * G;
-                    const bool ok = q < e;
-                    j[u] = ok ? __ldg(col + q) : -1;
-                    if (W) wv[u] = ok ? __ldg(w + q) : 0.f;
-                }
-                float v[U][LP];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (j[u] >= 0) {
-                        load_row<LP, TI>(zin + (size_t)j[u] * LP, v[u]);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < LP; ++c) v[u][c] = 0.f;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int c = 0; c < LP; ++c) acc[c] = W ? fmaf(wv[u], v[u][c], acc[c]) : acc[c] + v[u][c];
-            }
-        }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1)
-#pragma unroll
-            for (int c = 0; c < LP; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
         float y[LP];
-        if (active && sub == 0) {
-            float self[LP];
-            load_row<LP, TI>(zin + (size_t)row * LP, self);
-            const float id = invdeg[row];
-#pragma unroll
-            for (int c = 0; c < LP; ++c) y[c] = scale[c] * (0.5f * fmaf(id, acc[c], self[c]));
-            store_row<LP, TO>(zout + (size_t)row * LP, y);
+        if (power_row<LP, TI, TO, G, U, W, true>(row < n, row, sub, rp, col, w, invdeg, zin, zout, col_off, scale, y)) {
 #pragma unroll
             for (int c = 0; c < LP; ++c) cmx[c] = fmaxf(cmx[c], fabsf(y[c]));
         }
@@ -134,6 +168,7 @@ struct StepArgs {
     unsigned* cm_zero;
     int* expo;
     int last;
+    long long col_off;   // subtracted from column ids (graphs that are a slice of a larger CSR)
 };
 
 template <int LP, typename TI, typename TO, int G, int U, bool W>
@@ -151,7 +186,8 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, 256, 0, s>>>(a.n, a.rp, a.col, a.w, a.invdeg, static_cast<const TI*>(a.zin),
-                                         static_cast<TO*>(a.zout), a.cm_in, a.cm_out, a.cm_zero, a.expo, a.last);
+                                         static_cast<TO*>(a.zout), a.cm_in, a.cm_out, a.cm_zero, a.expo, a.last,
+                                         a.col_off);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,9 @@ from .graphs import (
     with_isolated,
     permuted,
     equal_sizes,
+    GraphBatch,
+    union,
+    sbm_batch,
 )
 
 __all__ = [
@@ -33,4 +36,7 @@ __all__ = [
     "with_isolated",
     "permuted",
     "equal_sizes",
+    "GraphBatch",
+    "union",
+    "sbm_batch",
 ]

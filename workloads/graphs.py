@@ -302,3 +302,51 @@ def image_grid(height: int = 321, width: int = 481, nsites: int = 8, noise: floa
     return _weighted_edges(n, lo, hi, w64, region.astype(np.int32), name,
                            {"height": height, "width": width, "nsites": nsites, "noise": noise,
                             "radius": radius, "seed": seed})
+
+
+@dataclass
+class GraphBatch:
+    """Disjoint union of graphs as one CSR with global vertex ids."""
+    vertex_offset: np.ndarray    # int64, G + 1
+    row_ptr: np.ndarray          # int64, total vertices + 1
+    col: np.ndarray              # int32, global ids
+    w: np.ndarray | None
+    labels: np.ndarray           # planted labels (local ids)
+    k: np.ndarray                # int32 planted clusters per graph
+    graphs: list                 # the member Graph objects (kept for per-graph checks), or None
+
+    @property
+    def num_graphs(self) -> int:
+        return int(self.k.size)
+
+    def member(self, g: int) -> Graph:
+        return self.graphs[g]
+
+
+def union(graphs, with_weights: bool = False) -> GraphBatch:
+    """Concatenate graphs into one block-diagonal CSR (global vertex and edge ids)."""
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    voff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(ns, out=voff[1:])
+    nnz = np.array([g.nnz for g in graphs], dtype=np.int64)
+    eoff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(nnz, out=eoff[1:])
+    row_ptr = np.concatenate([g.row_ptr[:-1] + eoff[i] for i, g in enumerate(graphs)] + [eoff[-1:]])
+    col = np.concatenate([g.col.astype(np.int64) + voff[i] for i, g in enumerate(graphs)]).astype(np.int32)
+    w = None
+    if with_weights or any(g.w is not None for g in graphs):
+        w = np.concatenate([g.w if g.w is not None else np.ones(g.nnz, np.float32) for g in graphs])
+    labels = np.concatenate([g.labels for g in graphs]).astype(np.int32)
+    k = np.array([g.k_planted for g in graphs], dtype=np.int32)
+    return GraphBatch(voff, row_ptr.astype(np.int64), col, w, labels, k, list(graphs))
+
+
+def sbm_batch(num_graphs: int, n_range, k_range, deg_in: float, deg_out: float, seed: int,
+              with_weights: bool = False) -> GraphBatch:
+    """Many SBMs: n ~ U[n_range], k ~ U[k_range] per graph (seeded), expected degrees given."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_range[0], n_range[1] + 1, num_graphs)
+    ks = rng.integers(k_range[0], k_range[1] + 1, num_graphs)
+    graphs = [sbm_by_degree(int(n), int(k), deg_in, deg_out, seed=int(seed * 100003 + i)) for i, (n, k) in
+              enumerate(zip(ns, ks))]
+    return union(graphs, with_weights)
