@@ -135,3 +135,35 @@ def test_autotune_then_batch(torch):
         lo, hi = gb.vertex_offset[q], gb.vertex_offset[q + 1]
         assert labels[lo:hi].min() >= 0 and labels[lo:hi].max() < gb.k[q]
     b.close()
+
+
+def test_full_scale_batch_4096_sampled(torch):
+    """The full batch (4096 SBMs, n ~ U[500, 50000], k ~ U[2, 20], degrees 15 / 1.5, bf16 iterates,
+    float32 weights) in one plan; sampled members against per-graph fsc_cluster (exact) and the
+    oracle (embedding within 2e-2; ARI within 0.01 where the oracle separates the graph)."""
+    import paper_2310_10939_gb300 as fsc
+    from _helpers import rel_fro
+    from oracle import spectral
+    gb = W.sbm_batch_gpu(4096, (500, 50_000), (2, 20), 15.0, 1.5, seed=13)
+    seeds = np.arange(gb.num_graphs, dtype=np.uint64) + 1
+    b = fsc.Batch(gb.vertex_offset, gb.row_ptr, gb.col, gb.k, seeds, w=gb.w, store=fsc.BF16)
+    labels = b.run().cpu().numpy()
+    stats, _, _ = b.results()
+    assert all(1 <= s["iterations"] <= 100 for s in stats)
+    rng = np.random.default_rng(0)
+    for i, g in enumerate(rng.choice(gb.num_graphs, 6, replace=False)):
+        m = gb.member(int(g))
+        lo, hi = gb.vertex_offset[g], gb.vertex_offset[g + 1]
+        l, t = fsc.default_params(m.n, int(gb.k[g]))
+        G = fsc.Graph(torch.as_tensor(m.row_ptr, device="cuda"), torch.as_tensor(m.col, device="cuda"),
+                      torch.as_tensor(m.w, device="cuda"))
+        ref, _ = fsc.cluster(G, int(gb.k[g]), l, t, int(seeds[g]), store=fsc.BF16, rescale=True, threads_per_row=4)
+        assert np.array_equal(labels[lo:hi], ref.cpu().numpy()), g
+        if i < 2:
+            emb = b.embedding(int(g), m.n, l).cpu().numpy()
+            assert rel_fro(emb[:, :l], spectral.embed(m, l, t, int(seeds[g]))) <= 2e-2
+            oref = ocluster.fast_spectral_cluster(m, int(gb.k[g]), l, t, int(seeds[g]))
+            a_ref = metrics.ari(oref["labels"], m.labels)
+            if a_ref >= 0.9:
+                assert abs(metrics.ari(labels[lo:hi], m.labels) - a_ref) <= 0.01
+    b.close()

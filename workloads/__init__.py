@@ -21,6 +21,7 @@ from .graphs import (
     GraphBatch,
     union,
     sbm_batch,
+    sbm_batch_gpu,
 )
 
 __all__ = [
@@ -39,4 +40,5 @@ __all__ = [
     "GraphBatch",
     "union",
     "sbm_batch",
+    "sbm_batch_gpu",
 ]

@@ -320,7 +320,16 @@ class GraphBatch:
         return int(self.k.size)
 
     def member(self, g: int) -> Graph:
-        return self.graphs[g]
+        """Graph g alone (local vertex ids), as host numpy arrays."""
+        if self.graphs is not None:
+            return self.graphs[g]
+        lo, hi = int(self.vertex_offset[g]), int(self.vertex_offset[g + 1])
+        rp = _host(self.row_ptr[lo:hi + 1])
+        e0, e1 = int(rp[0]), int(rp[-1])
+        col = (_host(self.col[e0:e1]).astype(np.int64) - lo).astype(np.int32)
+        w = None if self.w is None else _host(self.w[e0:e1])
+        return Graph(hi - lo, (rp - e0).astype(np.int64), col, w, _host(self.labels[lo:hi]).astype(np.int32),
+                     f"member{g}")
 
 
 def union(graphs, with_weights: bool = False) -> GraphBatch:
@@ -350,3 +359,83 @@ def sbm_batch(num_graphs: int, n_range, k_range, deg_in: float, deg_out: float, 
     graphs = [sbm_by_degree(int(n), int(k), deg_in, deg_out, seed=int(seed * 100003 + i)) for i, (n, k) in
               enumerate(zip(ns, ks))]
     return union(graphs, with_weights)
+
+
+def _host(a):
+    return a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
+
+
+def sbm_batch_gpu(num_graphs: int, n_range, k_range, deg_in: float, deg_out: float, seed: int,
+                  with_weights: bool = True, device: str = "cuda") -> GraphBatch:
+    """Large batches of SBM-like graphs generated on the GPU with torch (input plumbing only).
+
+    Per graph: n ~ U[n_range], k ~ U[k_range] (numpy, seeded) and k near-equal blocks.  The
+    number of within-block edges is Poisson(deg_in * n / 2), of cross-block edges
+    Poisson(deg_out * n / 2); each edge has a uniform first endpoint and a uniform second
+    endpoint in (respectively outside) its block; repeated pairs are dropped.  This is the SBM
+    of the same expected degrees up to the dropped repeats (a vanishing fraction at these
+    densities).  Row pointers, columns (global ids) and weights (all 1.0 if ``with_weights``)
+    stay on the device as torch tensors.
+    """
+    import torch
+    rng = np.random.default_rng(seed)
+    G = num_graphs
+    ns = rng.integers(n_range[0], n_range[1] + 1, G).astype(np.int64)
+    ks = rng.integers(k_range[0], k_range[1] + 1, G).astype(np.int64)
+    m_in = rng.poisson(deg_in * ns / 2.0).astype(np.int64)
+    m_out = rng.poisson(deg_out * ns / 2.0).astype(np.int64)
+    voff = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum(ns, out=voff[1:])
+    NV = int(voff[-1])
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    dev = torch.device(device)
+    t_ns = torch.as_tensor(ns, device=dev)
+    t_ks = torch.as_tensor(ks, device=dev)
+    t_voff = torch.as_tensor(voff, device=dev)
+
+    def blocks(g, u):                       # block id, start and size of local vertex u of graph g
+        n, k = t_ns[g], t_ks[g]
+        base, extra = n // k, n % k
+        big = extra * (base + 1)
+        b = torch.where(u < big, u // (base + 1), extra + (u - big) // torch.clamp(base, min=1))
+        start = torch.where(b < extra, b * (base + 1), big + (b - extra) * base)
+        size = base + (b < extra).to(torch.int64)
+        return b, start, size
+
+    keys = []
+    for counts, inside in ((m_in, True), (m_out, False)):
+        g = torch.repeat_interleave(torch.arange(G, device=dev), torch.as_tensor(counts, device=dev))
+        n = t_ns[g]
+        u = torch.floor(torch.rand(g.numel(), generator=gen, device=dev, dtype=torch.float64) * n).to(torch.int64)
+        _, start, size = blocks(g, u)
+        r = torch.rand(g.numel(), generator=gen, device=dev, dtype=torch.float64)
+        if inside:
+            v = start + torch.floor(r * (size - 1)).to(torch.int64)
+            v = v + (v >= u).to(torch.int64)
+        else:
+            v = torch.floor(r * (n - size)).to(torch.int64)
+            v = v + (v >= start).to(torch.int64) * size
+        off = t_voff[g]
+        a, c = u + off, v + off
+        keys.append(torch.minimum(a, c) * NV + torch.maximum(a, c))
+        del g, n, u, start, size, r, v, off, a, c
+    key = torch.unique(torch.cat(keys))
+    del keys
+    lo, hi = key // NV, key % NV
+    del key
+    rows = torch.cat([lo, hi])
+    cols = torch.cat([hi, lo])
+    del lo, hi
+    order = torch.argsort(rows * NV + cols)
+    rows, cols = rows[order], cols[order].to(torch.int32)
+    del order
+    counts = torch.bincount(rows, minlength=NV)
+    del rows
+    row_ptr = torch.zeros(NV + 1, dtype=torch.int64, device=dev)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    w = torch.ones(cols.numel(), dtype=torch.float32, device=dev) if with_weights else None
+    gv = torch.repeat_interleave(torch.arange(G, device=dev), t_ns)
+    local = torch.arange(NV, device=dev) - t_voff[gv]
+    labels, _, _ = blocks(gv, local)
+    return GraphBatch(voff, row_ptr, cols, w, labels.to(torch.int32), ks.astype(np.int32), None)
