@@ -69,6 +69,8 @@ typedef struct fsc_graph_info_t {
     const double* deg;          /* device, n: d(v) = sum_{u != v} w(u, v), float64 */
     const float* dinv;          /* device, n: d(v)^-1/2 rounded to float (0 if isolated) */
     const float* invdeg;        /* device, n: 1/d(v) rounded to float (0 if isolated) */
+    double deg_sumsq;           /* sum of d(v)^2 */
+    double deg_max;             /* max d(v) */
 } fsc_graph_info_t;
 
 typedef struct fsc_embed_opts {
@@ -256,6 +258,43 @@ fsc_status fsc_batch_results(fsc_batch* batch, fsc_kmeans_stats* stats, int64_t*
  * n_g * fsc_pad_l(l_g) floats).  Asynchronous on `stream`. */
 fsc_status fsc_batch_embedding(fsc_batch* batch, int graph, float* out, void* stream);
 fsc_status fsc_batch_destroy(fsc_batch* batch);
+
+/*
+ * Learned polynomial filter (no counterpart in the paper: an extension of Algorithm 2).
+ *
+ * p(M) X = sum_{j=0..8} c_j T_j(A_hat) X, A_hat = 2M - I = D^-1/2 A D^-1/2, replaces M^t X
+ * (Chebyshev three-term recurrence: 8 sparse products instead of t).  The coefficients come
+ * from an MLP 16 -> 64 -> 64 -> 9 (GELU, float32, 5833 parameters: W1 64x16, b1, W2 64x64, b2,
+ * W3 9x64, b3, row-major, in that order) fed 16 features of the graph and its start block:
+ * log n, log mean degree, degree std / mean, log(max degree / mean), log k, log(n/k), l/8,
+ * isolated fraction, and the Chebyshev moments mu_j = sum_c x_c^T T_j(A_hat) x_c / sum_c
+ * x_c^T x_c, j = 1..8 (from inner products fused into the recurrence).  It is trained to
+ * minimise ||p(M) X - P X||^2 / ||P X||^2, P the top-k eigenprojector of M (the quantity
+ * Lemma 3.1 bounds for M^t).
+ *
+ * fsc_filter_embed: the filtered embedding D^-1/2 p(M) X (emb: n x fsc_pad_l(l) floats), with
+ *   X the same start block as fsc_embed(seed).  params: device MLP parameters, or NULL when
+ *   coeffs_override (device, 9 floats) gives the coefficients.  feats_out (16) and coeffs_out
+ *   (9) are optional device outputs.  opts: threads_per_row and the events bracketing the 8
+ *   sparse steps (flags ignored).  Asynchronous.
+ * fsc_cluster_filtered: fsc_filter_embed then fsc_kmeans; synchronous.
+ * fsc_mlp_forward: coefficients (batch x 9) of features (batch x 16), device arrays.
+ * fsc_mlp_train_step: adds the gradient of the mean loss c^T Gn c - 2 bn^T c + 1 over the
+ *   batch (feats batch x 16, Gn batch x 81, bn batch x 9, device float32) to grad (5833);
+ *   with apply_update != 0 then takes an Adam step (beta 0.9 / 0.999, eps 1e-8, step >= 1
+ *   for bias correction, weight decay added to the gradient) and zeroes grad.  loss_out
+ *   (device scalar) receives the mean loss, may be NULL.  Asynchronous.
+ */
+fsc_status fsc_filter_embed(const fsc_graph* g, int l, int k, uint64_t seed, fsc_dtype store, const float* params,
+                            const float* coeffs_override, float* emb, float* feats_out, float* coeffs_out,
+                            const fsc_embed_opts* opts, void* stream);
+fsc_status fsc_cluster_filtered(const fsc_graph* g, int k, int l, uint64_t seed, fsc_dtype store, const float* params,
+                                int max_iter, int32_t* labels, fsc_kmeans_stats* stats, const fsc_embed_opts* opts,
+                                void* stream);
+fsc_status fsc_mlp_forward(const float* params, const float* feats, int batch, float* coeffs, void* stream);
+fsc_status fsc_mlp_train_step(float* params, float* grad, float* adam_m, float* adam_v, int step, float lr,
+                              float weight_decay, const float* feats, const float* Gn, const float* bn, int batch,
+                              float* loss_out, int apply_update, void* stream);
 
 /*
  * fsc_default_params - l and t for n vertices and k clusters (host, no device work).

@@ -22,6 +22,7 @@ __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
     "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
     "F32", "BF16", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
+    "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
@@ -67,7 +68,8 @@ class BatchDesc(C.Structure):
 
 class GraphInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("n_isolated", C.c_int64), ("weighted", C.c_int32),
-                ("volume", C.c_double), ("deg", C.c_void_p), ("dinv", C.c_void_p), ("invdeg", C.c_void_p)]
+                ("volume", C.c_double), ("deg", C.c_void_p), ("dinv", C.c_void_p), ("invdeg", C.c_void_p),
+                ("deg_sumsq", C.c_double), ("deg_max", C.c_double)]
 
 
 _lib = None
@@ -101,6 +103,13 @@ def lib() -> C.CDLL:
         L.fsc_batch_embedding.argtypes = [vp, i32, vp, vp]
         for name in ("fsc_autotune", "fsc_batch_create", "fsc_batch_run", "fsc_batch_results", "fsc_batch_destroy",
                      "fsc_batch_embedding"):
+            getattr(L, name).restype = i32
+        L.fsc_filter_embed.argtypes = [vp, i32, i32, u64, i32, vp, vp, vp, vp, vp, C.POINTER(EmbedOpts), vp]
+        L.fsc_cluster_filtered.argtypes = [vp, i32, i32, u64, i32, vp, i32, vp, C.POINTER(KmeansStats),
+                                           C.POINTER(EmbedOpts), vp]
+        L.fsc_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+        L.fsc_mlp_train_step.argtypes = [vp, vp, vp, vp, i32, C.c_float, C.c_float, vp, vp, vp, i32, vp, i32, vp]
+        for name in ("fsc_filter_embed", "fsc_cluster_filtered", "fsc_mlp_forward", "fsc_mlp_train_step"):
             getattr(L, name).restype = i32
         L.fsc_default_params.argtypes = [i64, i32, i32, C.POINTER(i32), C.POINTER(i32)]
         L.fsc_sync_status.argtypes = [vp]
@@ -400,3 +409,63 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+NPARAM = 5833
+FILTER_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "filter", "mlp_weights.npz")
+
+
+def load_filter_params(path: str | None = None, device="cuda"):
+    """The trained filter MLP parameters (5833 float32) as a device tensor."""
+    import numpy as np
+    torch = _torch()
+    p = np.load(path or FILTER_WEIGHTS)["params"].astype(np.float32)
+    assert p.size == NPARAM
+    return torch.as_tensor(p, device=device)
+
+
+def filter_embed(g: Graph, l: int, k: int, seed: int, params=None, coeffs=None, store: int = F32, out=None,
+                 threads_per_row: int = 0, events=None, stream=None):
+    """fsc_filter_embed: returns (embedding n x pad_l(l), features (16), coefficients (9)) device tensors."""
+    torch = _torch()
+    dev = g.row_ptr.device
+    if out is None:
+        out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=dev)
+    feats = torch.empty(16, dtype=torch.float32, device=dev)
+    cf = torch.empty(9, dtype=torch.float32, device=dev)
+    o = _opts(False, threads_per_row, events)
+    _check(lib().fsc_filter_embed(g.handle, int(l), int(k), int(seed) & (2**64 - 1), int(store), _ptr(params),
+                                  _ptr(coeffs), _ptr(out), _ptr(feats), _ptr(cf), C.byref(o), _stream(stream)),
+           "fsc_filter_embed")
+    return out, feats, cf
+
+
+def cluster_filtered(g: Graph, k: int, l: int, seed: int, params, store: int = BF16, max_iter: int = 100,
+                     labels=None, threads_per_row: int = 0, events=None, stream=None):
+    """fsc_cluster_filtered: Algorithm 2 with the learned filter in place of M^t.  Returns (labels, stats)."""
+    torch = _torch()
+    if labels is None:
+        labels = torch.empty(g.n, dtype=torch.int32, device=g.row_ptr.device)
+    st = KmeansStats()
+    o = _opts(False, threads_per_row, events)
+    _check(lib().fsc_cluster_filtered(g.handle, int(k), int(l), int(seed) & (2**64 - 1), int(store), _ptr(params),
+                                      int(max_iter), _ptr(labels), C.byref(st), C.byref(o), _stream(stream)),
+           "fsc_cluster_filtered")
+    return labels, st.as_dict()
+
+
+def mlp_forward(params, feats, stream=None):
+    """fsc_mlp_forward: coefficients (B x 9) of features (B x 16)."""
+    torch = _torch()
+    out = torch.empty((feats.shape[0], 9), dtype=torch.float32, device=feats.device)
+    _check(lib().fsc_mlp_forward(_ptr(params), _ptr(feats), int(feats.shape[0]), _ptr(out), _stream(stream)),
+           "fsc_mlp_forward")
+    return out
+
+
+def mlp_train_step(params, grad, m, v, step, lr, feats, Gn, bn, weight_decay=0.0, loss=None, apply_update=True,
+                   stream=None):
+    """fsc_mlp_train_step (see the header): one gradient accumulation and optional Adam step."""
+    _check(lib().fsc_mlp_train_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
+                                    float(weight_decay), _ptr(feats), _ptr(Gn), _ptr(bn), int(feats.shape[0]),
+                                    _ptr(loss), 1 if apply_update else 0, _stream(stream)), "fsc_mlp_train_step")

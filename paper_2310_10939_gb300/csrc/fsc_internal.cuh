@@ -211,6 +211,8 @@ struct fsc_graph {
     float* invdeg;
     int64_t n_isolated;
     double volume;
+    double deg_sumsq;   // sum of d(v)^2
+    double deg_max;     // max d(v)
     // embedding workspace (grown on demand)
     void* ws;
     size_t ws_bytes;

@@ -75,13 +75,14 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
                                                 int check_sorted, double* __restrict__ deg,
                                                 float* __restrict__ dinv, float* __restrict__ invdeg,
                                                 unsigned long long* __restrict__ n_iso, double* __restrict__ vol,
-                                                int* __restrict__ status) {
+                                                int* __restrict__ status, double* __restrict__ sumsq,
+                                                unsigned long long* __restrict__ dmax_bits) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (tid == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
     int bad = 0;
     unsigned iso = 0;
-    double vsum = 0.0;
+    double vsum = 0.0, vsq = 0.0, vmax = 0.0;
     long long cnt_total = 0;
     for (int64_t i = tid; i < n; i += stride) {
         const int64_t s = rp[i], e = rp[i + 1];
@@ -113,6 +114,8 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
             vsum += d;
         }
         deg[i] = d;
+        vsq += d * d;
+        vmax = fmax(vmax, d);
         if (d > 0.0) {
             const float df = (float)d;
             dinv[i] = 1.0f / sqrtf(df);
@@ -131,7 +134,13 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
     if (w) {
         for (int off = 16; off > 0; off >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
     }
+    for (int off = 16; off > 0; off >>= 1) {
+        vsq += __shfl_xor_sync(0xffffffffu, vsq, off);
+        vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+    }
     if ((threadIdx.x & 31) == 0) {
+        if (vsq != 0.0) atomicAdd(sumsq, vsq);
+        if (vmax > 0.0) atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(vmax));
         if (bad) atomicOr(status, bad);
         if (iso) atomicAdd(n_iso, (unsigned long long)iso);
         const double v = w ? vsum : (double)cnt_total;
@@ -207,8 +216,10 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
         const int64_t want = (n + threads - 1) / threads;
         const int blocks = (int)(want < (int64_t)device_props().num_sms * 64 ? want : (int64_t)device_props().num_sms * 64);
         const int check_sorted = (flags & FSC_VALIDATE_SYMMETRY) ? 1 : 0;
+        double* sumsq = reinterpret_cast<double*>(base + n8 + 32);
+        unsigned long long* dmaxb = reinterpret_cast<unsigned long long*>(base + n8 + 40);
         k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,
-                                            g->invdeg, niso, vol, status);
+                                            g->invdeg, niso, vol, status, sumsq, dmaxb);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         int bits = 0;
         if ((e = cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
@@ -224,9 +235,15 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
         double v = 0;
         if ((e = cudaMemcpyAsync(&iso, niso, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(&v, vol, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        double sq = 0.0;
+        unsigned long long mx = 0;
+        if ((e = cudaMemcpyAsync(&sq, base + n8 + 32, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(&mx, base + n8 + 40, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
         g->n_isolated = (int64_t)iso;
         g->volume = v;
+        g->deg_sumsq = sq;
+        memcpy(&g->deg_max, &mx, 8);
     } while (0);
     if (e != cudaSuccess) rc = cuda_status(e);
     if (rc != FSC_OK) {
@@ -258,6 +275,8 @@ extern "C" fsc_status fsc_graph_info(const fsc_graph* g, fsc_graph_info_t* info)
     info->n_isolated = g->n_isolated;
     info->weighted = g->w != nullptr;
     info->volume = g->volume;
+    info->deg_sumsq = g->deg_sumsq;
+    info->deg_max = g->deg_max;
     info->deg = g->deg;
     info->dinv = g->dinv;
     info->invdeg = g->invdeg;

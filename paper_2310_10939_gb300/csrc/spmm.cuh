@@ -47,16 +47,13 @@ __device__ __forceinline__ void load_z(const T* p, float (&v)[LP]) {
     }
 }
 
-// One output row of the power step, computed by the G lanes `sub` = 0..G-1 of a group; every
-// lane of the warp must call it (the group reduction uses full-warp shuffles).  `row` indexes
-// rp/invdeg/zout; column ids are shifted by col_off to index zin.  Returns true on the lane
-// that wrote the row (sub == 0), with the row in y.
-template <int LP, typename TI, typename TO, int G, int U, bool W, bool NC>
-__device__ __forceinline__ bool power_row(bool active, long long row, int sub, const int64_t* __restrict__ rp,
-                                          const int32_t* __restrict__ col, const float* __restrict__ w,
-                                          const float* __restrict__ invdeg, const TI* zin, TO* zout,
-                                          long long col_off, const float (&scale)[LP], float (&y)[LP]) {
-    float acc[LP];
+// sum_j w_ij z_j of one row, computed by the G lanes `sub` = 0..G-1 of a group and reduced with
+// full-warp shuffles (every lane of the warp must call it).  `row` indexes rp; column ids are
+// shifted by col_off to index zin.  After the call every lane of the group holds the sum.
+template <int LP, typename TI, int G, int U, bool W, bool NC>
+__device__ __forceinline__ void row_gather(bool active, long long row, int sub, const int64_t* __restrict__ rp,
+                                           const int32_t* __restrict__ col, const float* __restrict__ w,
+                                           const TI* zin, long long col_off, float (&acc)[LP]) {
 #pragma unroll
     for (int c = 0; c < LP; ++c) acc[c] = 0.f;
     if (active) {
@@ -91,6 +88,17 @@ __device__ __forceinline__ bool power_row(bool active, long long row, int sub, c
     for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
         for (int c = 0; c < LP; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+}
+
+// One output row of the power step, y = scale * (z_in[row] + (1/d) sum_j w_ij z_in[j]) / 2,
+// written by lane sub == 0 of the group (which returns true, with the row in y).
+template <int LP, typename TI, typename TO, int G, int U, bool W, bool NC>
+__device__ __forceinline__ bool power_row(bool active, long long row, int sub, const int64_t* __restrict__ rp,
+                                          const int32_t* __restrict__ col, const float* __restrict__ w,
+                                          const float* __restrict__ invdeg, const TI* zin, TO* zout,
+                                          long long col_off, const float (&scale)[LP], float (&y)[LP]) {
+    float acc[LP];
+    row_gather<LP, TI, G, U, W, NC>(active, row, sub, rp, col, w, zin, col_off, acc);
     if (active && sub == 0) {
         float self[LP];
         load_z<LP, TI, NC>(zin + (size_t)row * LP, self);

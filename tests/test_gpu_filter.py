@@ -1,0 +1,175 @@
+"""Learned polynomial filter on the GPU against the float64 oracle.
+
+The MLP forward pass and its gradients against the oracle's hand-written float64 versions;
+the Chebyshev basis T_j(A_hat) X against the oracle's recurrence (unit coefficient vectors);
+the Chebyshev expansion of gamma^8 against 8 power iterations; the 16 features against the
+oracle's; and what the trained network gains over the plain method on held-out graphs.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from _helpers import rel_fro, require_cuda
+from oracle import cluster as ocluster
+from oracle import filter as fl
+from oracle import metrics, spectral
+from oracle.rng import gaussian_block
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+def _theta(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0, scale, fl.NPARAM)
+
+
+def test_mlp_forward_matches_oracle(torch):
+    import paper_2310_10939_gb300 as fsc
+    theta = _theta(1)
+    F = np.random.default_rng(2).normal(size=(37, 16))
+    c = fsc.mlp_forward(torch.as_tensor(theta, dtype=torch.float32, device="cuda"),
+                        torch.as_tensor(F, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ref, _ = fl.mlp_forward(theta.astype(np.float32).astype(np.float64), F.astype(np.float32).astype(np.float64))
+    assert np.allclose(c, ref, rtol=1e-4, atol=1e-5 * np.abs(ref).max())
+
+
+def test_mlp_gradient_matches_oracle(torch):
+    import paper_2310_10939_gb300 as fsc
+    rng = np.random.default_rng(3)
+    theta = _theta(4).astype(np.float32).astype(np.float64)
+    B = 23
+    F = rng.normal(size=(B, 16)).astype(np.float32).astype(np.float64)
+    A = rng.normal(size=(B, 9, 9))
+    G = (np.einsum("bij,bkj->bik", A, A) / 9 + np.eye(9)).astype(np.float32).astype(np.float64)
+    b = rng.normal(size=(B, 9)).astype(np.float32).astype(np.float64)
+    loss_ref, grad_ref = fl.batch_loss_and_grad(theta, F, G, b, np.ones(B))
+    t = lambda a: torch.as_tensor(a, dtype=torch.float32, device="cuda").contiguous()
+    P, grad = t(theta), torch.zeros(fl.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    fsc.mlp_train_step(P, grad, None, None, 1, 0.0, t(F), t(G.reshape(B, 81)), t(b), loss=loss, apply_update=False)
+    g = grad.cpu().numpy()
+    assert np.isclose(float(loss.item()), loss_ref, rtol=1e-4)
+    assert np.abs(g - grad_ref).max() <= 1e-4 * np.abs(grad_ref).max()
+
+
+def test_adam_step_decreases_the_loss(torch):
+    import paper_2310_10939_gb300 as fsc
+    rng = np.random.default_rng(5)
+    B = 64
+    F = rng.normal(size=(B, 16))
+    A = rng.normal(size=(B, 9, 9))
+    G = np.einsum("bij,bkj->bik", A, A) / 9 + np.eye(9)
+    b = rng.normal(size=(B, 9))
+    t = lambda a: torch.as_tensor(a, dtype=torch.float32, device="cuda").contiguous()
+    P = t(_theta(6, 0.1))
+    grad, m, v = (torch.zeros_like(P) for _ in range(3))
+    losses = []
+    for step in range(1, 201):
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        fsc.mlp_train_step(P, grad, m, v, step, 1e-2, t(F), t(G.reshape(B, 81)), t(b), loss=loss)
+        losses.append(float(loss.item()))
+    assert losses[-1] < 0.5 * losses[0]
+    theta = P.cpu().numpy().astype(np.float64)
+    assert np.isclose(fl.batch_loss_and_grad(theta, F, G, b, np.ones(B))[0], losses[-1], rtol=0.05)
+
+
+@pytest.mark.parametrize("store_name,tol", [("f32", 1e-5), ("bf16", 2e-2)])
+@pytest.mark.parametrize("name", ["sbm", "knn"])
+def test_chebyshev_basis_matches_oracle(torch, store_name, tol, name):
+    import paper_2310_10939_gb300 as fsc
+    store = fsc.F32 if store_name == "f32" else fsc.BF16
+    g = W.sbm([300] * 4, 0.06, 0.004, 7) if name == "sbm" else W.knn_mixture(2000, 8, 5, 10, seed=8)
+    G = fsc.Graph.from_workload(g)
+    l, seed = 3, 21
+    K = fl.cheb_basis(g, gaussian_block(g.n, l, seed))
+    dm = spectral.inv_sqrt_degrees(spectral.degrees(g))[:, None]
+    for j in range(9):
+        e = torch.zeros(9, dtype=torch.float32, device="cuda")
+        e[j] = 1.0
+        emb, _, cf = fsc.filter_embed(G, l, 4, seed, coeffs=e, store=store)
+        assert torch.equal(cf, e)
+        assert rel_fro(emb.cpu().numpy()[:, :l], dm * K[j]) <= tol, j
+
+
+def test_gamma8_coefficients_reproduce_eight_power_iterations(torch):
+    import paper_2310_10939_gb300 as fsc
+    g = W.image_grid(40, 50, 5, seed=2)
+    G = fsc.Graph.from_workload(g)
+    c8 = torch.as_tensor(fl.power_coefficients(8), dtype=torch.float32, device="cuda")
+    emb, _, _ = fsc.filter_embed(G, 4, 5, 9, coeffs=c8)
+    ref = spectral.embed(g, 4, 8, 9)
+    assert rel_fro(emb.cpu().numpy()[:, :4], ref) <= 1e-5
+    plain = fsc.embed(G, 4, 8, 9).cpu().numpy()
+    assert rel_fro(emb.cpu().numpy(), plain) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["sbm", "knn", "isolated"])
+def test_features_match_oracle(torch, name):
+    import paper_2310_10939_gb300 as fsc
+    g = {"sbm": lambda: W.sbm_by_degree(20_000, 12, 18.0, 2.0, seed=3),
+         "knn": lambda: W.knn_mixture(3000, 16, 6, 10, seed=4),
+         "isolated": lambda: W.with_isolated(W.sbm([300, 500], 0.05, 0.004, 5), 20)}[name]()
+    G = fsc.Graph.from_workload(g)
+    k, l, seed = 12 if name == "sbm" else 6, 4, 17
+    _, feats, _ = fsc.filter_embed(G, l, k, seed, coeffs=torch.zeros(9, device="cuda"))
+    ref = fl.features(g, k, l, gaussian_block(g.n, l, seed))
+    f = feats.cpu().numpy().astype(np.float64)
+    assert np.allclose(f[:8], ref[:8], rtol=1e-5, atol=1e-6)
+    assert np.allclose(f[8:], ref[8:], rtol=0, atol=2e-5)
+
+
+def _weights_available():
+    import paper_2310_10939_gb300 as fsc
+    return os.path.exists(fsc.FILTER_WEIGHTS)
+
+
+def test_trained_filter_gains_over_plain_method_on_held_out_graphs(torch):
+    """On graphs unseen in training, the learned degree-8 filter has a lower subspace error
+    ||p(M)X - PX||^2 / ||PX||^2 than 8 power iterations (the same number of sparse products)."""
+    import paper_2310_10939_gb300 as fsc
+    assert _weights_available(), "trained filter weights are missing"
+    params = fsc.load_filter_params()
+    rng = np.random.default_rng(12345)
+    learned, plain8, plain22 = [], [], []
+    for i in range(12):
+        n = int(np.exp(rng.uniform(np.log(2000), np.log(40_000))))
+        k = int(np.exp(rng.uniform(np.log(3), np.log(min(60, n // 40)))))
+        g = W.sbm_by_degree(n, k, float(rng.uniform(12, 36)), float(rng.uniform(1, 3)), seed=900_000 + i)
+        l = max(1, int(np.ceil(np.log2(k))))
+        seed = 77 + i
+        X = gaussian_block(g.n, l, seed)
+        Gq, b, e0 = fl.target(g, k, X)
+        G = fsc.Graph.from_workload(g)
+        _, _, cf = fsc.filter_embed(G, l, k, seed, params=params)
+        learned.append(fl.filter_loss(cf.cpu().numpy().astype(np.float64), Gq, b, e0))
+        plain8.append(fl.filter_loss(fl.power_coefficients(8), Gq, b, e0))
+        PX = fl.top_projection(g, k, X)
+        Y = spectral.power_method(spectral.signless_laplacian(g), X, 22)
+        plain22.append(float(((Y - PX) ** 2).sum() / e0))
+    learned, plain8 = np.array(learned), np.array(plain8)
+    print("held-out subspace error: learned %.4f, plain t=8 %.4f, plain t=22 %.4f"
+          % (learned.mean(), plain8.mean(), np.mean(plain22)))
+    assert learned.mean() < plain8.mean()
+    assert (learned < plain8).mean() >= 0.75
+
+
+def test_filtered_clustering_recovers_sbm(torch):
+    """Algorithm 2 with the learned filter (bf16 basis) clusters an SBM as well as the plain method."""
+    import paper_2310_10939_gb300 as fsc
+    assert _weights_available(), "trained filter weights are missing"
+    params = fsc.load_filter_params()
+    g = W.sbm_by_degree(100_000, 20, 30.0, 3.0, seed=31)
+    G = fsc.Graph.from_workload(g)
+    lab_f, st = fsc.cluster_filtered(G, 20, 5, 31, params, store=fsc.BF16)
+    l, t = 5, 17
+    ref = ocluster.fast_spectral_cluster(g, 20, l, t, 31)
+    a_f = metrics.ari(lab_f.cpu().numpy(), g.labels)
+    a_ref = metrics.ari(ref["labels"], g.labels)
+    assert a_f >= a_ref - 0.01, (a_f, a_ref)

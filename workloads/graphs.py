@@ -99,7 +99,22 @@ def sbm(sizes, p_in: float, p_out: float, seed: int, name: str = "sbm") -> Graph
     block_of = np.repeat(np.arange(k, dtype=np.int64), sizes)
 
     keys = np.empty(0, dtype=np.int64)
-    need = counts.copy()
+    # dense block pairs (many of their pairs are edges): choose the subset from the full enumeration
+    dense = (npairs <= 20000) | (counts * 4 >= npairs)
+    dense_keys = []
+    for gi in np.nonzero(dense & (counts > 0))[0]:
+        b1, b2 = int(bi[gi]), int(bj[gi])
+        if b1 == b2:
+            iu, ju = np.triu_indices(int(sizes[b1]), 1)
+            lo_c, hi_c = iu + starts[b1], ju + starts[b1]
+        else:
+            ii, jj = np.meshgrid(np.arange(sizes[b1]), np.arange(sizes[b2]), indexing="ij")
+            lo_c, hi_c = ii.ravel() + starts[b1], jj.ravel() + starts[b2]
+        pick = rng.choice(lo_c.size, int(counts[gi]), replace=False)
+        dense_keys.append(lo_c[pick].astype(np.int64) * n + hi_c[pick].astype(np.int64))
+    if dense_keys:
+        keys = _sorted_unique(np.concatenate(dense_keys))
+    need = np.where(dense, 0, counts)
     for _ in range(64):
         if need.sum() == 0:
             break
@@ -113,7 +128,7 @@ def sbm(sizes, p_in: float, p_out: float, seed: int, name: str = "sbm") -> Graph
         lo_all = keys // n
         hi_all = keys % n
         have = np.bincount(group_of[block_of[lo_all], block_of[hi_all]], minlength=bi.size)
-        need = counts - have
+        need = np.where(dense, 0, counts - have)
         assert (need >= 0).all()
     else:
         raise RuntimeError("SBM sampler did not converge")
