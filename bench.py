@@ -38,6 +38,10 @@ WORKLOADS = {
                              "k=10, l=4, t=20, float32"),
     "image_481x321_bf16": dict(kind="image", k=8, l=3, t=30, store="bf16", seed=3,
                                desc="481x321 Voronoi image graph, radius 3; k=8, l=3, t=30, bfloat16 storage"),
+    "sbm_n2p22_k100": dict(kind="sbm_gpu", n=2 ** 22, k=100, deg_in=36.0, deg_out=4.0, l=7, t=22, store="f32", seed=19,
+                           desc="SBM n=2^22, 100 equal blocks, intra-degree 36, inter-degree 4 (GPU generator), "
+                                "k=100, l=7; plain t=22 float32 (value) vs the learned degree-8 filter with bf16 "
+                                "iterates (variants)"),
     "sbm_batch_4096": dict(kind="batch", G=4096, n_range=(500, 50_000), k_range=(2, 20), deg_in=15.0, deg_out=1.5,
                            store="bf16", seed=13,
                            desc="4096 SBM graphs, n~U[500,50000], k~U[2,20], intra-degree 15, inter-degree 1.5, "
@@ -57,6 +61,11 @@ def make_graph(w):
         return W.knn_mixture(w["npts"], w["dim"], w["ncomp"], w["knn"], seed=w["seed"], device=dev)
     if w["kind"] == "image":
         return W.image_grid(321, 481, 8, seed=w["seed"])
+    if w["kind"] == "sbm_gpu":
+        gb = W.sbm_batch_gpu(1, (w["n"], w["n"]), (w["k"], w["k"]), w["deg_in"], w["deg_out"], seed=w["seed"],
+                             with_weights=False)
+        return W.Graph(w["n"], gb.row_ptr.cpu().numpy(), gb.col.cpu().numpy(), None, gb.labels.cpu().numpy(),
+                       "sbm_n2p22_k100")
     raise ValueError(w["kind"])
 
 
@@ -237,6 +246,8 @@ def gpu_arm(args, w, rank, world, local_rank):
         torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
         e2e = float(x[0])
 
+    variants = time_variants(args, g, rp, col, wt, k, l, t, seed, flush) if not args.no_variants else None
+
     bytes_launch = spmm_bytes_per_launch(g, l, w["store"])
     peak, peak_src = read_peaks()
     achieved = bytes_launch / (spmm_launch_ms * 1e-3) / 1e9
@@ -270,8 +281,43 @@ def gpu_arm(args, w, rank, world, local_rank):
         "wall_s": round(wall, 3),
         "gpu_launches": args.steps * (1 + 1 + t + 2),
         "clocks": clk,
+        "variants": variants,
     }
     return out, g
+
+
+def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
+    """The same clustering with bf16 iterates, and with the learned degree-8 filter (bf16):
+    ms per clustering (create_graph + cluster) and ARI against the planted labels."""
+    import torch
+    import paper_2310_10939_gb300 as fsc
+    from paper_2310_10939_gb300 import metrics as pm
+    out = {}
+    params = fsc.load_filter_params() if os.path.exists(fsc.FILTER_WEIGHTS) else None
+    runs = {"plain_bf16": lambda G: fsc.cluster(G, k, l, t, seed, store=fsc.BF16, rescale=True)[0]}
+    if params is not None:
+        runs["learned_filter_bf16"] = lambda G: fsc.cluster_filtered(G, k, l, seed, params, store=fsc.BF16)[0]
+    for name, fn in runs.items():
+        for _ in range(3):
+            G = fsc.Graph(rp, col, wt)
+            fn(G)
+            G.close()
+        times = []
+        lab = None
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            G = fsc.Graph(rp, col, wt)
+            lab = fn(G)
+            G.close()
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        out[name] = {"ms": round(float(np.mean(times)), 4), "ari_vs_planted": round(pm.ari(lab.cpu().numpy(), g.labels), 4)}
+    if params is None:
+        out["learned_filter_bf16"] = "weights file missing"
+    return out
 
 
 def batch_arm(args, w):
@@ -408,6 +454,7 @@ def main():
     ap.add_argument("--impl", choices=["fsc", "reference"], default="fsc")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sbm_n2p20_k16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -432,7 +479,7 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     out, g = gpu_arm(args, w, rank, world, local_rank)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and g.n <= 2 ** 20:
         t0 = time.perf_counter()
         ari_cpu, _ = cpu_oracle_step(g, w)
         cpu_ms = (time.perf_counter() - t0) * 1e3

@@ -251,12 +251,23 @@ struct LloydArgs {
     const unsigned* amax;
     long long chunk;
     int ntab;
+    float* lbound;       // per point: lower bound on the distance to every other centroid (pruning)
+    float* pmove;        // per cluster: how far its centroid moved in the last update (rounded up)
+    int prune;           // 1: skip the k-way scan of points whose bounds prove the label unchanged
     KmDevStats* st;
     GridBarrier* bar;
     int* status;
     long long limit;
     int stall;
 };
+
+// Exact pruning (Hamerly's bounds): a point whose distance to its current centroid is below
+// max(s(a), lb) - where s(a) is half the distance from centroid a to its nearest other centroid
+// and lb a lower bound on the distance to every other centroid - keeps its label without the
+// k-way scan (triangle inequality).  The bounds are computed in float32 and widened by the
+// relative margin PRUNE_EPS, far above the float32 rounding of the distances (< 1e-6), so a
+// skipped point is exactly one the full scan would leave in place (no tie is possible).
+constexpr float PRUNE_EPS = 1e-5f;
 
 template <int LP>
 __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydArgs a) {
@@ -267,10 +278,12 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
     float* s_c = reinterpret_cast<float*>(km_smem);
     unsigned long long* s_tab =
         reinterpret_cast<unsigned long long*>(km_smem + (((size_t)k * LP * 4 + 15) & ~(size_t)15));
+    float* s_sep = reinterpret_cast<float*>(s_tab + (size_t)ntab * rowlen);   // k floats
     __shared__ long long s_red[KM_WARPS];
     __shared__ int s_redi[KM_WARPS];
     __shared__ long long s_tot[LP + 1];
     __shared__ int s_stop, s_changed;
+    __shared__ unsigned s_pmax;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
     const long long chunk = a.chunk;
@@ -282,9 +295,33 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
         for (int q = tid; q < k * LP; q += KM_THREADS) a.c64[q] = (double)__ldcg(a.c32 + q);
     }
     for (int it = 1; it <= a.max_iter; ++it) {
+        const bool pr = a.prune && it > 1;
         for (int q = tid; q < k * LP; q += KM_THREADS) s_c[q] = __ldcg(a.c32 + q);
         for (size_t q = tid; q < (size_t)ntab * rowlen; q += KM_THREADS) s_tab[q] = 0ull;
+        if (pr) {
+            for (int q = tid; q < k; q += KM_THREADS) reinterpret_cast<unsigned*>(s_sep)[q] = 0x7f800000u;   // +inf
+            if (tid == 0) s_pmax = 0u;
+        }
         __syncthreads();
+        if (pr) {
+            // half the distance of each centroid to its nearest other centroid, and the largest move
+            for (int q = tid; q < k * k; q += KM_THREADS) {
+                const int j = q / k, jj = q % k;
+                if (jj > j) {
+                    float cj[LP];
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) cj[c] = s_c[j * LP + c];
+                    const unsigned d = __float_as_uint(sqdist<LP>(cj, s_c + jj * LP));
+                    atomicMin(reinterpret_cast<unsigned*>(s_sep) + j, d);
+                    atomicMin(reinterpret_cast<unsigned*>(s_sep) + jj, d);
+                }
+            }
+            for (int q = tid; q < k; q += KM_THREADS) atomicMax(&s_pmax, __float_as_uint(__ldcg(a.pmove + q)));
+            __syncthreads();
+            for (int q = tid; q < k; q += KM_THREADS) s_sep[q] = 0.5f * sqrtf(s_sep[q]) * (1.0f - PRUNE_EPS);
+            __syncthreads();
+        }
+        const float pmax = pr ? __uint_as_float(s_pmax) * (1.0f + PRUNE_EPS) : 0.f;
         long long inert = 0;
         int changed = 0;
         // ---- phase A: assignment of KM_PPT consecutive points per thread
@@ -300,37 +337,70 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
             const long long i0 = t0 + (long long)KM_PPT * tid;
             float x[KM_PPT][LP];
             int old[KM_PPT];
+            float lbv[KM_PPT];
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
                 if (i0 + u < hi) {
                     load_point<LP>(a.X, i0 + u, a.l, x[u]);
                     old[u] = a.labels[i0 + u];
+                    lbv[u] = pr ? a.lbound[i0 + u] : 0.f;
                 } else {
 #pragma unroll
                     for (int c = 0; c < LP; ++c) x[u][c] = 0.f;
                     old[u] = 0;
+                    lbv[u] = 0.f;
                 }
             }
-            float best[KM_PPT];
+            float best[KM_PPT], sec[KM_PPT], lbn[KM_PPT];
             int bj[KM_PPT];
+            bool need[KM_PPT];
+            bool any = false;
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
-                best[u] = __int_as_float(0x7f800000);   // +inf
+                best[u] = __int_as_float(0x7f800000);
+                sec[u] = __int_as_float(0x7f800000);
                 bj[u] = 0;
-            }
-            for (int j = 0; j < k; ++j) {
-                float cj[LP];
-#pragma unroll
-                for (int c = 0; c < LP; ++c) cj[c] = s_c[j * LP + c];
-#pragma unroll
-                for (int u = 0; u < KM_PPT; ++u) {
-                    const float d = sqdist<LP>(x[u], cj);
-                    if (d < best[u]) { best[u] = d; bj[u] = j; }
+                need[u] = i0 + u < hi;
+                lbn[u] = 0.f;
+                if (pr && need[u]) {
+                    const int ca = old[u];
+                    const float da = sqdist<LP>(x[u], s_c + ca * LP);
+                    const float lw = fmaxf(0.f, lbv[u] - pmax);
+                    if (sqrtf(da) * (1.0f + PRUNE_EPS) < fmaxf(s_sep[ca], lw)) {
+                        best[u] = da;
+                        bj[u] = ca;
+                        lbn[u] = lw;
+                        need[u] = false;
+                    }
                 }
+                any |= need[u];
+            }
+            if (any) {
+                for (int j = 0; j < k; ++j) {
+                    float cj[LP];
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) cj[c] = s_c[j * LP + c];
+#pragma unroll
+                    for (int u = 0; u < KM_PPT; ++u) {
+                        if (!need[u]) continue;
+                        const float d = sqdist<LP>(x[u], cj);
+                        if (d < best[u]) {
+                            sec[u] = best[u];
+                            best[u] = d;
+                            bj[u] = j;
+                        } else if (d < sec[u]) {
+                            sec[u] = d;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u)
+                    if (need[u]) lbn[u] = sqrtf(sec[u]) * (1.0f - PRUNE_EPS);
             }
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
                 if (i0 + u >= hi) break;
+                if (a.prune) a.lbound[i0 + u] = lbn[u];
                 const int lab = bj[u];
                 changed += old[u] != lab;
                 a.labels[i0 + u] = lab;
@@ -430,14 +500,21 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
                 if (lane == 0) s_tot[wid] = tot;
             }
             __syncthreads();
-            if (tid < LP) {
+            if (wid == 0) {
                 const long long cntj = s_tot[LP];
-                if (cntj > 0) {
-                    const double m = ((double)s_tot[tid] * pow2d(-sc.Sx)) / (double)cntj;
-                    a.c64[(size_t)j * LP + tid] = m;
-                    a.c32[(size_t)j * LP + tid] = (float)m;
-                } else if (tid == 0) {
-                    atomicAdd(&a.st->empty_events, 1);
+                float mv = 0.f;
+                if (lane < LP && cntj > 0) {
+                    const double m = ((double)s_tot[lane] * pow2d(-sc.Sx)) / (double)cntj;
+                    const float c32n = (float)m;
+                    const float dlt = __fsub_rn(c32n, s_c[j * LP + lane]);
+                    mv = __fmul_rn(dlt, dlt);
+                    a.c64[(size_t)j * LP + lane] = m;
+                    a.c32[(size_t)j * LP + lane] = c32n;
+                }
+                mv = warp_sum_f(mv);
+                if (lane == 0) {
+                    a.pmove[j] = sqrtf(mv) * (1.0f + PRUNE_EPS);
+                    if (cntj == 0) atomicAdd(&a.st->empty_events, 1);
                 }
             }
             __syncthreads();
@@ -473,7 +550,8 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     int ntab = (int)(65536 / tab_bytes);
     if (ntab > KM_WARPS) ntab = KM_WARPS;
     if (ntab < 1) ntab = 1;
-    const size_t lloyd_smem = (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes;
+    const size_t lloyd_smem =
+        (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes + (size_t)k * 4;
     auto kpp = k_kmeanspp<LP>;
     auto lly = k_lloyd<LP>;
     FSC_CUDA(cudaFuncSetAttribute(kpp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kpp_smem));
@@ -502,6 +580,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
     const size_t o_seed = off; off += up((size_t)k * 8);
+    const size_t o_pmove = off; off += up((size_t)k * 4);
     char* ws = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, s);
     if (e != cudaSuccess) return cuda_status(e);
@@ -552,6 +631,9 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.amax = amax;
         la.chunk = chunk;
         la.ntab = ntab;
+        la.lbound = ka.d2[0];          // the k-means++ D^2 buffers are free once seeding is done
+        la.pmove = reinterpret_cast<float*>(ws + o_pmove);
+        la.prune = k <= 256 ? 1 : 0;
         la.st = st;
         la.bar = bar;
         la.status = call_status;
@@ -684,7 +766,8 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     int ntab = (int)(65536 / tab_bytes);
     if (ntab > KM_WARPS) ntab = KM_WARPS;
     if (ntab < 1) ntab = 1;
-    const size_t lloyd_smem = (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes;
+    const size_t lloyd_smem =
+        (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes + (size_t)k * 4;
     auto kpp = k_kmeanspp<LP>;
     auto lly = k_lloyd<LP>;
     FSC_CUDA(cudaFuncSetAttribute(kpp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kpp_smem));
@@ -712,6 +795,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
     const size_t o_seed = off; off += up((size_t)k * 8);
+    const size_t o_pmove = off; off += up((size_t)k * 4);
     if (off > (size_t)FSC_KMEANS_STATIC_SCRATCH_BYTES) return FSC_ERR_TOO_LARGE;
 
     KmDevStats* st = reinterpret_cast<KmDevStats*>(ws + o_hdr);
@@ -760,6 +844,9 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     la.amax = amax;
     la.chunk = chunk;
     la.ntab = ntab;
+    la.lbound = ka.d2[0];
+    la.pmove = reinterpret_cast<float*>(ws + o_pmove);
+    la.prune = k <= 256 ? 1 : 0;
     la.st = st;
     la.bar = bar;
     la.status = call_status;
