@@ -35,7 +35,8 @@ def main():
     ap.add_argument("--out", default=HERE)
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--batch", type=int, default=256)
-    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval-every", type=int, default=10)
     ap.add_argument("--val-frac", type=float, default=0.15)
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
@@ -79,6 +80,7 @@ def main():
     step = 0
     t0 = time.time()
     history = []
+    best_val, best_params, best_epoch = float("inf"), P.clone(), -1
     for ep in range(args.epochs):
         perm = torch.as_tensor(rng.permutation(tr.size), device=dev)
         for s in range(steps_per_epoch):
@@ -87,10 +89,16 @@ def main():
             lr = args.lr * 0.5 * (1.0 + math.cos(math.pi * step / total))
             fsc.mlp_train_step(P, grad, m, v, step, lr, Fn_tr[sel].contiguous(), G_tr[sel].contiguous(),
                                b_tr[sel].contiguous(), loss=loss_buf, apply_update=True)
-        if ep % 25 == 0 or ep == args.epochs - 1:
-            history.append({"epoch": ep, "train": eval_loss(Fn_tr, G_tr, b_tr), "val": eval_loss(Fn_va, G_va, b_va)})
+        if ep % args.eval_every == 0 or ep == args.epochs - 1:
+            vl = eval_loss(Fn_va, G_va, b_va)
+            if vl < best_val:                      # keep the best validation snapshot
+                best_val, best_epoch = vl, ep
+                best_params.copy_(P)
+            if ep % (10 * args.eval_every) == 0 or ep == args.epochs - 1:
+                history.append({"epoch": ep, "train": eval_loss(Fn_tr, G_tr, b_tr), "val": vl})
     torch.cuda.synchronize()
     secs = time.time() - t0
+    P.copy_(best_params)
 
     # fold the standardisation into the first layer: W1' = W1 / sd, b1' = b1 - W1' mu
     th = P.cpu().numpy().astype(np.float64)
@@ -106,7 +114,7 @@ def main():
     lv = np.array([c[i] @ Gn[val][i] @ c[i] - 2 * bn[val][i] @ c[i] + 1.0 for i in range(val.size)])
     summary = {
         "graphs": int(N), "train": int(tr.size), "val": int(val.size), "epochs": args.epochs, "steps": step,
-        "train_seconds": round(secs, 2), "start": start, "history": history,
+        "train_seconds": round(secs, 2), "start": start, "history": history, "best_epoch": best_epoch,
         "val_mean_loss_learned": float(lv.mean()),
         "val_mean_loss_plain_t8": float(d["loss8"][val].mean()),
         "val_mean_loss_plain_t22": float(d["loss22"][val].mean()),
