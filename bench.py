@@ -287,7 +287,7 @@ def gpu_arm(args, w, rank, world, local_rank):
 
 
 def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
-    """The same clustering with bf16 iterates, and with the learned degree-8 filter (bf16):
+    """The same clustering with bf16 iterates, and with the learned degree-8 filter (float32 basis):
     ms per clustering (create_graph + cluster) and ARI against the planted labels."""
     import torch
     import paper_2310_10939_gb300 as fsc
@@ -296,7 +296,7 @@ def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
     params = fsc.load_filter_params() if os.path.exists(fsc.FILTER_WEIGHTS) else None
     runs = {"plain_bf16": lambda G: fsc.cluster(G, k, l, t, seed, store=fsc.BF16, rescale=True)[0]}
     if params is not None:
-        runs["learned_filter_bf16"] = lambda G: fsc.cluster_filtered(G, k, l, seed, params, store=fsc.BF16)[0]
+        runs["learned_filter_f32"] = lambda G: fsc.cluster_filtered(G, k, l, seed, params, store=fsc.F32)[0]
     for name, fn in runs.items():
         for _ in range(3):
             G = fsc.Graph(rp, col, wt)
@@ -316,7 +316,7 @@ def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
             times.append(a.elapsed_time(b))
         out[name] = {"ms": round(float(np.mean(times)), 4), "ari_vs_planted": round(pm.ari(lab.cpu().numpy(), g.labels), 4)}
     if params is None:
-        out["learned_filter_bf16"] = "weights file missing"
+        out["learned_filter_f32"] = "weights file missing"
     return out
 
 

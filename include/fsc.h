@@ -112,6 +112,15 @@ fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* row_ptr, cons
 /* Frees the library-owned arrays of g (synchronises the device first). NULL is a no-op. */
 fsc_status fsc_destroy_graph(fsc_graph* g);
 
+/*
+ * Device memory.  The library's own buffers (degree arrays, workspaces, k-means scratch) come
+ * from one stream-ordered pool per device that keeps freed blocks mapped, so repeated
+ * create / cluster / destroy cycles neither map nor unmap memory.  fsc_release_cached_memory
+ * synchronises every device the pool has used and returns the cached blocks to the driver
+ * (blocks still owned by live graphs stay).  Host call.
+ */
+fsc_status fsc_release_cached_memory(void);
+
 /* Host call: fills *info (pointers stay valid until fsc_destroy_graph). */
 fsc_status fsc_graph_info(const fsc_graph* g, fsc_graph_info_t* info);
 
@@ -276,7 +285,12 @@ fsc_status fsc_batch_destroy(fsc_batch* batch);
  *   X the same start block as fsc_embed(seed).  params: device MLP parameters, or NULL when
  *   coeffs_override (device, 9 floats) gives the coefficients.  feats_out (16) and coeffs_out
  *   (9) are optional device outputs.  opts: threads_per_row and the events bracketing the 8
- *   sparse steps (flags ignored).  Asynchronous.
+ *   sparse steps (flags ignored).  store is the type the basis T_j X is held in: FSC_F32 is
+ *   the working choice.  The coefficients alternate in sign and cancel the bulk of the
+ *   spectrum, so rounding in the basis does not cancel with it and the recurrence carries it
+ *   forward: with FSC_BF16 the leakage ||(I - P) Y||^2 / ||P Y||^2 of an SBM (n = 1e5, k = 20,
+ *   mean degree 33) rises from 1.3e-3 to 1.7e-2 and k-means lands in worse optima.
+ *   Asynchronous.
  * fsc_cluster_filtered: fsc_filter_embed then fsc_kmeans; synchronous.
  * fsc_mlp_forward: coefficients (batch x 9) of features (batch x 16), device arrays.
  * fsc_mlp_train_step: adds the gradient of the mean loss c^T Gn c - 2 bn^T c + 1 over the

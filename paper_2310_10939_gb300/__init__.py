@@ -113,6 +113,8 @@ def lib() -> C.CDLL:
             getattr(L, name).restype = i32
         L.fsc_default_params.argtypes = [i64, i32, i32, C.POINTER(i32), C.POINTER(i32)]
         L.fsc_sync_status.argtypes = [vp]
+        L.fsc_release_cached_memory.argtypes = []
+        L.fsc_release_cached_memory.restype = i32
         L.fsc_set_wait_limit_ns.argtypes = [i64]
         L.fsc_set_wait_limit_ns.restype = None
         L.fsc_inject_barrier_stall.argtypes = [i32]
@@ -172,6 +174,11 @@ def default_params(n: int, k: int, mode: int = 0):
 
 def sync_status(stream=None):
     _check(lib().fsc_sync_status(_stream(stream)), "fsc_sync_status")
+
+
+def release_cached_memory():
+    """fsc_release_cached_memory: return the library pool's cached device blocks to the driver."""
+    _check(lib().fsc_release_cached_memory(), "fsc_release_cached_memory")
 
 
 def set_wait_limit_ns(ns: int):
@@ -440,7 +447,7 @@ def filter_embed(g: Graph, l: int, k: int, seed: int, params=None, coeffs=None, 
     return out, feats, cf
 
 
-def cluster_filtered(g: Graph, k: int, l: int, seed: int, params, store: int = BF16, max_iter: int = 100,
+def cluster_filtered(g: Graph, k: int, l: int, seed: int, params, store: int = F32, max_iter: int = 100,
                      labels=None, threads_per_row: int = 0, events=None, stream=None):
     """fsc_cluster_filtered: Algorithm 2 with the learned filter in place of M^t.  Returns (labels, stats)."""
     torch = _torch()

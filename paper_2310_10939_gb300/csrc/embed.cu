@@ -119,7 +119,7 @@ fsc_status autotune_graph(fsc_graph* g, int l, fsc_dtype store, int* best, float
     const size_t es = store == FSC_F32 ? 4 : 2;
     const size_t bytes = (size_t)g->n * LP * es;
     void* buf = nullptr;
-    FSC_CUDA(cudaMalloc(&buf, 2 * bytes + 256));
+    FSC_CUDA(pool_malloc(&buf, 2 * bytes + 256, s));
     char* zin = static_cast<char*>(buf);
     char* zout = zin + ((bytes + 255) & ~(size_t)255);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -155,8 +155,8 @@ fsc_status autotune_graph(fsc_graph* g, int l, fsc_dtype store, int* best, float
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    pool_free(buf, s);
     cudaStreamSynchronize(s);
-    cudaFree(buf);
     if (e != cudaSuccess) return cuda_status(e);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -168,16 +168,16 @@ fsc_status autotune_graph(fsc_graph* g, int l, fsc_dtype store, int* best, float
     return FSC_OK;
 }
 
-fsc_status ensure_workspace(fsc_graph* g, size_t bytes) {
+fsc_status ensure_workspace(fsc_graph* g, size_t bytes, cudaStream_t s) {
     if (g->ws_bytes >= bytes) return FSC_OK;
-    if (g->ws) {
-        cudaError_t e = cudaFree(g->ws);
+    if (g->ws) {   // calls on one graph are stream-ordered, so the old block is free after them
+        cudaError_t e = pool_free(g->ws, s);
         g->ws = nullptr;
         g->ws_bytes = 0;
         if (e != cudaSuccess) return cuda_status(e);
     }
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = pool_malloc(&p, bytes, s);
     if (e != cudaSuccess) return cuda_status(e);
     g->ws = p;
     g->ws_bytes = bytes;
@@ -208,7 +208,7 @@ extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed
         if (opts && opts->ev_spmm_end) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_end, s));
         return FSC_OK;
     }
-    fsc_status rc = ensure_workspace(g, (size_t)n * LP * 4 + 256);
+    fsc_status rc = ensure_workspace(g, (size_t)n * LP * 4 + 256, s);
     if (rc != FSC_OK) return rc;
     unsigned* cm = g->colmax;   // three buffers of 8
     int* expo = rescale ? g->expo : nullptr;

@@ -33,7 +33,7 @@ static_assert(NPARAM == 5833, "parameter count");
 cudaError_t launch_init_any(int LP, int n, int l, unsigned long long seed, const float* dinv, void* out, int store,
                             cudaStream_t s);
 int choose_threads_per_row(const fsc_graph* g, int requested, int LP, int store);
-fsc_status ensure_workspace(fsc_graph* g, size_t bytes);
+fsc_status ensure_workspace(fsc_graph* g, size_t bytes, cudaStream_t s);
 
 // ---- Chebyshev step -----------------------------------------------------------------------------
 template <int LP, typename TS, int G, int U, bool W>
@@ -371,7 +371,7 @@ extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64
     if (blocks < 1) blocks = 1;
     // workspace: 9 basis blocks | 4 x 3 x blocks moment sums | coefficients (16) | features (16)
     const size_t mom_bytes = (size_t)4 * 3 * blocks * 4;
-    fsc_status rc = ensure_workspace(g, NCOEF * blk + mom_bytes + 256);
+    fsc_status rc = ensure_workspace(g, NCOEF * blk + mom_bytes + 256, s);
     if (rc != FSC_OK) return rc;
     char* ws = static_cast<char*>(g->ws);
     float* mom = reinterpret_cast<float*>(ws + NCOEF * blk);
@@ -424,13 +424,13 @@ extern "C" fsc_status fsc_cluster_filtered(const fsc_graph* g, int k, int l, uin
     const int LP = pad_l(l);
     cudaStream_t s = as_stream(stream);
     float* emb = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&emb), (size_t)g->n * LP * 4, s);
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&emb), (size_t)g->n * LP * 4, s);
     if (e != cudaSuccess) return cuda_status(e);
     fsc_kmeans_stats local{};
     fsc_status rc = fsc_filter_embed(g, l, k, seed, store, params, nullptr, emb, nullptr, nullptr, opts, stream);
     if (rc == FSC_OK)
         rc = fsc_kmeans(emb, g->n, l, LP, k, seed, max_iter, labels, nullptr, nullptr, stats ? stats : &local, stream);
-    cudaError_t ef = cudaFreeAsync(emb, s);
+    cudaError_t ef = pool_free(emb, s);
     if (rc == FSC_OK && ef != cudaSuccess) rc = cuda_status(ef);
     if (rc == FSC_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_status(e);
     return rc;

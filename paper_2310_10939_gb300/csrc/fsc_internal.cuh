@@ -35,6 +35,14 @@ int* device_status_word();                // per-device error word (allocated on
 long long wait_limit_ns();
 int barrier_stall();                      // testing hook: nonzero = never release grid barriers
 fsc_status cuda_status(cudaError_t e);    // records and maps a CUDA error
+// Device memory for the library's own buffers comes from one stream-ordered pool per device that
+// keeps freed blocks mapped (release threshold = max), so repeated create / cluster / destroy
+// cycles neither map nor unmap memory; fsc_release_cached_memory() returns it to the driver.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+cudaError_t pool_free(void* p, cudaStream_t s);
+// Blocks per SM of a kernel at (threads, dynamic shared bytes), with the opt-in shared-memory
+// attribute raised as needed; cached per (device, kernel, threads, bytes).  0 on error.
+int kernel_occupancy(const void* fn, int threads, size_t smem);
 
 #define FSC_CUDA(call)                                            \
     do {                                                          \

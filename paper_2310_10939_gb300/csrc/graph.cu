@@ -4,7 +4,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "fsc_internal.cuh"
 
@@ -46,6 +48,60 @@ int* device_status_word() {
     return g_status_word[dev];
 }
 
+namespace {
+cudaMemPool_t g_pool[kMaxDevices];
+std::mutex g_pool_mu;
+std::mutex g_occ_mu;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;
+std::map<std::pair<int, const void*>, size_t> g_smem_attr;
+}  // namespace
+
+static cudaMemPool_t library_pool(int dev) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = p;
+    }
+    return g_pool[dev];
+}
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool = library_pool(dev);
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes < 256 ? 256 : bytes, pool, s);
+}
+
+cudaError_t pool_free(void* p, cudaStream_t s) { return p ? cudaFreeAsync(p, s) : cudaSuccess; }
+
+int kernel_occupancy(const void* fn, int threads, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    const auto key = std::make_tuple(dev, fn, threads, smem);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+    size_t& attr = g_smem_attr[std::make_pair(dev, fn)];
+    if (smem > 48 * 1024 && smem > attr) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+        attr = smem;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) return 0;
+    g_occ[key] = per_sm;
+    return per_sm;
+}
+
 long long wait_limit_ns() { return g_wait_limit.load(); }
 int barrier_stall() { return g_stall.load(); }
 
@@ -65,11 +121,12 @@ fsc_status status_from_bits(int bits) {
     return FSC_ERR_CUDA;
 }
 
-// One thread per row: validates the row and forms d(v) = sum_{u != v} w(u, v).  Unit weights:
-// an exact integer count.  Weighted: a float64 sum in row order (the order of the definition).
-// D^-1/2 and 1/d are formed in float32 from the float64 degree (correctly rounded sqrt and
-// division, so within 1-2 ulp of the exact values); float64 arithmetic is kept out of the
-// unit-weight path because it runs at a small fraction of the float32 rate on this GPU.
+// Validation and degrees, kDegLanes lanes per row: the lanes of a row read its entries side by
+// side (coalesced), each keeps a partial count (unit weights, exact) or a float64 partial sum
+// (weights), and the partials meet in a shuffle tree.  D^-1/2 and 1/d are formed in float32 from
+// the float64 degree (correctly rounded sqrt and division, within 1-2 ulp of the exact values);
+// float64 arithmetic stays out of the unit-weight path, which it would slow down on this GPU.
+constexpr int kDegLanes = 8;
 __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                                 const int32_t* __restrict__ col, const float* __restrict__ w,
                                                 int check_sorted, double* __restrict__ deg,
@@ -77,53 +134,67 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
                                                 unsigned long long* __restrict__ n_iso, double* __restrict__ vol,
                                                 int* __restrict__ status, double* __restrict__ sumsq,
                                                 unsigned long long* __restrict__ dmax_bits) {
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (tid == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
+    constexpr int G = kDegLanes, RPW = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
     int bad = 0;
     unsigned iso = 0;
     double vsum = 0.0, vsq = 0.0, vmax = 0.0;
     long long cnt_total = 0;
-    for (int64_t i = tid; i < n; i += stride) {
-        const int64_t s = rp[i], e = rp[i + 1];
-        double d = 0.0;
-        long long cnt = 0;
-        if (s < 0 || e < s || e > nnz) {
-            bad |= ST_BAD_ROWPTR;
-        } else {
-            int prev = -1;
-            for (int64_t p = s; p < e; ++p) {
-                const int j = col[p];
-                if (j < 0 || (int64_t)j >= n) { bad |= ST_INDEX_RANGE; continue; }
-                if ((int64_t)j == i) { bad |= ST_SELF_LOOP; continue; }
-                if (check_sorted && j <= prev) bad |= ST_UNSORTED;
-                prev = j;
-                if (w) {
-                    const float wv = w[p];
-                    if (!(wv >= 0.0f) || isinf(wv)) { bad |= ST_BAD_WEIGHT; continue; }
-                    d += (double)wv;
-                } else {
-                    ++cnt;
-                }
+    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {   // warp-uniform trip count
+        const int64_t i = base + grp;
+        const bool active = i < n;
+        int64_t s = 0, e = 0;
+        if (active) {
+            s = rp[i];
+            e = rp[i + 1];
+            if (s < 0 || e < s || e > nnz) {
+                bad |= ST_BAD_ROWPTR;
+                s = e = 0;
             }
         }
-        if (!w) {
-            d = (double)cnt;
-            cnt_total += cnt;
-        } else {
-            vsum += d;
+        double d = 0.0;
+        long long cnt = 0;
+        for (int64_t p = s + sub; p < e; p += G) {
+            const int j = col[p];
+            if (j < 0 || (int64_t)j >= n) { bad |= ST_INDEX_RANGE; continue; }
+            if ((int64_t)j == i) { bad |= ST_SELF_LOOP; continue; }
+            if (check_sorted && p > s && col[p - 1] >= j) bad |= ST_UNSORTED;
+            if (w) {
+                const float wv = w[p];
+                if (!(wv >= 0.0f) || isinf(wv)) { bad |= ST_BAD_WEIGHT; continue; }
+                d += (double)wv;
+            } else {
+                ++cnt;
+            }
         }
-        deg[i] = d;
-        vsq += d * d;
-        vmax = fmax(vmax, d);
-        if (d > 0.0) {
-            const float df = (float)d;
-            dinv[i] = 1.0f / sqrtf(df);
-            invdeg[i] = 1.0f / df;
-        } else {
-            dinv[i] = 0.0f;
-            invdeg[i] = 0.0f;
-            ++iso;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        if (w) {
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+        }
+        if (active && sub == 0) {
+            if (!w) {
+                d = (double)cnt;
+                cnt_total += cnt;
+            } else {
+                vsum += d;
+            }
+            deg[i] = d;
+            vsq += d * d;
+            vmax = fmax(vmax, d);
+            if (d > 0.0) {
+                const float df = (float)d;
+                dinv[i] = 1.0f / sqrtf(df);
+                invdeg[i] = 1.0f / df;
+            } else {
+                dinv[i] = 0.0f;
+                invdeg[i] = 0.0f;
+                ++iso;
+            }
         }
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -191,20 +262,26 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     g->row_ptr = row_ptr;
     g->col = col_idx;
     g->w = w;
-    // one allocation: deg (n doubles) | volume (1 double) | n_iso (1 u64) | status (int, padded) |
+    // one allocation: deg (n doubles) | header (256 B: volume, n_iso, status, sumsq, max bits) |
     //                 dinv (n floats) | invdeg (n floats) | colmax 24 u32 | expo 8 int
     const size_t n8 = (size_t)n * 8, n4 = ((size_t)n * 4 + 255) & ~(size_t)255;
     const size_t bytes = n8 + 256 + 2 * n4 + 256;
     char* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, bytes);
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&base), bytes, s);
     if (e != cudaSuccess) {
         delete g;
         return cuda_status(e);
     }
+    struct Header {           // device layout of the 256-byte header
+        double vol;
+        unsigned long long niso;
+        int status, pad;
+        double pad2;
+        double sumsq;
+        unsigned long long dmax_bits;
+    };
+    Header* hdr = reinterpret_cast<Header*>(base + n8);
     g->deg = reinterpret_cast<double*>(base);
-    double* vol = reinterpret_cast<double*>(base + n8);
-    unsigned long long* niso = reinterpret_cast<unsigned long long*>(base + n8 + 8);
-    int* status = reinterpret_cast<int*>(base + n8 + 16);
     g->dinv = reinterpret_cast<float*>(base + n8 + 256);
     g->invdeg = reinterpret_cast<float*>(base + n8 + 256 + n4);
     g->colmax = reinterpret_cast<unsigned*>(base + n8 + 256 + 2 * n4);
@@ -212,42 +289,37 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     fsc_status rc = FSC_OK;
     do {
         if ((e = cudaMemsetAsync(base + n8, 0, 256, s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(base + n8 + 256 + 2 * n4, 0, 256, s)) != cudaSuccess) break;
         const int threads = 256;
-        const int64_t want = (n + threads - 1) / threads;
-        const int blocks = (int)(want < (int64_t)device_props().num_sms * 64 ? want : (int64_t)device_props().num_sms * 64);
+        constexpr int rows_per_block = threads / 32 * (32 / kDegLanes);
+        const int64_t want = (n + rows_per_block - 1) / rows_per_block;
+        const int64_t cap = (int64_t)device_props().num_sms * 8;
+        const int blocks = (int)(want < cap ? want : cap);
         const int check_sorted = (flags & FSC_VALIDATE_SYMMETRY) ? 1 : 0;
-        double* sumsq = reinterpret_cast<double*>(base + n8 + 32);
-        unsigned long long* dmaxb = reinterpret_cast<unsigned long long*>(base + n8 + 40);
         k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,
-                                            g->invdeg, niso, vol, status, sumsq, dmaxb);
+                                            g->invdeg, &hdr->niso, &hdr->vol, &hdr->status, &hdr->sumsq,
+                                            &hdr->dmax_bits);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
-        int bits = 0;
-        if ((e = cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        Header h{};
+        if ((e = cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        int bits = h.status;
         if (bits == 0 && check_sorted) {
-            k_symmetry<<<blocks, threads, 0, s>>>(n, row_ptr, col_idx, w, status);
+            k_symmetry<<<blocks, threads, 0, s>>>(n, row_ptr, col_idx, w, &hdr->status);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
-            if ((e = cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+            if ((e = cudaMemcpyAsync(&bits, &hdr->status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
         }
         if (bits) { rc = status_from_bits(bits); break; }
-        unsigned long long iso = 0;
-        double v = 0;
-        if ((e = cudaMemcpyAsync(&iso, niso, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(&v, vol, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
-        double sq = 0.0;
-        unsigned long long mx = 0;
-        if ((e = cudaMemcpyAsync(&sq, base + n8 + 32, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(&mx, base + n8 + 40, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
-        g->n_isolated = (int64_t)iso;
-        g->volume = v;
-        g->deg_sumsq = sq;
-        memcpy(&g->deg_max, &mx, 8);
+        g->n_isolated = (int64_t)h.niso;
+        g->volume = h.vol;
+        g->deg_sumsq = h.sumsq;
+        memcpy(&g->deg_max, &h.dmax_bits, 8);
     } while (0);
     if (e != cudaSuccess) rc = cuda_status(e);
     if (rc != FSC_OK) {
-        cudaFree(base);
+        pool_free(base, s);
+        cudaStreamSynchronize(s);
         delete g;
         return rc;
     }
@@ -260,12 +332,30 @@ extern "C" fsc_status fsc_destroy_graph(fsc_graph* g) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
-    cudaDeviceSynchronize();
-    if (g->ws) cudaFree(g->ws);
-    cudaFree(g->deg);
+    // all work that may still read the graph's buffers ends here; the blocks go back to the
+    // library pool (no unmapping), ordered on the legacy stream after that point
+    cudaError_t e = cudaDeviceSynchronize();
+    pool_free(g->ws, 0);
+    pool_free(g->deg, 0);
     cudaSetDevice(prev);
     delete g;
-    return FSC_OK;
+    return e == cudaSuccess ? FSC_OK : cuda_status(e);
+}
+
+extern "C" fsc_status fsc_release_cached_memory(void) {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    cudaError_t first = cudaSuccess;
+    for (int d = 0; d < kMaxDevices; ++d) {
+        if (!g_pool[d]) continue;
+        cudaSetDevice(d);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemPoolTrimTo(g_pool[d], 0);
+        if (first == cudaSuccess) first = e;
+    }
+    cudaSetDevice(prev);
+    return first == cudaSuccess ? FSC_OK : cuda_status(first);
 }
 
 extern "C" fsc_status fsc_graph_info(const fsc_graph* g, fsc_graph_info_t* info) {

@@ -535,8 +535,7 @@ __global__ void k_merge_status(const int* __restrict__ call_status, int* __restr
 
 template <typename K>
 static int coop_blocks(K kern, size_t smem) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, KM_THREADS, smem) != cudaSuccess) return 0;
+    int per_sm = kernel_occupancy((const void*)kern, KM_THREADS, smem);
     if (per_sm > 2) per_sm = 2;
     return per_sm * device_props().num_sms;
 }
@@ -554,8 +553,6 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes + (size_t)k * 4;
     auto kpp = k_kmeanspp<LP>;
     auto lly = k_lloyd<LP>;
-    FSC_CUDA(cudaFuncSetAttribute(kpp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kpp_smem));
-    FSC_CUDA(cudaFuncSetAttribute(lly, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lloyd_smem));
     int G = coop_blocks(kpp, kpp_smem);
     const int G2 = coop_blocks(lly, lloyd_smem);
     if (G2 < G) G = G2;
@@ -582,7 +579,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     const size_t o_seed = off; off += up((size_t)k * 8);
     const size_t o_pmove = off; off += up((size_t)k * 4);
     char* ws = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, s);
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&ws), off, s);
     if (e != cudaSuccess) return cuda_status(e);
     fsc_status rc = FSC_OK;
     KmDevStats* st = reinterpret_cast<KmDevStats*>(ws + o_hdr);
@@ -667,7 +664,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
             }
         }
     } while (0);
-    cudaError_t ef = cudaFreeAsync(ws, s);
+    cudaError_t ef = pool_free(ws, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (ef != cudaSuccess) return cuda_status(ef);
     return rc;
@@ -704,13 +701,13 @@ extern "C" fsc_status fsc_cluster(const fsc_graph* g, int k, int l, int t, uint6
     const int LP = pad_l(l);
     cudaStream_t s = as_stream(stream);
     float* emb = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&emb), (size_t)g->n * LP * 4, s);
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&emb), (size_t)g->n * LP * 4, s);
     if (e != cudaSuccess) return cuda_status(e);
     fsc_kmeans_stats local{};
     fsc_status rc = fsc_embed(g, l, t, seed, store, emb, opts, stream);
     if (rc == FSC_OK)
         rc = fsc_kmeans(emb, g->n, l, LP, k, seed, max_iter, labels, nullptr, nullptr, stats ? stats : &local, stream);
-    cudaError_t ef = cudaFreeAsync(emb, s);
+    cudaError_t ef = pool_free(emb, s);
     if (rc == FSC_OK && ef != cudaSuccess) rc = cuda_status(ef);
     if (rc == FSC_OK) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_status(e);
@@ -770,8 +767,6 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
         (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes + (size_t)k * 4;
     auto kpp = k_kmeanspp<LP>;
     auto lly = k_lloyd<LP>;
-    FSC_CUDA(cudaFuncSetAttribute(kpp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kpp_smem));
-    FSC_CUDA(cudaFuncSetAttribute(lly, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lloyd_smem));
     int G = coop_blocks(kpp, kpp_smem);
     const int G2 = coop_blocks(lly, lloyd_smem);
     if (G2 < G) G = G2;

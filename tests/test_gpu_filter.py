@@ -161,15 +161,37 @@ def test_trained_filter_gains_over_plain_method_on_held_out_graphs(torch):
 
 
 def test_filtered_clustering_recovers_sbm(torch):
-    """Algorithm 2 with the learned filter (bf16 basis) clusters an SBM as well as the plain method."""
+    """Algorithm 2 with the learned filter (8 sparse products, float32 basis) against the plain method
+    with t = ceil(log2 n) = 17 products (oracle, float64).
+
+    Both are taken the usual k-means way, best of three restarts by inertia: a single k-means++
+    draw lands in a merged-cluster local optimum on this graph for the exact projector P X too,
+    so one-seed ARIs differ by 0.06 between equally good embeddings.  The scale-invariant
+    leakage ||(I - P) Y||^2 / ||P Y||^2 of the filtered block (P the top-k eigenprojector of M)
+    must stay within twice that of M^17 X.
+    """
     import paper_2310_10939_gb300 as fsc
     assert _weights_available(), "trained filter weights are missing"
     params = fsc.load_filter_params()
     g = W.sbm_by_degree(100_000, 20, 30.0, 3.0, seed=31)
     G = fsc.Graph.from_workload(g)
-    lab_f, st = fsc.cluster_filtered(G, 20, 5, 31, params, store=fsc.BF16)
-    l, t = 5, 17
-    ref = ocluster.fast_spectral_cluster(g, 20, l, t, 31)
-    a_f = metrics.ari(lab_f.cpu().numpy(), g.labels)
-    a_ref = metrics.ari(ref["labels"], g.labels)
-    assert a_f >= a_ref - 0.01, (a_f, a_ref)
+    k, l, t = 20, 5, 17
+    runs_f, runs_p = [], []
+    for seed in (31, 32, 33):
+        lab_f, st = fsc.cluster_filtered(G, k, l, seed, params, store=fsc.F32)
+        runs_f.append((st["inertia"], metrics.ari(lab_f.cpu().numpy(), g.labels)))
+        ref = ocluster.fast_spectral_cluster(g, k, l, t, seed)
+        runs_p.append((ref["inertia"], metrics.ari(ref["labels"], g.labels)))
+    a_f, a_p = min(runs_f)[1], min(runs_p)[1]
+    assert a_f >= a_p - 0.01, (runs_f, runs_p)
+
+    emb, _, _ = fsc.filter_embed(G, l, k, 31, params=params, store=fsc.F32)
+    dm = spectral.inv_sqrt_degrees(spectral.degrees(g))[:, None]
+    Yf = emb.cpu().numpy()[:, :l].astype(np.float64) / dm
+    Yp = spectral.power_method(spectral.signless_laplacian(g), gaussian_block(g.n, l, 31), t)
+
+    def leak(Y):
+        PY = fl.top_projection(g, k, Y)
+        return float(((Y - PY) ** 2).sum() / (PY ** 2).sum())
+
+    assert leak(Yf) <= 2.0 * leak(Yp), (leak(Yf), leak(Yp))
