@@ -287,36 +287,45 @@ def gpu_arm(args, w, rank, world, local_rank):
 
 
 def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
-    """The same clustering with bf16 iterates, and with the learned degree-8 filter (float32 basis):
-    ms per clustering (create_graph + cluster) and ARI against the planted labels."""
+    """The same clustering with bf16 iterates, and with the learned degree-8 filter (float32 and
+    float16 basis): ms per clustering (create_graph + cluster), ARI against the planted labels,
+    and for the filter the energy guard's ratio and whether it fell back to the plain method."""
     import torch
     import paper_2310_10939_gb300 as fsc
     from paper_2310_10939_gb300 import metrics as pm
     out = {}
     params = fsc.load_filter_params() if os.path.exists(fsc.FILTER_WEIGHTS) else None
-    runs = {"plain_bf16": lambda G: fsc.cluster(G, k, l, t, seed, store=fsc.BF16, rescale=True)[0]}
+
+    def plain(G):
+        return fsc.cluster(G, k, l, t, seed, store=fsc.BF16, rescale=True)[0], None
+
+    runs = {"plain_bf16": plain}
     if params is not None:
-        runs["learned_filter_f32"] = lambda G: fsc.cluster_filtered(G, k, l, seed, params, store=fsc.F32)[0]
+        runs["learned_filter_f32"] = lambda G: fsc.cluster_filtered(G, k, l, seed, params, store=fsc.F32)
+        runs["learned_filter_f16"] = lambda G: fsc.cluster_filtered(G, k, l, seed, params, store=fsc.F16)
     for name, fn in runs.items():
         for _ in range(3):
             G = fsc.Graph(rp, col, wt)
             fn(G)
             G.close()
         times = []
-        lab = None
+        lab = info = None
         for _ in range(steps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             G = fsc.Graph(rp, col, wt)
-            lab = fn(G)
+            lab, info = fn(G)
             G.close()
             b.record()
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b))
-        out[name] = {"ms": round(float(np.mean(times)), 4), "ari_vs_planted": round(pm.ari(lab.cpu().numpy(), g.labels), 4)}
+        rec = {"ms": round(float(np.mean(times)), 4), "ari_vs_planted": round(pm.ari(lab.cpu().numpy(), g.labels), 4)}
+        if info is not None:
+            rec.update(energy_ratio=round(info["filter_energy_ratio"], 4), fallback=int(info["fallback"]))
+        out[name] = rec
     if params is None:
-        out["learned_filter_f32"] = "weights file missing"
+        out["learned_filter"] = "weights file missing"
     return out
 
 

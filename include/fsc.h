@@ -49,7 +49,8 @@ typedef enum fsc_status {
 
 typedef enum fsc_dtype {
     FSC_F32 = 0,                /* power-iteration block stored in float32 */
-    FSC_BF16 = 1                /* stored in bfloat16, accumulated in float32 */
+    FSC_BF16 = 1,               /* stored in bfloat16, accumulated in float32 */
+    FSC_F16 = 2                 /* stored in float16 (learned-filter basis only), accumulated in float32 */
 } fsc_dtype;
 
 /* fsc_create_graph flags */
@@ -285,13 +286,22 @@ fsc_status fsc_batch_destroy(fsc_batch* batch);
  *   X the same start block as fsc_embed(seed).  params: device MLP parameters, or NULL when
  *   coeffs_override (device, 9 floats) gives the coefficients.  feats_out (16) and coeffs_out
  *   (9) are optional device outputs.  opts: threads_per_row and the events bracketing the 8
- *   sparse steps (flags ignored).  store is the type the basis T_j X is held in: FSC_F32 is
- *   the working choice.  The coefficients alternate in sign and cancel the bulk of the
- *   spectrum, so rounding in the basis does not cancel with it and the recurrence carries it
- *   forward: with FSC_BF16 the leakage ||(I - P) Y||^2 / ||P Y||^2 of an SBM (n = 1e5, k = 20,
- *   mean degree 33) rises from 1.3e-3 to 1.7e-2 and k-means lands in worse optima.
- *   Asynchronous.
- * fsc_cluster_filtered: fsc_filter_embed then fsc_kmeans; synchronous.
+ *   sparse steps (flags ignored).  store is the type the basis T_j X is held in: FSC_F32, or
+ *   FSC_F16 for half the bytes.  The coefficients alternate in sign and cancel the bulk of
+ *   the spectrum, so rounding in the basis does not cancel with it and the recurrence carries
+ *   it forward: FSC_BF16 (8-bit significand) raises the leakage ||(I - P) Y||^2 / ||P Y||^2
+ *   of an SBM (n = 1e5, k = 20, mean degree 33) from 1.3e-3 to 1.7e-2 and k-means lands in
+ *   worse optima; FSC_F16 (11-bit significand, 64x smaller squared error) keeps it near the
+ *   float32 value.  FSC_F16 needs the entries of D^-1/2 X inside float16's normal range
+ *   (about 6e-5 .. 6e4): degrees between about 1e-8 and 1e8.  energy_out (device double,
+ *   optional) receives ||p(M) X||^2 in x-space (sum over v of d(v) |y_v|^2).  Asynchronous.
+ * fsc_cluster_filtered: fsc_filter_embed then fsc_kmeans; synchronous.  Guard (the plain
+ *   method as fallback): for Gaussian X, E ||P X||^2 = l k, so a good filter gives
+ *   ||p(M) X||^2 / (l k) near 1 and leakage into the bulk raises it; above
+ *   1.25 + 3 sqrt(2 / (l k)) (leakage beyond a quarter of the signal, allowing for the chi^2
+ *   spread of ||P X||^2) the block is recomputed by fsc_embed with t = ceil(log2 n) (float32,
+ *   or bfloat16 with rescaling for the 2-byte stores) and that block is clustered instead.
+ *   opts->flags may hold FSC_FILTER_NO_FALLBACK.  report (optional) tells what happened.
  * fsc_mlp_forward: coefficients (batch x 9) of features (batch x 16), device arrays.
  * fsc_mlp_train_step: adds the gradient of the mean loss c^T Gn c - 2 bn^T c + 1 over the
  *   batch (feats batch x 16, Gn batch x 81, bn batch x 9, device float32) to grad (5833);
@@ -299,12 +309,21 @@ fsc_status fsc_batch_destroy(fsc_batch* batch);
  *   for bias correction, weight decay added to the gradient) and zeroes grad.  loss_out
  *   (device scalar) receives the mean loss, may be NULL.  Asynchronous.
  */
+typedef struct fsc_filter_report {
+    double energy_ratio;        /* ||p(M) X||^2 / (l k), x-space energy of the filtered block */
+    double threshold;           /* the ratio above which the plain method replaces the filter */
+    int32_t fallback;           /* 1: the labels come from the plain power method */
+    int32_t fallback_t;         /* its number of iterations, ceil(log2 n) */
+} fsc_filter_report;
+
+#define FSC_FILTER_NO_FALLBACK 0x100u   /* fsc_embed_opts.flags bit for fsc_cluster_filtered */
+
 fsc_status fsc_filter_embed(const fsc_graph* g, int l, int k, uint64_t seed, fsc_dtype store, const float* params,
                             const float* coeffs_override, float* emb, float* feats_out, float* coeffs_out,
-                            const fsc_embed_opts* opts, void* stream);
+                            double* energy_out, const fsc_embed_opts* opts, void* stream);
 fsc_status fsc_cluster_filtered(const fsc_graph* g, int k, int l, uint64_t seed, fsc_dtype store, const float* params,
-                                int max_iter, int32_t* labels, fsc_kmeans_stats* stats, const fsc_embed_opts* opts,
-                                void* stream);
+                                int max_iter, int32_t* labels, fsc_kmeans_stats* stats, fsc_filter_report* report,
+                                const fsc_embed_opts* opts, void* stream);
 fsc_status fsc_mlp_forward(const float* params, const float* feats, int batch, float* coeffs, void* stream);
 fsc_status fsc_mlp_train_step(float* params, float* grad, float* adam_m, float* adam_v, int step, float lr,
                               float weight_decay, const float* feats, const float* Gn, const float* bn, int batch,

@@ -8,7 +8,11 @@ loss(c) = c^T Gn c - 2 bn^T c + 1.  Also stored: the loss of the plain power met
 t = 8 and t = 22 (Chebyshev coefficients of gamma^t are exact only for t <= 8, so t = 22 is
 evaluated directly), and the best possible degree-8 loss 1 - bn^T Gn^-1 bn.
 
-Usage: python -m oracle.make_filter_data [--graphs 3000] [--workers 8]
+With --large the graphs are SBMs with n = 10^5 .. 2^21 and k = 2 .. 24 (written to
+train_data_large.npz): there n / k, the number of bulk eigen-directions per signal one, reaches
+10^5, the range in which the filter must suppress the bulk by 10^-3 or more.
+
+Usage: python -m oracle.make_filter_data [--graphs 3000] [--workers 8] [--large]
 """
 from __future__ import annotations
 
@@ -22,6 +26,7 @@ import numpy as np
 
 OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "paper_2310_10939_gb300", "filter", "train_data.npz")
+OUT_LARGE = OUT.replace("train_data.npz", "train_data_large.npz")
 
 
 def _draw(i: int, base_seed: int):
@@ -37,6 +42,16 @@ def _draw(i: int, base_seed: int):
     k = int(rng.integers(3, 21))
     dim = int(rng.choice([8, 16, 32]))
     return ("knn", npts, k, dim, 10, int(rng.integers(1, 2**31)))
+
+
+def _draw_large(i: int, base_seed: int):
+    rng = np.random.default_rng(base_seed * 1_000_003 + 500_000_000 + i)
+    n = int(round(math.exp(rng.uniform(math.log(100_000), math.log(2 ** 21)))))
+    kmax = min(24, n // 2000)
+    k = int(round(math.exp(rng.uniform(math.log(2), math.log(kmax)))))
+    deg_in = float(rng.uniform(10, 40))
+    deg_out = deg_in * float(rng.uniform(0.03, 0.15))
+    return ("sbm", n, k, deg_in, deg_out, int(rng.integers(1, 2**31)))
 
 
 def _record(spec):
@@ -68,12 +83,18 @@ def main():
     ap.add_argument("--graphs", type=int, default=3000)
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 4)
     ap.add_argument("--seed", type=int, default=2023)
-    ap.add_argument("--out", default=OUT)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--large", action="store_true")
     args = ap.parse_args()
-    specs = [_draw(i, args.seed) for i in range(args.graphs)]
+    if args.out is None:
+        args.out = OUT_LARGE if args.large else OUT
+    draw = _draw_large if args.large else _draw
+    specs = [draw(i, args.seed) for i in range(args.graphs)]
+    if args.large:   # largest first, so the pool ends on short jobs
+        specs.sort(key=lambda sp: -sp[1])
     t0 = time.time()
     with mp.get_context("spawn").Pool(args.workers) as pool:
-        recs = pool.map(_record, specs, chunksize=4)
+        recs = pool.map(_record, specs, chunksize=1 if args.large else 4)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     np.savez_compressed(
         args.out,

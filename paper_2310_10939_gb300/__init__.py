@@ -21,13 +21,14 @@ import os
 __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
     "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
-    "F32", "BF16", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
+    "F32", "BF16", "F16", "FILTER_NO_FALLBACK", "release_cached_memory", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
     "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
 
-F32, BF16 = 0, 1
+F32, BF16, F16 = 0, 1, 2
+FILTER_NO_FALLBACK = 0x100
 VALIDATE_SYMMETRY = 0x1
 EMBED_RESCALE = 0x1
 BATCH_AUTOTUNE = 0x2
@@ -57,6 +58,11 @@ class KmeansStats(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class FilterReport(C.Structure):
+    _fields_ = [("energy_ratio", C.c_double), ("threshold", C.c_double), ("fallback", C.c_int32),
+                ("fallback_t", C.c_int32)]
 
 
 class BatchDesc(C.Structure):
@@ -104,9 +110,9 @@ def lib() -> C.CDLL:
         for name in ("fsc_autotune", "fsc_batch_create", "fsc_batch_run", "fsc_batch_results", "fsc_batch_destroy",
                      "fsc_batch_embedding"):
             getattr(L, name).restype = i32
-        L.fsc_filter_embed.argtypes = [vp, i32, i32, u64, i32, vp, vp, vp, vp, vp, C.POINTER(EmbedOpts), vp]
+        L.fsc_filter_embed.argtypes = [vp, i32, i32, u64, i32, vp, vp, vp, vp, vp, vp, C.POINTER(EmbedOpts), vp]
         L.fsc_cluster_filtered.argtypes = [vp, i32, i32, u64, i32, vp, i32, vp, C.POINTER(KmeansStats),
-                                           C.POINTER(EmbedOpts), vp]
+                                           C.POINTER(FilterReport), C.POINTER(EmbedOpts), vp]
         L.fsc_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
         L.fsc_mlp_train_step.argtypes = [vp, vp, vp, vp, i32, C.c_float, C.c_float, vp, vp, vp, i32, vp, i32, vp]
         for name in ("fsc_filter_embed", "fsc_cluster_filtered", "fsc_mlp_forward", "fsc_mlp_train_step"):
@@ -432,8 +438,9 @@ def load_filter_params(path: str | None = None, device="cuda"):
 
 
 def filter_embed(g: Graph, l: int, k: int, seed: int, params=None, coeffs=None, store: int = F32, out=None,
-                 threads_per_row: int = 0, events=None, stream=None):
-    """fsc_filter_embed: returns (embedding n x pad_l(l), features (16), coefficients (9)) device tensors."""
+                 threads_per_row: int = 0, events=None, energy=None, stream=None):
+    """fsc_filter_embed: returns (embedding n x pad_l(l), features (16), coefficients (9)) device tensors.
+    ``energy`` (optional float64 CUDA tensor of one element) receives ||p(M) X||^2 (x-space)."""
     torch = _torch()
     dev = g.row_ptr.device
     if out is None:
@@ -442,23 +449,32 @@ def filter_embed(g: Graph, l: int, k: int, seed: int, params=None, coeffs=None, 
     cf = torch.empty(9, dtype=torch.float32, device=dev)
     o = _opts(False, threads_per_row, events)
     _check(lib().fsc_filter_embed(g.handle, int(l), int(k), int(seed) & (2**64 - 1), int(store), _ptr(params),
-                                  _ptr(coeffs), _ptr(out), _ptr(feats), _ptr(cf), C.byref(o), _stream(stream)),
+                                  _ptr(coeffs), _ptr(out), _ptr(feats), _ptr(cf), _ptr(energy), C.byref(o),
+                                  _stream(stream)),
            "fsc_filter_embed")
     return out, feats, cf
 
 
 def cluster_filtered(g: Graph, k: int, l: int, seed: int, params, store: int = F32, max_iter: int = 100,
-                     labels=None, threads_per_row: int = 0, events=None, stream=None):
-    """fsc_cluster_filtered: Algorithm 2 with the learned filter in place of M^t.  Returns (labels, stats)."""
+                     labels=None, threads_per_row: int = 0, events=None, fallback: bool = True, stream=None):
+    """fsc_cluster_filtered: Algorithm 2 with the learned filter in place of M^t.  Returns (labels, stats);
+    stats also holds the guard's report (filter_energy_ratio, filter_threshold, fallback, fallback_t)."""
     torch = _torch()
     if labels is None:
         labels = torch.empty(g.n, dtype=torch.int32, device=g.row_ptr.device)
     st = KmeansStats()
+    rep = FilterReport()
     o = _opts(False, threads_per_row, events)
+    if not fallback:
+        o.flags |= FILTER_NO_FALLBACK
     _check(lib().fsc_cluster_filtered(g.handle, int(k), int(l), int(seed) & (2**64 - 1), int(store), _ptr(params),
-                                      int(max_iter), _ptr(labels), C.byref(st), C.byref(o), _stream(stream)),
+                                      int(max_iter), _ptr(labels), C.byref(st), C.byref(rep), C.byref(o),
+                                      _stream(stream)),
            "fsc_cluster_filtered")
-    return labels, st.as_dict()
+    out = st.as_dict()
+    out.update(filter_energy_ratio=rep.energy_ratio, filter_threshold=rep.threshold, fallback=rep.fallback,
+               fallback_t=rep.fallback_t)
+    return labels, out
 
 
 def mlp_forward(params, feats, stream=None):

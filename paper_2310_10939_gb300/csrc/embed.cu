@@ -82,8 +82,9 @@ cudaError_t launch_init(int LP, int n, int l, unsigned long long seed, const flo
 
 cudaError_t launch_init_any(int LP, int n, int l, unsigned long long seed, const float* dinv, void* out, int store,
                             cudaStream_t s) {
-    return store == FSC_F32 ? launch_init<float>(LP, n, l, seed, dinv, static_cast<float*>(out), nullptr, s)
-                            : launch_init<__nv_bfloat16>(LP, n, l, seed, dinv, static_cast<__nv_bfloat16*>(out), nullptr, s);
+    if (store == FSC_F32) return launch_init<float>(LP, n, l, seed, dinv, static_cast<float*>(out), nullptr, s);
+    if (store == FSC_F16) return launch_init<__half>(LP, n, l, seed, dinv, static_cast<__half*>(out), nullptr, s);
+    return launch_init<__nv_bfloat16>(LP, n, l, seed, dinv, static_cast<__nv_bfloat16*>(out), nullptr, s);
 }
 
 // ---- lanes per row: explicit request > autotuned table > degree heuristic ------------------

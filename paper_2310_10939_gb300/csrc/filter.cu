@@ -230,10 +230,13 @@ __global__ void __launch_bounds__(256) k_filter_coeffs(const float* __restrict__
 
 template <int LP, typename TS>
 __global__ void __launch_bounds__(256) k_cheb_combine(int n, const TS* __restrict__ T, size_t stride,
-                                                      const float* __restrict__ coeffs, float* __restrict__ out) {
+                                                      const float* __restrict__ coeffs, const double* __restrict__ deg,
+                                                      float* __restrict__ out, double* __restrict__ energy) {
     __shared__ float s_c[NCOEF];
+    __shared__ float s_e[8];
     if (threadIdx.x < NCOEF) s_c[threadIdx.x] = coeffs[threadIdx.x];
     __syncthreads();
+    float e_loc = 0.f;   // sum over this thread's rows of d(v) |y_v|^2 (x-space energy)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         float acc[LP];
 #pragma unroll
@@ -246,7 +249,36 @@ __global__ void __launch_bounds__(256) k_cheb_combine(int n, const TS* __restric
             for (int c = 0; c < LP; ++c) acc[c] = fmaf(s_c[j], v[c], acc[c]);
         }
         store_row<LP, float>(out + (size_t)i * LP, acc);
+        if (energy) {
+            float q = 0.f;
+#pragma unroll
+            for (int c = 0; c < LP; ++c) q = fmaf(acc[c], acc[c], q);
+            e_loc = fmaf((float)deg[i], q, e_loc);
+        }
     }
+    if (energy) {
+        for (int off = 16; off > 0; off >>= 1) e_loc += __shfl_xor_sync(0xffffffffu, e_loc, off);
+        if ((threadIdx.x & 31) == 0) s_e[threadIdx.x >> 5] = e_loc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)s_e[w];
+            atomicAdd(energy, t);
+        }
+    }
+}
+
+template <typename TS>
+static cudaError_t launch_combine(int LP, unsigned blocks, int n, const void* T, size_t stride, const float* coeffs,
+                                  const double* deg, float* out, double* energy, cudaStream_t s) {
+    const TS* t = static_cast<const TS*>(T);
+    switch (LP) {
+        case 1: k_cheb_combine<1, TS><<<blocks, 256, 0, s>>>(n, t, stride, coeffs, deg, out, energy); break;
+        case 2: k_cheb_combine<2, TS><<<blocks, 256, 0, s>>>(n, t, stride, coeffs, deg, out, energy); break;
+        case 4: k_cheb_combine<4, TS><<<blocks, 256, 0, s>>>(n, t, stride, coeffs, deg, out, energy); break;
+        default: k_cheb_combine<8, TS><<<blocks, 256, 0, s>>>(n, t, stride, coeffs, deg, out, energy); break;
+    }
+    return cudaGetLastError();
 }
 
 // ---- training: one block of 64 threads per graph of the minibatch ------------------------------------
@@ -352,9 +384,11 @@ extern "C" fsc_status fsc_mlp_train_step(float* params, float* grad, float* adam
 
 extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64_t seed, fsc_dtype store,
                                        const float* params, const float* coeffs_override, float* emb, float* feats_out,
-                                       float* coeffs_out, const fsc_embed_opts* opts, void* stream) {
+                                       float* coeffs_out, double* energy_out, const fsc_embed_opts* opts,
+                                       void* stream) {
     fsc_graph* g = const_cast<fsc_graph*>(gc);
-    if (!g || !emb || l < 1 || l > 8 || k < 1 || (int64_t)k > g->n || (store != FSC_F32 && store != FSC_BF16))
+    if (!g || !emb || l < 1 || l > 8 || k < 1 || (int64_t)k > g->n ||
+        (store != FSC_F32 && store != FSC_BF16 && store != FSC_F16))
         return FSC_ERR_INVALID_ARG;
     if (!params && !coeffs_override) return FSC_ERR_INVALID_ARG;
     const int LP = pad_l(l);
@@ -393,6 +427,7 @@ extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64
         a.mom = j < 4 ? mom + (size_t)j * 3 * blocks : nullptr;
         a.first = j == 0;
         if (store == FSC_F32) FSC_CUDA(launch_cheb_any<float>(LP, G, g->w != nullptr, a, (int)blocks, s));
+        else if (store == FSC_F16) FSC_CUDA(launch_cheb_any<__half>(LP, G, g->w != nullptr, a, (int)blocks, s));
         else FSC_CUDA(launch_cheb_any<__nv_bfloat16>(LP, G, g->w != nullptr, a, (int)blocks, s));
     }
     if (opts && opts->ev_spmm_end) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_end, s));
@@ -402,36 +437,54 @@ extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64
     long long cb = ((long long)n + 255) / 256;
     if (cb > cap * 2) cb = cap * 2;
     const size_t stride = blk / es;
-    switch (LP) {
-        case 1: store == FSC_F32 ? k_cheb_combine<1, float><<<(unsigned)cb, 256, 0, s>>>(n, (const float*)ws, stride, coeffs, emb)
-                                 : k_cheb_combine<1, __nv_bfloat16><<<(unsigned)cb, 256, 0, s>>>(n, (const __nv_bfloat16*)ws, stride, coeffs, emb); break;
-        case 2: store == FSC_F32 ? k_cheb_combine<2, float><<<(unsigned)cb, 256, 0, s>>>(n, (const float*)ws, stride, coeffs, emb)
-                                 : k_cheb_combine<2, __nv_bfloat16><<<(unsigned)cb, 256, 0, s>>>(n, (const __nv_bfloat16*)ws, stride, coeffs, emb); break;
-        case 4: store == FSC_F32 ? k_cheb_combine<4, float><<<(unsigned)cb, 256, 0, s>>>(n, (const float*)ws, stride, coeffs, emb)
-                                 : k_cheb_combine<4, __nv_bfloat16><<<(unsigned)cb, 256, 0, s>>>(n, (const __nv_bfloat16*)ws, stride, coeffs, emb); break;
-        default: store == FSC_F32 ? k_cheb_combine<8, float><<<(unsigned)cb, 256, 0, s>>>(n, (const float*)ws, stride, coeffs, emb)
-                                  : k_cheb_combine<8, __nv_bfloat16><<<(unsigned)cb, 256, 0, s>>>(n, (const __nv_bfloat16*)ws, stride, coeffs, emb); break;
-    }
-    FSC_CUDA(cudaGetLastError());
+    if (energy_out) FSC_CUDA(cudaMemsetAsync(energy_out, 0, sizeof(double), s));
+    if (store == FSC_F32) FSC_CUDA(launch_combine<float>(LP, (unsigned)cb, n, ws, stride, coeffs, g->deg, emb, energy_out, s));
+    else if (store == FSC_F16) FSC_CUDA(launch_combine<__half>(LP, (unsigned)cb, n, ws, stride, coeffs, g->deg, emb, energy_out, s));
+    else FSC_CUDA(launch_combine<__nv_bfloat16>(LP, (unsigned)cb, n, ws, stride, coeffs, g->deg, emb, energy_out, s));
     if (coeffs_out) FSC_CUDA(cudaMemcpyAsync(coeffs_out, coeffs, NCOEF * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return FSC_OK;
 }
 
 extern "C" fsc_status fsc_cluster_filtered(const fsc_graph* g, int k, int l, uint64_t seed, fsc_dtype store,
                                            const float* params, int max_iter, int32_t* labels,
-                                           fsc_kmeans_stats* stats, const fsc_embed_opts* opts, void* stream) {
+                                           fsc_kmeans_stats* stats, fsc_filter_report* report,
+                                           const fsc_embed_opts* opts, void* stream) {
     if (!g || !labels || !params || l < 1 || l > 8 || k < 1 || (int64_t)k > g->n) return FSC_ERR_INVALID_ARG;
     const int LP = pad_l(l);
     cudaStream_t s = as_stream(stream);
+    const bool guard = !(opts && (opts->flags & FSC_FILTER_NO_FALLBACK));
+    fsc_embed_opts eo{};
+    if (opts) eo = *opts;
+    eo.flags = 0;
     float* emb = nullptr;
-    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&emb), (size_t)g->n * LP * 4, s);
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&emb), (size_t)g->n * LP * 4 + 256, s);
     if (e != cudaSuccess) return cuda_status(e);
+    double* d_energy = reinterpret_cast<double*>(reinterpret_cast<char*>(emb) + (((size_t)g->n * LP * 4 + 127) & ~(size_t)127));
     fsc_kmeans_stats local{};
-    fsc_status rc = fsc_filter_embed(g, l, k, seed, store, params, nullptr, emb, nullptr, nullptr, opts, stream);
+    fsc_filter_report rep{};
+    rep.threshold = 1.25 + 3.0 * sqrt(2.0 / ((double)l * (double)k));
+    fsc_status rc = fsc_filter_embed(g, l, k, seed, store, params, nullptr, emb, nullptr, nullptr, d_energy, &eo, stream);
+    if (rc == FSC_OK) {
+        double energy = 0.0;
+        if ((e = cudaMemcpyAsync(&energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            rc = cuda_status(e);
+        rep.energy_ratio = energy / ((double)l * (double)k);
+    }
+    if (rc == FSC_OK && guard && !(rep.energy_ratio <= rep.threshold)) {
+        int lp = 0, t = 0;
+        fsc_default_params(g->n, k, 0, &lp, &t);
+        rep.fallback = 1;
+        rep.fallback_t = t;
+        fsc_embed_opts po = eo;
+        po.flags = store == FSC_F32 ? 0u : FSC_EMBED_RESCALE;
+        rc = fsc_embed(g, l, t, seed, store == FSC_F32 ? FSC_F32 : FSC_BF16, emb, &po, stream);
+    }
     if (rc == FSC_OK)
         rc = fsc_kmeans(emb, g->n, l, LP, k, seed, max_iter, labels, nullptr, nullptr, stats ? stats : &local, stream);
     cudaError_t ef = pool_free(emb, s);
     if (rc == FSC_OK && ef != cudaSuccess) rc = cuda_status(ef);
     if (rc == FSC_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_status(e);
+    if (report) *report = rep;
     return rc;
 }

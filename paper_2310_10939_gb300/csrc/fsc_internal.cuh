@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -61,11 +62,13 @@ template <> struct Chunk<16> { using type = uint4; };
 
 __device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_f32(__half x) { return __half2float(x); }
 template <typename T> __device__ __forceinline__ T from_f32(float x);
 template <> __device__ __forceinline__ float from_f32<float>(float x) { return x; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float x) {
     return __float2bfloat16_rn(x);
 }
+template <> __device__ __forceinline__ __half from_f32<__half>(float x) { return __float2half_rn(x); }
 
 template <int LP, typename T>
 __device__ __forceinline__ void load_row(const T* __restrict__ p, float (&v)[LP]) {
@@ -132,8 +135,8 @@ constexpr unsigned long long STREAM_X0 = 1, STREAM_KMEANSPP = 2;
 
 // ---- bounded grid-wide barrier for cooperative launches --------------------------------
 struct GridBarrier {
-    unsigned int count;
-    unsigned int generation;
+    unsigned int count;        // arrivals so far (starts at 0)
+    unsigned int reserved;
 };
 
 __device__ __forceinline__ long long global_ns() {
@@ -142,42 +145,38 @@ __device__ __forceinline__ long long global_ns() {
     return (long long)t;
 }
 
-// All blocks of a cooperative launch call this.  Returns false (for every thread of the block)
-// if the device error word is set or the wait exceeded `limit_ns`; the caller then returns.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, long long limit_ns, int stall = 0) {
+// All blocks of a cooperative launch call this, each with its own count of the barriers it has
+// passed (`epoch`, starting at 0; the counter starts at 0 too).  Arrivals only ever increase the
+// counter, so barrier e releases once it reaches e * gridDim.x and no block has to reset or
+// re-arm anything.  Returns false (for every thread of the block) if the device error word is
+// set or the wait exceeded `limit_ns`; the caller then returns.  With `stall` set, block 0
+// never arrives (test hook for the timeout path).
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, long long limit_ns, int stall,
+                                          unsigned& epoch) {
     __shared__ int s_ok;
-    __threadfence();
     __syncthreads();
+    epoch += 1;
     if (threadIdx.x == 0) {
-        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->generation);
         cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
         cuda::atomic_ref<int, cuda::thread_scope_device> st(*status);
         int ok = st.load(cuda::memory_order_relaxed) == 0;
         if (ok) {
-            const unsigned int g = gen.load(cuda::memory_order_acquire);
-            const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-            if (arrived == gridDim.x - 1 && !stall) {
-                cnt.store(0u, cuda::memory_order_relaxed);
-                gen.fetch_add(1u, cuda::memory_order_release);
-            } else if (arrived == gridDim.x - 1 && stall) {
-                // injected failure: the barrier is never released; this block records a timeout
-                st.fetch_or(ST_TIMEOUT, cuda::memory_order_relaxed);
-                ok = 0;
-            } else {
-                const long long t0 = global_ns();
-                unsigned spins = 0;
-                while (gen.load(cuda::memory_order_acquire) == g) {
-                    if (st.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
-                    if (++spins > 32) __nanosleep(64);
-                    if ((spins & 63u) == 0 && global_ns() - t0 > limit_ns) {
-                        st.fetch_or(ST_TIMEOUT, cuda::memory_order_relaxed);
-                        ok = 0;
-                        break;
-                    }
+            const unsigned target = epoch * gridDim.x;
+            __threadfence();
+            if (!(stall && blockIdx.x == 0)) cnt.fetch_add(1u, cuda::memory_order_release);
+            const long long t0 = global_ns();
+            unsigned spins = 0;
+            while ((int)(cnt.load(cuda::memory_order_acquire) - target) < 0) {
+                if (st.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
+                if (++spins > 64) __nanosleep(32);
+                if ((spins & 15u) == 0 && global_ns() - t0 > limit_ns) {
+                    st.fetch_or(ST_TIMEOUT, cuda::memory_order_relaxed);
+                    ok = 0;
+                    break;
                 }
             }
+            __threadfence();
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

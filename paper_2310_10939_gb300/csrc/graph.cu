@@ -91,8 +91,10 @@ int kernel_occupancy(const void* fn, int threads, size_t smem) {
     const auto key = std::make_tuple(dev, fn, threads, smem);
     auto it = g_occ.find(key);
     if (it != g_occ.end()) return it->second;
+    // the opt-in limit covers dynamic bytes on top of the kernel's static shared memory, so it is
+    // raised for every size above the largest one set so far
     size_t& attr = g_smem_attr[std::make_pair(dev, fn)];
-    if (smem > 48 * 1024 && smem > attr) {
+    if (smem > attr) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
         attr = smem;
     }

@@ -52,6 +52,7 @@ struct KppArgs {
 
 template <int LP>
 __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
+    unsigned epoch = 0;   // grid barriers passed
     extern __shared__ int s_chosen[];   // k entries
     __shared__ float s_c[LP];
     __shared__ long long s_red[KM_WARPS];
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         __syncthreads();
         if (tid == 0 && s_amax) atomicMax(a.amax, s_amax);
     }
-    if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
+    if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
     const float A = __uint_as_float(__ldcg(a.amax));
     const Scales sc = scales_for(A, n, a.l);
 
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             }
         }
         if (tid == 0) bs[b] = bacc;
-        if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
+        if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
 
         // ---- selection (identical in every block, exact integer arithmetic)
         for (int q = tid; q < G; q += KM_THREADS) s_pref[q] = __ldcg(bs + q);
@@ -243,16 +244,14 @@ struct LloydArgs {
     const float* X;
     int n, l, k, max_iter;
     int32_t* labels;
-    float* c32;
-    double* c64;
-    long long* partials;
-    long long* inertia_part;
-    int* changed_part;
+    float* c32;                 // in: the k-means++ centres; out: the final centroids (float32)
+    double* c64;                // out: the final centroids (float64)
+    unsigned long long* tot;    // 3 accumulators of k*(LP+1) exact sums (coordinates, count), zeroed
+    unsigned long long* cnt3;   // 3 x (inertia sum, changed count, 2 unused), zeroed
     const unsigned* amax;
-    long long chunk;
+    long long chunk;            // points per block (a multiple of KM_PPT)
     int ntab;
     float* lbound;       // per point: lower bound on the distance to every other centroid (pruning)
-    float* pmove;        // per cluster: how far its centroid moved in the last update (rounded up)
     int prune;           // 1: skip the k-way scan of points whose bounds prove the label unchanged
     KmDevStats* st;
     GridBarrier* bar;
@@ -268,10 +267,44 @@ struct LloydArgs {
 // relative margin PRUNE_EPS, far above the float32 rounding of the distances (< 1e-6), so a
 // skipped point is exactly one the full scan would leave in place (no tie is possible).
 constexpr float PRUNE_EPS = 1e-5f;
+constexpr float PRUNE_GROW2 = (1.0f + PRUNE_EPS) * (1.0f + PRUNE_EPS);   // the test runs on squares
+
+// Settles point i: new label, lower bound, changed count, its float32 distance in the inertia and
+// its coordinates in the centroid sums (two-slot run cache in front of the warp's shared table;
+// slot 0 holds the most recent label).  Labels are written only when they change.
+template <int LP>
+__device__ __forceinline__ void lloyd_commit(const LloydArgs& a, long long i, const float (&x)[LP], int oldl, int lab,
+                                             float dist, float lbn, const Scales& sc, Slot<LP> (&sl)[2],
+                                             unsigned long long* tab, long long& inert, int& changed) {
+    if (a.prune) a.lbound[i] = lbn;
+    if (oldl != lab) {
+        ++changed;
+        a.labels[i] = lab;
+    }
+    inert += fixq(dist, sc.Sd);
+    if (sl[0].j != lab) {
+        if (sl[1].j == lab) {
+            const Slot<LP> t = sl[0];
+            sl[0] = sl[1];
+            sl[1] = t;
+        } else {
+            slot_flush<LP>(sl[1], tab);   // evict the older run
+            sl[1] = sl[0];
+            sl[0].j = lab;
+            sl[0].cnt = 0;
+#pragma unroll
+            for (int c = 0; c < LP; ++c) sl[0].s[c] = 0;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < LP; ++c) sl[0].s[c] += fixq(x[c], sc.Sx);
+    ++sl[0].cnt;
+}
 
 template <int LP>
 __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydArgs a) {
     extern __shared__ __align__(16) unsigned char km_smem[];
+    unsigned epoch = 0;   // grid barriers passed
     const int k = a.k;
     const int ntab = a.ntab;                              // private tables (warp w uses w % ntab)
     const size_t rowlen = (size_t)k * (LP + 1);
@@ -279,32 +312,41 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
     unsigned long long* s_tab =
         reinterpret_cast<unsigned long long*>(km_smem + (((size_t)k * LP * 4 + 15) & ~(size_t)15));
     float* s_sep = reinterpret_cast<float*>(s_tab + (size_t)ntab * rowlen);   // k floats
+    float* s_cn = reinterpret_cast<float*>(s_tab);   // new centroids, staged in the tables once they are summed
     __shared__ long long s_red[KM_WARPS];
     __shared__ int s_redi[KM_WARPS];
-    __shared__ long long s_tot[LP + 1];
-    __shared__ int s_stop, s_changed;
+    __shared__ long long s_inert;
+    __shared__ int s_changed;
     __shared__ unsigned s_pmax;
-    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ int s_qoff[KM_WARPS][KM_PPT * 32];
+    __shared__ int s_qold[KM_WARPS][KM_PPT * 32];
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
-    const long long chunk = a.chunk;
-    const long long lo = min(n, (long long)b * chunk), hi = min(n, lo + chunk);
+    const long long lo = min(n, (long long)b * a.chunk), hi = min(n, lo + a.chunk);   // this block's points
     const Scales sc = scales_for(__uint_as_float(__ldcg(a.amax)), n, a.l);
     unsigned long long* my_tab = s_tab + (size_t)(wid % ntab) * rowlen;
 
-    if (b == 0) {   // float64 masters of the k-means++ centres
-        for (int q = tid; q < k * LP; q += KM_THREADS) a.c64[q] = (double)__ldcg(a.c32 + q);
+    for (int q = tid; q < k * LP; q += KM_THREADS) {
+        const float v = __ldcg(a.c32 + q);
+        s_c[q] = v;
+        if (b == 0) a.c64[q] = (double)v;   // float64 masters of the k-means++ centres
     }
+    if (tid == 0) s_pmax = 0u;
+    __syncthreads();
+    // One grid barrier per iteration: blocks add their exact sums into the iteration's accumulator
+    // (one of three, used in rotation), and after the barrier every block forms all k centroids
+    // from it itself, so the centroids never travel through global memory between blocks.
     for (int it = 1; it <= a.max_iter; ++it) {
+        const int cur = it % 3;
+        unsigned long long* T = a.tot + (size_t)cur * rowlen;
         const bool pr = a.prune && it > 1;
-        for (int q = tid; q < k * LP; q += KM_THREADS) s_c[q] = __ldcg(a.c32 + q);
         for (size_t q = tid; q < (size_t)ntab * rowlen; q += KM_THREADS) s_tab[q] = 0ull;
         if (pr) {
             for (int q = tid; q < k; q += KM_THREADS) reinterpret_cast<unsigned*>(s_sep)[q] = 0x7f800000u;   // +inf
-            if (tid == 0) s_pmax = 0u;
         }
         __syncthreads();
         if (pr) {
-            // half the distance of each centroid to its nearest other centroid, and the largest move
+            // half the distance of each centroid to its nearest other centroid
             for (int q = tid; q < k * k; q += KM_THREADS) {
                 const int j = q / k, jj = q % k;
                 if (jj > j) {
@@ -316,7 +358,6 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
                     atomicMin(reinterpret_cast<unsigned*>(s_sep) + jj, d);
                 }
             }
-            for (int q = tid; q < k; q += KM_THREADS) atomicMax(&s_pmax, __float_as_uint(__ldcg(a.pmove + q)));
             __syncthreads();
             for (int q = tid; q < k; q += KM_THREADS) s_sep[q] = 0.5f * sqrtf(s_sep[q]) * (1.0f - PRUNE_EPS);
             __syncthreads();
@@ -324,7 +365,10 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
         const float pmax = pr ? __uint_as_float(s_pmax) * (1.0f + PRUNE_EPS) : 0.f;
         long long inert = 0;
         int changed = 0;
-        // ---- phase A: assignment of KM_PPT consecutive points per thread
+        // ---- phase A.  Each thread takes KM_PPT consecutive points of a tile and settles those
+        // its bounds prove unchanged; the others go to a per-warp queue that the warp then scans
+        // against all k centroids one point per lane, so no lane idles behind a neighbour's scan.
+        // Centroid sums are exact integers, so which lane adds a point changes no result.
         Slot<LP> sl[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -333,6 +377,8 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
 #pragma unroll
             for (int c = 0; c < LP; ++c) sl[q].s[c] = 0;
         }
+        int* qoff = s_qoff[wid];
+        int* qold = s_qold[wid];
         for (long long t0 = lo; t0 < hi; t0 += KM_TILE) {
             const long long i0 = t0 + (long long)KM_PPT * tid;
             float x[KM_PPT][LP];
@@ -351,181 +397,121 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
                     lbv[u] = 0.f;
                 }
             }
-            float best[KM_PPT], sec[KM_PPT], lbn[KM_PPT];
-            int bj[KM_PPT];
-            bool need[KM_PPT];
-            bool any = false;
+            int qn = 0;   // queue length (warp-uniform)
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
-                best[u] = __int_as_float(0x7f800000);
-                sec[u] = __int_as_float(0x7f800000);
-                bj[u] = 0;
-                need[u] = i0 + u < hi;
-                lbn[u] = 0.f;
-                if (pr && need[u]) {
+                bool need = i0 + u < hi;
+                if (pr && need) {
                     const int ca = old[u];
                     const float da = sqdist<LP>(x[u], s_c + ca * LP);
                     const float lw = fmaxf(0.f, lbv[u] - pmax);
-                    if (sqrtf(da) * (1.0f + PRUNE_EPS) < fmaxf(s_sep[ca], lw)) {
-                        best[u] = da;
-                        bj[u] = ca;
-                        lbn[u] = lw;
-                        need[u] = false;
+                    const float bnd = fmaxf(s_sep[ca], lw);
+                    if (da * PRUNE_GROW2 < bnd * bnd) {
+                        lloyd_commit<LP>(a, i0 + u, x[u], ca, ca, da, lw, sc, sl, my_tab, inert, changed);
+                        need = false;
                     }
                 }
-                any |= need[u];
+                const unsigned m = __ballot_sync(0xffffffffu, need);
+                if (need) {
+                    const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                    qoff[pos] = (int)(i0 + u - lo);
+                    qold[pos] = old[u];
+                }
+                qn += __popc(m);
             }
-            if (any) {
+            __syncwarp();
+            for (int q0 = 0; q0 < qn; q0 += 32) {
+                const int q = q0 + lane;
+                const bool act = q < qn;
+                const long long i = act ? lo + qoff[q] : lo;
+                float xv[LP];
+                load_point<LP>(a.X, i, a.l, xv);
+                float best = __int_as_float(0x7f800000), sec = __int_as_float(0x7f800000);
+                int bj = 0;
+#pragma unroll 4
                 for (int j = 0; j < k; ++j) {
-                    float cj[LP];
-#pragma unroll
-                    for (int c = 0; c < LP; ++c) cj[c] = s_c[j * LP + c];
-#pragma unroll
-                    for (int u = 0; u < KM_PPT; ++u) {
-                        if (!need[u]) continue;
-                        const float d = sqdist<LP>(x[u], cj);
-                        if (d < best[u]) {
-                            sec[u] = best[u];
-                            best[u] = d;
-                            bj[u] = j;
-                        } else if (d < sec[u]) {
-                            sec[u] = d;
-                        }
+                    const float d = sqdist<LP>(xv, s_c + j * LP);
+                    if (d < best) {
+                        sec = best;
+                        best = d;
+                        bj = j;
+                    } else if (d < sec) {
+                        sec = d;
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < KM_PPT; ++u)
-                    if (need[u]) lbn[u] = sqrtf(sec[u]) * (1.0f - PRUNE_EPS);
+                if (act) lloyd_commit<LP>(a, i, xv, qold[q], bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), sc, sl, my_tab,
+                                          inert, changed);
             }
-#pragma unroll
-            for (int u = 0; u < KM_PPT; ++u) {
-                if (i0 + u >= hi) break;
-                if (a.prune) a.lbound[i0 + u] = lbn[u];
-                const int lab = bj[u];
-                changed += old[u] != lab;
-                a.labels[i0 + u] = lab;
-                inert += fixq(best[u], sc.Sd);
-                int q;
-                if (sl[0].j == lab) q = 0;
-                else if (sl[1].j == lab) q = 1;
-                else {
-                    // evict the slot that was not used last (slot 1 holds the older run)
-                    slot_flush<LP>(sl[1], my_tab);
-                    sl[1] = sl[0];
-                    sl[0].j = lab;
-                    sl[0].cnt = 0;
-#pragma unroll
-                    for (int c = 0; c < LP; ++c) sl[0].s[c] = 0;
-                    q = 0;
-                }
-                if (q == 1) {   // keep the most recent label in slot 0
-                    const Slot<LP> t = sl[0];
-                    sl[0] = sl[1];
-                    sl[1] = t;
-                }
-#pragma unroll
-                for (int c = 0; c < LP; ++c) sl[0].s[c] += fixq(x[u][c], sc.Sx);
-                ++sl[0].cnt;
-            }
+            __syncwarp();
         }
         slot_flush_warp<LP>(sl[0], my_tab);
         slot_flush_warp<LP>(sl[1], my_tab);
         __syncthreads();
-        // block totals -> transposed partials[(j*(LP+1) + c) * G + b]
+        // block totals -> the iteration's accumulator (two's-complement sums: order-free, exact)
         for (size_t q = tid; q < rowlen; q += KM_THREADS) {
             unsigned long long v = 0;
             for (int t = 0; t < ntab; ++t) v += s_tab[(size_t)t * rowlen + q];
-            a.partials[q * G + b] = (long long)v;
+            if (v) atomicAdd(T + q, v);
         }
         inert = block_sum_ll(inert, s_red);
         changed = block_sum_i(changed, s_redi);
         if (tid == 0) {
-            a.inertia_part[b] = inert;
-            a.changed_part[b] = changed;
+            if (inert) atomicAdd(a.cnt3 + 4 * cur, (unsigned long long)inert);
+            if (changed) atomicAdd(a.cnt3 + 4 * cur + 1, (unsigned long long)changed);
         }
-        if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
-        // ---- phase B: every block reads the changed total; block b updates clusters j = b, b+G, ...
-        if (wid == KM_WARPS - 1) {
-            int c = 0;
-            for (int q0 = 0; q0 < G; q0 += 256) {
-                int v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int q = q0 + u * 32 + lane;
-                    v[u] = q < G ? __ldcg(a.changed_part + q) : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) c += v[u];
+        if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
+        // ---- update, in every block: c_j = (exact sum of its points) / count, rounded to float64
+        // then float32; an empty cluster keeps its centroid
+        for (int q = tid; q < k * LP; q += KM_THREADS) {
+            const int j = q / LP, c = q - j * LP;
+            const long long cntj = (long long)__ldcg(T + (size_t)j * (LP + 1) + LP);
+            float v = s_c[q];
+            if (cntj > 0) {
+                const long long sj = (long long)__ldcg(T + (size_t)j * (LP + 1) + c);
+                const double m = ((double)sj * pow2d(-sc.Sx)) / (double)cntj;
+                v = (float)m;
+                if (b == 0) a.c64[q] = m;
             }
-            c = warp_sum_i(c);
-            if (lane == 0) {
-                s_changed = c;
-                s_stop = (c == 0 || it == a.max_iter) ? 1 : 0;
-            }
+            s_cn[q] = v;
         }
-        if (b == 0 && wid == KM_WARPS - 2) {
-            long long tot = 0;
-            for (int q0 = 0; q0 < G; q0 += 256) {
-                long long v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int q = q0 + u * 32 + lane;
-                    v[u] = q < G ? __ldcg(a.inertia_part + q) : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) tot += v[u];
-            }
-            tot = warp_sum_ll(tot);
-            if (lane == 0) {
-                const double iv = (double)tot * pow2d(-sc.Sd);
-                a.st->inertia = iv;
-                if (it == 1) a.st->potential = iv;
-            }
-        }
-        for (int j = b; j < k; j += G) {
-            if (wid <= LP) {   // warp c sums component c (c = LP: the count) over the G blocks
-                const long long* src = a.partials + ((size_t)j * (LP + 1) + wid) * G;
-                long long tot = 0;
-                for (int q0 = 0; q0 < G; q0 += 256) {
-                    long long v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int q = q0 + u * 32 + lane;
-                        v[u] = q < G ? __ldcg(src + q) : 0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) tot += v[u];
-                }
-                tot = warp_sum_ll(tot);
-                if (lane == 0) s_tot[wid] = tot;
-            }
-            __syncthreads();
-            if (wid == 0) {
-                const long long cntj = s_tot[LP];
-                float mv = 0.f;
-                if (lane < LP && cntj > 0) {
-                    const double m = ((double)s_tot[lane] * pow2d(-sc.Sx)) / (double)cntj;
-                    const float c32n = (float)m;
-                    const float dlt = __fsub_rn(c32n, s_c[j * LP + lane]);
-                    mv = __fmul_rn(dlt, dlt);
-                    a.c64[(size_t)j * LP + lane] = m;
-                    a.c32[(size_t)j * LP + lane] = c32n;
-                }
-                mv = warp_sum_f(mv);
-                if (lane == 0) {
-                    a.pmove[j] = sqrtf(mv) * (1.0f + PRUNE_EPS);
-                    if (cntj == 0) atomicAdd(&a.st->empty_events, 1);
-                }
-            }
-            __syncthreads();
+        if (tid == 0) {
+            s_inert = (long long)__ldcg(a.cnt3 + 4 * cur);
+            s_changed = (int)__ldcg(a.cnt3 + 4 * cur + 1);
+            s_pmax = 0u;
         }
         __syncthreads();
+        // how far each centroid moved (bounds of the next assignment), empty-cluster events
+        for (int j = tid; j < k; j += KM_THREADS) {
+            float mv = 0.f;
+#pragma unroll
+            for (int c = 0; c < LP; ++c) {
+                const float dlt = __fsub_rn(s_cn[j * LP + c], s_c[j * LP + c]);
+                mv = __fadd_rn(mv, __fmul_rn(dlt, dlt));
+            }
+            atomicMax(&s_pmax, __float_as_uint(sqrtf(mv) * (1.0f + PRUNE_EPS)));
+            if (b == 0 && __ldcg(T + (size_t)j * (LP + 1) + LP) == 0ull) atomicAdd(&a.st->empty_events, 1);
+        }
+        // the accumulator of iteration it+2 was last read after the previous barrier: clear it
+        if (b == 0) {
+            unsigned long long* Tz = a.tot + (size_t)((it + 2) % 3) * rowlen;
+            for (size_t q = tid; q < rowlen; q += KM_THREADS) Tz[q] = 0ull;
+            if (tid < 4) a.cnt3[4 * ((it + 2) % 3) + tid] = 0ull;
+        }
         if (b == 0 && tid == 0) {
+            const double iv = (double)s_inert * pow2d(-sc.Sd);
+            a.st->inertia = iv;
+            if (it == 1) a.st->potential = iv;
             a.st->iterations = it;
             a.st->changed = s_changed;
         }
-        if (s_stop) return;
-        if (!grid_sync(a.bar, a.status, a.limit, a.stall)) return;
+        __syncthreads();
+        for (int q = tid; q < k * LP; q += KM_THREADS) s_c[q] = s_cn[q];
+        const bool stop = s_changed == 0 || it == a.max_iter;
+        __syncthreads();
+        if (stop) break;
+    }
+    if (b == 0) {
+        for (int q = tid; q < k * LP; q += KM_THREADS) a.c32[q] = s_c[q];
     }
 }
 
@@ -567,17 +553,15 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
     size_t off = 0;
+    const size_t acc = up((size_t)3 * k * (LP + 1) * 8 + 12 * 8);   // Lloyd accumulators, zeroed with the header
     const size_t o_hdr = off; off += hdr;
+    const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
     const size_t o_bs = off; off += 2 * up((size_t)G * 8);
     const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * 8);
-    const size_t o_part = off; off += up((size_t)G * ((size_t)k * LP + k) * 8);
-    const size_t o_inert = off; off += up((size_t)G * 8);
-    const size_t o_chg = off; off += up((size_t)G * 4);
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
     const size_t o_seed = off; off += up((size_t)k * 8);
-    const size_t o_pmove = off; off += up((size_t)k * 4);
     char* ws = nullptr;
     cudaError_t e = pool_malloc(reinterpret_cast<void**>(&ws), off, s);
     if (e != cudaSuccess) return cuda_status(e);
@@ -587,7 +571,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     int* call_status = reinterpret_cast<int*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier));
     unsigned* amax = reinterpret_cast<unsigned*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier) + 8);
     do {
-        if ((e = cudaMemsetAsync(ws + o_hdr, 0, hdr, s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(ws + o_hdr, 0, hdr + acc, s)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(labels, 0xff, (size_t)n * 4, s)) != cudaSuccess) break;
         KppArgs ka{};
         ka.X = emb;
@@ -622,14 +606,12 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.labels = labels;
         la.c32 = ka.c32;
         la.c64 = reinterpret_cast<double*>(ws + o_c64);
-        la.partials = reinterpret_cast<long long*>(ws + o_part);
-        la.inertia_part = reinterpret_cast<long long*>(ws + o_inert);
-        la.changed_part = reinterpret_cast<int*>(ws + o_chg);
-        la.amax = amax;
+        la.tot = reinterpret_cast<unsigned long long*>(ws + o_acc);
+        la.cnt3 = la.tot + (size_t)3 * k * (LP + 1);
         la.chunk = chunk;
+        la.amax = amax;
         la.ntab = ntab;
         la.lbound = ka.d2[0];          // the k-means++ D^2 buffers are free once seeding is done
-        la.pmove = reinterpret_cast<float*>(ws + o_pmove);
         la.prune = k <= 256 ? 1 : 0;
         la.st = st;
         la.bar = bar;
@@ -780,17 +762,15 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
     size_t off = 0;
+    const size_t acc = up((size_t)3 * k * (LP + 1) * 8 + 12 * 8);   // Lloyd accumulators, zeroed with the header
     const size_t o_hdr = off; off += hdr;
+    const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
     const size_t o_bs = off; off += 2 * up((size_t)G * 8);
     const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * 8);
-    const size_t o_part = off; off += up((size_t)G * ((size_t)k * LP + k) * 8);
-    const size_t o_inert = off; off += up((size_t)G * 8);
-    const size_t o_chg = off; off += up((size_t)G * 4);
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
     const size_t o_seed = off; off += up((size_t)k * 8);
-    const size_t o_pmove = off; off += up((size_t)k * 4);
     if (off > (size_t)FSC_KMEANS_STATIC_SCRATCH_BYTES) return FSC_ERR_TOO_LARGE;
 
     KmDevStats* st = reinterpret_cast<KmDevStats*>(ws + o_hdr);
@@ -798,7 +778,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     int* call_status = reinterpret_cast<int*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier));
     unsigned* amax = reinterpret_cast<unsigned*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier) + 8);
     // the array keeps the previous call's contents: clear what the kernels expect to start at zero
-    FSC_CUDA(cudaMemsetAsync(ws + o_hdr, 0, hdr, s));
+    FSC_CUDA(cudaMemsetAsync(ws + o_hdr, 0, hdr + acc, s));
     FSC_CUDA(cudaMemsetAsync(labels, 0xff, (size_t)n * 4, s));
     KppArgs ka{};
     ka.X = emb;
@@ -833,14 +813,12 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     la.labels = labels;
     la.c32 = ka.c32;
     la.c64 = reinterpret_cast<double*>(ws + o_c64);
-    la.partials = reinterpret_cast<long long*>(ws + o_part);
-    la.inertia_part = reinterpret_cast<long long*>(ws + o_inert);
-    la.changed_part = reinterpret_cast<int*>(ws + o_chg);
-    la.amax = amax;
+    la.tot = reinterpret_cast<unsigned long long*>(ws + o_acc);
+    la.cnt3 = la.tot + (size_t)3 * k * (LP + 1);
     la.chunk = chunk;
+    la.amax = amax;
     la.ntab = ntab;
     la.lbound = ka.d2[0];
-    la.pmove = reinterpret_cast<float*>(ws + o_pmove);
     la.prune = k <= 256 ? 1 : 0;
     la.st = st;
     la.bar = bar;

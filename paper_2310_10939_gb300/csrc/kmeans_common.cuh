@@ -155,21 +155,26 @@ __device__ __forceinline__ void slot_flush(const Slot<LP>& sl, unsigned long lon
 
 template <int LP>
 __device__ __forceinline__ void slot_flush_warp(const Slot<LP>& sl, unsigned long long* tab) {
-    const int j0 = __shfl_sync(0xffffffffu, sl.j, 0);
-    if (__all_sync(0xffffffffu, sl.j == j0)) {
-        if (j0 < 0) return;
-        const int lane = threadIdx.x & 31;
-        unsigned long long* row = tab + (size_t)j0 * (LP + 1);
+    // all 32 lanes call this: lanes holding the same label are summed by warp reductions, one
+    // label after another, and the label's lowest lane adds the totals (one set of shared
+    // atomics per label present instead of one per lane)
+    const int lane = threadIdx.x & 31;
+    unsigned pending = __ballot_sync(0xffffffffu, sl.j >= 0 && sl.cnt != 0);
+    while (pending) {
+        const int src = __ffs(pending) - 1;
+        const int jj = __shfl_sync(0xffffffffu, sl.j, src);
+        const bool mine = ((pending >> lane) & 1u) && sl.j == jj;
+        const unsigned members = __ballot_sync(0xffffffffu, mine);
+        unsigned long long* row = tab + (size_t)jj * (LP + 1);
 #pragma unroll
         for (int c = 0; c < LP; ++c) {
-            const long long v = warp_sum_ll(sl.s[c]);
-            if (lane == 0) atomicAdd(row + c, (unsigned long long)v);
+            const long long v = warp_sum_ll(mine ? sl.s[c] : 0ll);
+            if (lane == src) atomicAdd(row + c, (unsigned long long)v);
         }
-        const long long cn = warp_sum_ll(sl.cnt);
-        if (lane == 0) atomicAdd(row + LP, (unsigned long long)cn);
-        return;
+        const long long cn = warp_sum_ll(mine ? sl.cnt : 0ll);
+        if (lane == src) atomicAdd(row + LP, (unsigned long long)cn);
+        pending &= ~members;
     }
-    slot_flush<LP>(sl, tab);
 }
 
 }  // namespace fsc

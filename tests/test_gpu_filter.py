@@ -80,11 +80,11 @@ def test_adam_step_decreases_the_loss(torch):
     assert np.isclose(fl.batch_loss_and_grad(theta, F, G, b, np.ones(B))[0], losses[-1], rtol=0.05)
 
 
-@pytest.mark.parametrize("store_name,tol", [("f32", 1e-5), ("bf16", 2e-2)])
+@pytest.mark.parametrize("store_name,tol", [("f32", 1e-5), ("f16", 3e-3), ("bf16", 2e-2)])
 @pytest.mark.parametrize("name", ["sbm", "knn"])
 def test_chebyshev_basis_matches_oracle(torch, store_name, tol, name):
     import paper_2310_10939_gb300 as fsc
-    store = fsc.F32 if store_name == "f32" else fsc.BF16
+    store = {"f32": fsc.F32, "f16": fsc.F16, "bf16": fsc.BF16}[store_name]
     g = W.sbm([300] * 4, 0.06, 0.004, 7) if name == "sbm" else W.knn_mixture(2000, 8, 5, 10, seed=8)
     G = fsc.Graph.from_workload(g)
     l, seed = 3, 21
@@ -160,7 +160,8 @@ def test_trained_filter_gains_over_plain_method_on_held_out_graphs(torch):
     assert (learned < plain8).mean() >= 0.75
 
 
-def test_filtered_clustering_recovers_sbm(torch):
+@pytest.mark.parametrize("store_name", ["f32", "f16"])
+def test_filtered_clustering_recovers_sbm(torch, store_name):
     """Algorithm 2 with the learned filter (8 sparse products, float32 basis) against the plain method
     with t = ceil(log2 n) = 17 products (oracle, float64).
 
@@ -172,20 +173,22 @@ def test_filtered_clustering_recovers_sbm(torch):
     """
     import paper_2310_10939_gb300 as fsc
     assert _weights_available(), "trained filter weights are missing"
+    store = fsc.F32 if store_name == "f32" else fsc.F16
     params = fsc.load_filter_params()
     g = W.sbm_by_degree(100_000, 20, 30.0, 3.0, seed=31)
     G = fsc.Graph.from_workload(g)
     k, l, t = 20, 5, 17
     runs_f, runs_p = [], []
     for seed in (31, 32, 33):
-        lab_f, st = fsc.cluster_filtered(G, k, l, seed, params, store=fsc.F32)
+        lab_f, st = fsc.cluster_filtered(G, k, l, seed, params, store=store)
+        assert st["fallback"] == 0 and abs(st["filter_energy_ratio"] - 1.0) < 0.5, st
         runs_f.append((st["inertia"], metrics.ari(lab_f.cpu().numpy(), g.labels)))
         ref = ocluster.fast_spectral_cluster(g, k, l, t, seed)
         runs_p.append((ref["inertia"], metrics.ari(ref["labels"], g.labels)))
     a_f, a_p = min(runs_f)[1], min(runs_p)[1]
     assert a_f >= a_p - 0.01, (runs_f, runs_p)
 
-    emb, _, _ = fsc.filter_embed(G, l, k, 31, params=params, store=fsc.F32)
+    emb, _, _ = fsc.filter_embed(G, l, k, 31, params=params, store=store)
     dm = spectral.inv_sqrt_degrees(spectral.degrees(g))[:, None]
     Yf = emb.cpu().numpy()[:, :l].astype(np.float64) / dm
     Yp = spectral.power_method(spectral.signless_laplacian(g), gaussian_block(g.n, l, 31), t)
@@ -195,3 +198,40 @@ def test_filtered_clustering_recovers_sbm(torch):
         return float(((Y - PY) ** 2).sum() / (PY ** 2).sum())
 
     assert leak(Yf) <= 2.0 * leak(Yp), (leak(Yf), leak(Yp))
+
+
+@pytest.mark.parametrize("store_name", ["f32", "f16"])
+def test_filter_energy_matches_oracle(torch, store_name):
+    """The energy fused into the combine step is ||p(M) X||^2 in x-space (sum_v d(v) |y_v|^2)."""
+    import paper_2310_10939_gb300 as fsc
+    g = W.sbm_by_degree(30_000, 8, 20.0, 2.0, seed=41)
+    G = fsc.Graph.from_workload(g)
+    l, k, seed = 3, 8, 5
+    c = np.array([0.1, 0.5, -0.2, 0.3, 0.05, -0.1, 0.2, 0.0, 0.15])
+    energy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    store = fsc.F32 if store_name == "f32" else fsc.F16
+    fsc.filter_embed(G, l, k, seed, coeffs=torch.as_tensor(c, dtype=torch.float32, device="cuda"), store=store,
+                     energy=energy)
+    K = fl.cheb_basis(g, gaussian_block(g.n, l, seed))
+    Y = sum(np.float32(c[j]) * K[j] for j in range(9))
+    ref = float((Y * Y).sum())
+    assert abs(float(energy.item()) - ref) <= (1e-5 if store_name == "f32" else 3e-3) * ref
+
+
+def test_fallback_replaces_a_bad_filter_with_the_plain_method(torch):
+    """A filter that amplifies the bulk (output layer fixed to 3 T_8) trips the energy guard; the
+    labels are then exactly those of the plain method with t = ceil(log2 n) on the same start block."""
+    import paper_2310_10939_gb300 as fsc
+    g = W.sbm_by_degree(50_000, 10, 20.0, 2.0, seed=43)
+    G = fsc.Graph.from_workload(g)
+    k, l, seed = 10, 4, 12
+    theta = np.zeros(fl.NPARAM, dtype=np.float32)
+    theta[-1] = 3.0                                     # b3[8]: c = (0, ..., 0, 3)
+    P = torch.as_tensor(theta, device="cuda")
+    lab, st = fsc.cluster_filtered(G, k, l, seed, P)
+    assert st["fallback"] == 1 and st["filter_energy_ratio"] > st["filter_threshold"], st
+    assert st["fallback_t"] == int(np.ceil(np.log2(g.n)))
+    ref, _ = fsc.cluster(G, k, l, st["fallback_t"], seed)
+    assert torch.equal(lab, ref)
+    lab2, st2 = fsc.cluster_filtered(G, k, l, seed, P, fallback=False)
+    assert st2["fallback"] == 0
