@@ -176,8 +176,10 @@ def gpu_arm(args, w, rank, world, local_rank):
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
     stream = torch.cuda.current_stream(dev)
 
-    def step(evs=None):
+    def step(evs=None, mid=None):
         G = fsc.Graph(rp, col, wt)
+        if mid is not None:
+            mid.record(stream)
         _, st = fsc.cluster(G, k, l, t, seed, store=store, labels=labels, rescale=True, events=evs)
         G.close()
         return st
@@ -189,6 +191,7 @@ def gpu_arm(args, w, rank, world, local_rank):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local_rank)
@@ -199,7 +202,7 @@ def gpu_arm(args, w, rank, world, local_rank):
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
-        stats = step(sp[i])
+        stats = step(sp[i], mids[i])
         ends[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -207,6 +210,8 @@ def gpu_arm(args, w, rank, world, local_rank):
         torch.distributed.barrier()
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    create_ms = float(np.mean([s.elapsed_time(m) for s, m in zip(starts, mids)]))
+    cluster_ms = float(np.mean([m.elapsed_time(e) for m, e in zip(mids, ends)]))
     spmm_ms = [a.elapsed_time(b) for a, b in sp]
     ms = float(np.mean(step_ms))
     spmm_launch_ms = float(np.mean(spmm_ms)) / t
@@ -275,6 +280,8 @@ def gpu_arm(args, w, rank, world, local_rank):
                      if peak_src == "measured" else "fallback 6.8 TB/s",
                      "traffic": read_traffic("spmm_sbm_n2p20_l4_f32") if args.workload == "sbm_n2p20_k16" else None,
                      "bytes_per_launch": int(bytes_launch), "launch_ms": round(spmm_launch_ms, 5)},
+        "breakdown_ms": {"create_graph": round(create_ms, 4), "cluster": round(cluster_ms, 4),
+                         "power_iterations": round(spmm_launch_ms * t, 4)},
         "ari_vs_planted": round(ari, 4),
         "lloyd_iterations": stats["iterations"] if stats else None,
         "graphs_per_s": round(world * args.steps / (ms * args.steps * 1e-3), 3),

@@ -671,7 +671,7 @@ extern "C" fsc_status fsc_batch_create(const fsc_batch_desc* d, void* stream, fs
                 int best = 0;
                 float us = 0.f;
                 rc = autotune_graph(&view, gs[g].l, (fsc_dtype)d->store, &best, &us, s);
-                if (view.ws) cudaFree(view.ws);
+                if (view.ws) pool_free(view.ws, s);
                 if (rc != FSC_OK) break;
             }
             if (rc != FSC_OK) break;

@@ -211,13 +211,36 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
         vsq += __shfl_xor_sync(0xffffffffu, vsq, off);
         vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (vsq != 0.0) atomicAdd(sumsq, vsq);
-        if (vmax > 0.0) atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(vmax));
-        if (bad) atomicOr(status, bad);
-        if (iso) atomicAdd(n_iso, (unsigned long long)iso);
-        const double v = w ? vsum : (double)cnt_total;
-        if (v != 0.0) atomicAdd(vol, v);
+    // block totals first: one atomic per block and statistic (per-warp atomics on five single
+    // addresses serialised at L2 and dominated the kernel)
+    __shared__ double s_sq[8], s_mx[8], s_vol[8];
+    __shared__ int s_bad[8];
+    __shared__ unsigned s_iso[8];
+    const int wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_sq[wid] = vsq;
+        s_mx[wid] = vmax;
+        s_vol[wid] = w ? vsum : (double)cnt_total;
+        s_bad[wid] = bad;
+        s_iso[wid] = iso;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tsq = 0.0, tmx = 0.0, tvol = 0.0;
+        int tbad = 0;
+        unsigned tiso = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            tsq += s_sq[q];
+            tmx = fmax(tmx, s_mx[q]);
+            tvol += s_vol[q];
+            tbad |= s_bad[q];
+            tiso += s_iso[q];
+        }
+        if (tsq != 0.0) atomicAdd(sumsq, tsq);
+        if (tmx > 0.0) atomicMax(dmax_bits, (unsigned long long)__double_as_longlong(tmx));
+        if (tbad) atomicOr(status, tbad);
+        if (tiso) atomicAdd(n_iso, (unsigned long long)tiso);
+        if (tvol != 0.0) atomicAdd(vol, tvol);
     }
 }
 
@@ -295,7 +318,7 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
         const int threads = 256;
         constexpr int rows_per_block = threads / 32 * (32 / kDegLanes);
         const int64_t want = (n + rows_per_block - 1) / rows_per_block;
-        const int64_t cap = (int64_t)device_props().num_sms * 8;
+        const int64_t cap = (int64_t)device_props().num_sms * 4;
         const int blocks = (int)(want < cap ? want : cap);
         const int check_sorted = (flags & FSC_VALIDATE_SYMMETRY) ? 1 : 0;
         k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,

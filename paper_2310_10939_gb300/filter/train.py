@@ -1,8 +1,8 @@
 """Train the filter MLP on the GPU with the library's own forward/backward/Adam kernels.
 
-Input: train_data.npz next to this file (features, and per graph the normalised quadratic
-(Gn, bn) of the loss ||sum_j c_j T_j(A_hat) X - P X||^2 / ||P X||^2; written by the oracle's
-data script).  Output: mlp_weights.npz (5833 float32 parameters that take the raw features)
+Input: train_data.npz and train_data_large.npz next to this file (features, and per graph the
+normalised quadratic (Gn, bn) of the loss ||sum_j c_j T_j(A_hat) X - P X||^2 / ||P X||^2;
+written by the oracle's data script; the second file holds SBMs with n up to 2^21).  Output: mlp_weights.npz (5833 float32 parameters that take the raw features)
 and train_summary.json.
 
 Features are standardised for training (mean / std of the training split) and the affine map is
@@ -31,7 +31,9 @@ def main():
     import paper_2310_10939_gb300 as fsc
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--data", default=os.path.join(HERE, "train_data.npz"))
+    ap.add_argument("--data", default=",".join(p for p in (os.path.join(HERE, "train_data.npz"),
+                                                            os.path.join(HERE, "train_data_large.npz"))
+                                               if os.path.exists(p)))
     ap.add_argument("--out", default=HERE)
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--batch", type=int, default=256)
@@ -41,13 +43,14 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
 
-    d = np.load(args.data)
+    parts = [np.load(f) for f in args.data.split(",") if f]
+    d = {key: np.concatenate([q[key] for q in parts]) for key in ("f", "G", "b", "loss8", "loss22", "best", "n", "k")}
     F, Gn, bn = d["f"], d["G"], d["b"]
     N = F.shape[0]
     ok = np.isfinite(F).all(1) & np.isfinite(Gn.reshape(N, -1)).all(1) & np.isfinite(bn).all(1)
-    idx = np.nonzero(ok)[0]
+    idx = np.random.default_rng(args.seed + 1).permutation(np.nonzero(ok)[0])
     nval = int(round(args.val_frac * idx.size))
-    val, tr = idx[-nval:], idx[:-nval]
+    val, tr = np.sort(idx[:nval]), np.sort(idx[nval:])
     mu = F[tr].mean(0)
     sd = F[tr].std(0)
     sd[sd < 1e-8] = 1.0
@@ -122,6 +125,15 @@ def main():
         "val_frac_learned_beats_t8": float((lv < d["loss8"][val]).mean()),
         "val_frac_learned_beats_t22": float((lv < d["loss22"][val]).mean()),
     }
+    big = d["n"][val] >= 100_000
+    if big.any():
+        summary.update({
+            "val_large_graphs": int(big.sum()),
+            "val_large_mean_loss_learned": float(lv[big].mean()),
+            "val_large_mean_loss_plain_t22": float(d["loss22"][val][big].mean()),
+            "val_large_mean_loss_best_degree8": float(np.nanmean(d["best"][val][big])),
+            "val_large_frac_learned_beats_t22": float((lv[big] < d["loss22"][val][big]).mean()),
+        })
     with open(os.path.join(args.out, "train_summary.json"), "w") as fh:
         json.dump(summary, fh, indent=1)
     print(json.dumps(summary))
