@@ -206,6 +206,29 @@ fsc_status fsc_kmeans_static(const float* emb, int64_t n, int l, int ld, int k, 
                              void* stream);
 
 /*
+ * fsc_kmeans_best - k-means with restarts (not in the paper; the usual library practice of
+ * keeping the best of several k-means runs).  Run r (r = 0 .. n_init-1) is fsc_kmeans with
+ * seed + r (its own k-means++ draws); the run of lowest inertia is kept, ties going to the
+ * lowest r.  Outputs as fsc_kmeans for that run; *best_run (host, optional) receives r.
+ * Synchronous; allocates one spare labels/centroids/seeds set from the library pool when
+ * n_init > 1.
+ */
+fsc_status fsc_kmeans_best(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int n_init,
+                           int max_iter, int32_t* labels, double* centroids, int64_t* seed_idx,
+                           fsc_kmeans_stats* stats, int32_t* best_run, void* stream);
+
+/*
+ * fsc_partition_scores - adjusted Rand index and normalised mutual information of two labelings
+ * (the accuracy measures of Sec. 4).  labels_a (values in [0, ka)) and labels_b (in [0, kb)):
+ * device int32 arrays of n entries.  The contingency table is built on the device; ARI uses
+ * exact 64-bit pair counts, NMI the arithmetic-mean normalisation (natural logs).
+ * ari_nmi: host double[2] <- {ARI, NMI}.  ka * kb <= 2^24.  A label outside its range gives
+ * FSC_ERR_INDEX_RANGE.  Synchronous.
+ */
+fsc_status fsc_partition_scores(const int32_t* labels_a, const int32_t* labels_b, int64_t n, int ka, int kb,
+                                double* ari_nmi, void* stream);
+
+/*
  * fsc_cluster - Algorithm 2 end to end: fsc_embed then fsc_kmeans on its output.
  * labels: int32[n] output.  stats: host struct or NULL.  opts may be NULL.
  * Synchronous (returns after the device work and reports its status).

@@ -130,6 +130,19 @@ def kmeans(X: np.ndarray, k: int, seed: int, max_iter: int = 100):
     return out
 
 
+def kmeans_best(X: np.ndarray, k: int, seed: int, n_init: int, max_iter: int = 100):
+    """Restarts: runs r = 0..n_init-1 each seeded with seed + r (their own k-means++ draws), and
+    keeps the run of lowest inertia (ties: the lowest r).  Returns that run's result plus
+    `run` (its index) and `inertias` (every run's)."""
+    runs = [kmeans(X, k, seed + r, max_iter) for r in range(n_init)]
+    inertias = np.array([r["inertia"] for r in runs])
+    best = int(np.argmin(inertias))        # first minimum = lowest run index among ties
+    out = dict(runs[best])
+    out["run"] = best
+    out["inertias"] = inertias
+    return out
+
+
 def relative_margin(best: np.ndarray, second: np.ndarray) -> np.ndarray:
     """(d2 - d1) / d1 per point (inf where d1 = 0 < d2)."""
     b = best.astype(np.float64)

@@ -22,7 +22,7 @@ __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
     "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
     "F32", "BF16", "F16", "FILTER_NO_FALLBACK", "release_cached_memory", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
-    "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
+    "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
@@ -98,6 +98,11 @@ def lib() -> C.CDLL:
         L.fsc_power_step.argtypes = [vp, i32, i32, vp, vp, i32, vp]
         L.fsc_kmeans.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
         L.fsc_kmeans_static.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
+        L.fsc_kmeans_best.argtypes = [vp, i64, i32, i32, i32, u64, i32, i32, vp, vp, vp, C.POINTER(KmeansStats),
+                                      C.POINTER(i32), vp]
+        L.fsc_kmeans_best.restype = i32
+        L.fsc_partition_scores.argtypes = [vp, vp, i64, i32, i32, C.POINTER(C.c_double), vp]
+        L.fsc_partition_scores.restype = i32
         L.fsc_kmeans_static.restype = i32
         L.fsc_cluster.argtypes = [vp, i32, i32, i32, u64, i32, i32, vp, C.POINTER(KmeansStats),
                                   C.POINTER(EmbedOpts), vp]
@@ -308,6 +313,33 @@ def kmeans(emb, l: int, k: int, seed: int, max_iter: int = 100, labels=None, wan
                             _ptr(labels), _ptr(cen), _ptr(sd), C.byref(st) if sync else None, _stream(stream)),
            "fsc_kmeans")
     return labels, (st.as_dict() if sync else None), cen, sd
+
+
+def kmeans_best(emb, l: int, k: int, seed: int, n_init: int, max_iter: int = 100, labels=None,
+                want_centroids: bool = False, want_seeds: bool = False, stream=None):
+    """fsc_kmeans_best: the lowest-inertia run of n_init restarts (seeds seed .. seed+n_init-1).
+    Returns (labels, stats, centroids, seeds, best_run)."""
+    torch = _torch()
+    _require_cuda(emb, torch.float32, "emb")
+    n, ld = emb.shape
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=emb.device)
+    cen = torch.empty((k, l), dtype=torch.float64, device=emb.device) if want_centroids else None
+    sd = torch.empty(k, dtype=torch.int64, device=emb.device) if want_seeds else None
+    st = KmeansStats()
+    run = C.c_int(-1)
+    _check(lib().fsc_kmeans_best(_ptr(emb), n, int(l), int(ld), int(k), int(seed) & (2**64 - 1), int(n_init),
+                                 int(max_iter), _ptr(labels), _ptr(cen), _ptr(sd), C.byref(st), C.byref(run),
+                                 _stream(stream)), "fsc_kmeans_best")
+    return labels, st.as_dict(), cen, sd, run.value
+
+
+def partition_scores(labels_a, labels_b, ka: int, kb: int, stream=None):
+    """fsc_partition_scores: (ARI, NMI) of two int32 CUDA labelings with values in [0, ka), [0, kb)."""
+    out = (C.c_double * 2)()
+    _check(lib().fsc_partition_scores(_ptr(labels_a), _ptr(labels_b), int(labels_a.numel()), int(ka), int(kb), out,
+                                      _stream(stream)), "fsc_partition_scores")
+    return float(out[0]), float(out[1])
 
 
 def cluster(g: Graph, k: int, l: int, t: int, seed: int, store: int = F32, max_iter: int = 100, labels=None,

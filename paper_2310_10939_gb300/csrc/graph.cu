@@ -318,7 +318,9 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
         const int threads = 256;
         constexpr int rows_per_block = threads / 32 * (32 / kDegLanes);
         const int64_t want = (n + rows_per_block - 1) / rows_per_block;
-        const int64_t cap = (int64_t)device_props().num_sms * 4;
+        // enough warps that each walks only a few rows: every row is a dependent row_ptr -> col
+        // load chain, so the kernel is latency-bound with fewer warps in flight
+        const int64_t cap = (int64_t)device_props().num_sms * 32;
         const int blocks = (int)(want < cap ? want : cap);
         const int check_sorted = (flags & FSC_VALIDATE_SYMMETRY) ? 1 : 0;
         k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,

@@ -676,6 +676,60 @@ extern "C" fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int
     return FSC_ERR_INVALID_ARG;
 }
 
+// Restarts: run r seeds k-means++ with seed + r; the run of lowest inertia wins (ties: lowest r).
+// Two label (and centroid / seed) buffers swap roles, so the winner is copied at most once.
+extern "C" fsc_status fsc_kmeans_best(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int n_init,
+                                      int max_iter, int32_t* labels, double* centroids, int64_t* seed_idx,
+                                      fsc_kmeans_stats* stats, int32_t* best_run, void* stream) {
+    if (n_init < 1 || n_init > 1000000 || !labels || n < 1 || n > 2147483647LL || k < 1 || l < 1 || l > 8)
+        return FSC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    char* spare = nullptr;
+    const size_t lab_b = ((size_t)n * 4 + 255) & ~(size_t)255;
+    const size_t cen_b = (((size_t)k * l * 8) + 255) & ~(size_t)255;
+    const size_t sd_b = (((size_t)k * 8) + 255) & ~(size_t)255;
+    if (n_init > 1) {
+        cudaError_t e = pool_malloc(reinterpret_cast<void**>(&spare), lab_b + cen_b + sd_b, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    int32_t* lab_buf[2] = {labels, reinterpret_cast<int32_t*>(spare)};
+    double* cen_buf[2] = {centroids, centroids ? reinterpret_cast<double*>(spare + lab_b) : nullptr};
+    int64_t* sd_buf[2] = {seed_idx, seed_idx ? reinterpret_cast<int64_t*>(spare + lab_b + cen_b) : nullptr};
+    int best = -1, cur = 0, best_buf = 0;
+    fsc_kmeans_stats best_st{};
+    fsc_status rc = FSC_OK;
+    for (int r = 0; r < n_init && rc == FSC_OK; ++r) {
+        fsc_kmeans_stats st{};
+        rc = fsc_kmeans(emb, n, l, ld, k, seed + (uint64_t)r, max_iter, lab_buf[cur], cen_buf[cur], sd_buf[cur], &st,
+                        stream);
+        if (rc != FSC_OK) break;
+        if (best < 0 || st.inertia < best_st.inertia) {
+            best = r;
+            best_st = st;
+            best_buf = cur;
+            cur ^= 1;   // keep the winner, run the next restart in the other buffer
+        }
+    }
+    if (rc == FSC_OK && best_buf == 1) {
+        cudaError_t e = cudaMemcpyAsync(labels, lab_buf[1], (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && centroids)
+            e = cudaMemcpyAsync(centroids, cen_buf[1], (size_t)k * l * 8, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && seed_idx)
+            e = cudaMemcpyAsync(seed_idx, sd_buf[1], (size_t)k * 8, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    if (spare) {
+        pool_free(spare, s);
+        cudaStreamSynchronize(s);
+    }
+    if (rc == FSC_OK) {
+        if (stats) *stats = best_st;
+        if (best_run) *best_run = best;
+    }
+    return rc;
+}
+
 extern "C" fsc_status fsc_cluster(const fsc_graph* g, int k, int l, int t, uint64_t seed, fsc_dtype store,
                                   int max_iter, int32_t* labels, fsc_kmeans_stats* stats, const fsc_embed_opts* opts,
                                   void* stream) {

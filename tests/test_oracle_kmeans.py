@@ -140,3 +140,28 @@ def test_misclassified_volume_brute_force():
                 for p in itertools.permutations(range(3)))
     assert np.isclose(metrics.misclassified_volume(lab, planted, d), brute)
     assert metrics.misclassified_volume(planted, planted, d) == 0.0
+
+
+def test_kmeans_restarts_reach_the_brute_force_optimum():
+    """Restarts keep the lowest-inertia run: on tiny instances where a single k-means++ + Lloyd
+    run stops in a local optimum, 30 restarts reach the brute-force optimum, and restarts are
+    never worse than the single run (a restart rule that kept the worst run fails here)."""
+    stuck = 0
+    for seed in range(12):
+        X, _ = _blobs(9, 3, 2, seed, spread=1.5)
+        best = min(km.cost(X, np.array(lab))
+                   for lab in itertools.product(range(3), repeat=9) if len(set(lab)) == 3)
+        single = km.kmeans(X, 3, seed)
+        out = km.kmeans_best(X, 3, seed, n_init=30)
+        assert km.cost(X, out["labels"]) <= km.cost(X, single["labels"]) + 1e-9
+        if km.cost(X, single["labels"]) > best + 1e-6:
+            stuck += 1
+            assert abs(km.cost(X, out["labels"]) - best) <= 1e-6 * max(1.0, best), seed
+    assert stuck >= 4
+
+
+def test_kmeans_best_single_run_is_kmeans():
+    X, _ = _blobs(300, 5, 3, 4)
+    a = km.kmeans(X, 5, 11)
+    b = km.kmeans_best(X, 5, 11, n_init=1)
+    assert np.array_equal(a["labels"], b["labels"]) and b["run"] == 0 and a["inertia"] == b["inertia"]
