@@ -10,7 +10,9 @@ evaluated directly), and the best possible degree-8 loss 1 - bn^T Gn^-1 bn.
 
 With --large the graphs are SBMs with n = 10^5 .. 2^21 and k = 2 .. 24 (written to
 train_data_large.npz): there n / k, the number of bulk eigen-directions per signal one, reaches
-10^5, the range in which the filter must suppress the bulk by 10^-3 or more.
+10^5, the range in which the filter must suppress the bulk by 10^-3 or more.  With --many-k
+they are SBMs with n = 10^5 .. 6 10^5, k = 25 .. 100 and mean degree 20 .. 40
+(train_data_many_k.npz), for many clusters at large n.
 
 Usage: python -m oracle.make_filter_data [--graphs 3000] [--workers 8] [--large]
 """
@@ -27,6 +29,7 @@ import numpy as np
 OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "paper_2310_10939_gb300", "filter", "train_data.npz")
 OUT_LARGE = OUT.replace("train_data.npz", "train_data_large.npz")
+OUT_MANY_K = OUT.replace("train_data.npz", "train_data_many_k.npz")
 
 
 def _draw(i: int, base_seed: int):
@@ -51,6 +54,15 @@ def _draw_large(i: int, base_seed: int):
     k = int(round(math.exp(rng.uniform(math.log(2), math.log(kmax)))))
     deg_in = float(rng.uniform(10, 40))
     deg_out = deg_in * float(rng.uniform(0.03, 0.15))
+    return ("sbm", n, k, deg_in, deg_out, int(rng.integers(1, 2**31)))
+
+
+def _draw_many_k(i: int, base_seed: int):
+    rng = np.random.default_rng(base_seed * 1_000_003 + 900_000_000 + i)
+    n = int(round(math.exp(rng.uniform(math.log(100_000), math.log(600_000)))))
+    k = int(round(math.exp(rng.uniform(math.log(25), math.log(100)))))
+    deg_in = float(rng.uniform(18, 36))
+    deg_out = deg_in * float(rng.uniform(0.05, 0.15))
     return ("sbm", n, k, deg_in, deg_out, int(rng.integers(1, 2**31)))
 
 
@@ -85,16 +97,17 @@ def main():
     ap.add_argument("--seed", type=int, default=2023)
     ap.add_argument("--out", default=None)
     ap.add_argument("--large", action="store_true")
+    ap.add_argument("--many-k", action="store_true")
     args = ap.parse_args()
     if args.out is None:
-        args.out = OUT_LARGE if args.large else OUT
-    draw = _draw_large if args.large else _draw
+        args.out = OUT_MANY_K if args.many_k else (OUT_LARGE if args.large else OUT)
+    draw = _draw_many_k if args.many_k else (_draw_large if args.large else _draw)
     specs = [draw(i, args.seed) for i in range(args.graphs)]
-    if args.large:   # largest first, so the pool ends on short jobs
+    if args.large or args.many_k:   # largest first, so the pool ends on short jobs
         specs.sort(key=lambda sp: -sp[1])
     t0 = time.time()
     with mp.get_context("spawn").Pool(args.workers) as pool:
-        recs = pool.map(_record, specs, chunksize=1 if args.large else 4)
+        recs = pool.map(_record, specs, chunksize=1 if (args.large or args.many_k) else 4)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     np.savez_compressed(
         args.out,

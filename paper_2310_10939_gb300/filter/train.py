@@ -32,7 +32,8 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--data", default=",".join(p for p in (os.path.join(HERE, "train_data.npz"),
-                                                            os.path.join(HERE, "train_data_large.npz"))
+                                                            os.path.join(HERE, "train_data_large.npz"),
+                                                            os.path.join(HERE, "train_data_many_k.npz"))
                                                if os.path.exists(p)))
     ap.add_argument("--out", default=HERE)
     ap.add_argument("--epochs", type=int, default=300)

@@ -30,12 +30,14 @@ def test_kmeans_best_matches_oracle(torch, n, k, l, seed, n_init):
     Xp[:, :l] = X
     lab, st, _, _, run = fsc.kmeans_best(torch.as_tensor(Xp, device="cuda"), l, k, seed, n_init)
     ref = km.kmeans_best(X, k, seed, n_init)
-    order = np.sort(ref["inertias"])
-    if order.size > 1 and (order[1] - order[0]) <= 1e-6 * order[0]:
-        pytest.skip("two restarts tie within the inertia rounding: either is a correct winner")
-    assert run == ref["run"], (run, ref["inertias"])
-    margin = km.relative_margin(ref["best"], ref["second"])
-    assert not ((lab.cpu().numpy() != ref["labels"]) & (margin >= 1e-6)).any()
+    # runs whose inertia is within rounding of the best are equally correct winners (restarts
+    # that reach the same partition tie exactly in exact arithmetic); the winner must be one of
+    # them and its labels must be that run's
+    tied = np.nonzero(ref["inertias"] <= ref["inertia"] * (1 + 1e-6))[0]
+    assert run in tied, (run, ref["inertias"])
+    won = km.kmeans(X, k, seed + run)
+    margin = km.relative_margin(won["best"], won["second"])
+    assert not ((lab.cpu().numpy() != won["labels"]) & (margin >= 1e-6)).any()
     assert np.isclose(st["inertia"], ref["inertia"], rtol=1e-5)
 
 
