@@ -103,9 +103,11 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         float* d2n = a.d2[r & 1];
         const float* d2o = a.d2[(r - 1) & 1];
         long long* bs = a.bsum[r & 1];
-        long long* ts = a.tsum[r & 1] + (size_t)b * a.max_tiles;
-        // ---- phase A: D^2 update, KM_PPT consecutive points per thread, exact tile sums
-        long long bacc = 0;
+        // ---- phase A: D^2 update, KM_PPT consecutive points per thread.  Exact partial sums are
+        // kept per (tile, warp) - 128 consecutive points - so no block barrier is needed per tile
+        // and the loads of successive tiles overlap; one block reduction forms the block total.
+        long long* ts = a.tsum[r & 1] + (size_t)b * a.max_tiles * KM_WARPS;
+        long long wacc = 0;
         int tile = 0;
         for (long long t0 = lo; t0 < hi; t0 += KM_TILE, ++tile) {
             const long long i0 = t0 + (long long)KM_PPT * tid;
@@ -126,12 +128,11 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                     v += fixq(dd, sc.Sd);
                 }
             }
-            const long long tsv = block_sum_ll(v, s_red);
-            if (tid == 0) {
-                ts[tile] = tsv;
-                bacc += tsv;
-            }
+            v = warp_sum_ll(v);
+            if (lane == 0) ts[(size_t)tile * KM_WARPS + wid] = v;
+            wacc += v;
         }
+        const long long bacc = block_sum_ll(lane == 0 ? wacc : 0ll, s_red);
         if (tid == 0) bs[b] = bacc;
         if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
 
@@ -181,45 +182,52 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         } else {
             const int bq = s_bstar;
             const long long blo = min(n, (long long)bq * chunk), bhi = min(n, blo + chunk);
-            const int ntiles = (int)((bhi - blo + KM_TILE - 1) / KM_TILE);
-            const long long* tsb = a.tsum[r & 1] + (size_t)bq * a.max_tiles;
+            const int nseg = (int)((bhi - blo + KM_TILE - 1) / KM_TILE) * KM_WARPS;   // (tile, warp) segments
+            const long long* tsb = a.tsum[r & 1] + (size_t)bq * a.max_tiles * KM_WARPS;
             if (tid == 0) {
                 s_tile = -1;
                 s_idx = INT_MAX;
             }
-            for (int q0 = 0; q0 < ntiles; q0 += KM_THREADS) {
-                const int cnt = min(KM_THREADS, ntiles - q0);
+            // the segment holding the target: block-parallel prefix over the block's segments
+            for (int q0 = 0; q0 < nseg; q0 += KM_THREADS) {
                 __syncthreads();
-                if (tid < cnt) s_tiles[tid] = __ldcg(tsb + q0 + tid);
-                __syncthreads();
-                if (tid == 0) {
-                    long long run = s_base;
-                    for (int q = 0; q < cnt; ++q) {
-                        if (run + s_tiles[q] > s_T) { s_tile = q0 + q; break; }
-                        run += s_tiles[q];
-                    }
-                    s_base = run;
+                const long long base = s_base;
+                const long long v = q0 + tid < nseg ? __ldcg(tsb + q0 + tid) : 0ll;
+                const long long incl = block_scan_ll(v, s_red);
+                if (v > 0 && base + incl > s_T && base + incl - v <= s_T) {
+                    s_tile = q0 + tid;
+                    s_base = base + incl - v;
                 }
                 __syncthreads();
                 if (s_tile >= 0) break;
+                if (tid == KM_THREADS - 1) s_base = base + incl;
             }
-            if (tid == 0 && s_tile < 0) s_tile = ntiles - 1;   // defensive only (exact sums always cross)
+            if (tid == 0 && s_tile < 0) s_tile = nseg - 1;   // defensive only (exact sums always cross)
             __syncthreads();
-            const long long i0 = blo + (long long)s_tile * KM_TILE + (long long)KM_PPT * tid;
-            long long q[KM_PPT];
-            long long v = 0;
+            if (wid == 0) {   // the point within the segment: 32 lanes x KM_PPT consecutive points
+                const int tq = s_tile / KM_WARPS, wq = s_tile % KM_WARPS;
+                const long long i0 = blo + (long long)tq * KM_TILE + (long long)KM_PPT * (wq * 32 + lane);
+                long long q[KM_PPT];
+                long long v = 0;
 #pragma unroll
-            for (int u = 0; u < KM_PPT; ++u) {
-                q[u] = i0 + u < bhi ? fixq(__ldcg(d2n + i0 + u), sc.Sd) : 0;
-                v += q[u];
-            }
-            long long run = block_scan_ll(v, s_red) - v + s_base;   // exclusive prefix of this thread
+                for (int u = 0; u < KM_PPT; ++u) {
+                    q[u] = i0 + u < bhi ? fixq(__ldcg(d2n + i0 + u), sc.Sd) : 0;
+                    v += q[u];
+                }
+                long long incl = v;
 #pragma unroll
-            for (int u = 0; u < KM_PPT; ++u) {
-                run += q[u];
-                if (q[u] > 0 && run > s_T) {
-                    atomicMin(&s_idx, (int)(i0 + u));
-                    break;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const long long t = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += t;
+                }
+                long long run = incl - v + s_base;   // exclusive prefix of this lane
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    run += q[u];
+                    if (q[u] > 0 && run > s_T) {
+                        atomicMin(&s_idx, (int)(i0 + u));
+                        break;
+                    }
                 }
             }
             __syncthreads();
@@ -558,7 +566,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
     const size_t o_bs = off; off += 2 * up((size_t)G * 8);
-    const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * 8);
+    const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * KM_WARPS * 8);
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
     const size_t o_seed = off; off += up((size_t)k * 8);
@@ -584,7 +592,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         ka.bsum[0] = reinterpret_cast<long long*>(ws + o_bs);
         ka.bsum[1] = reinterpret_cast<long long*>(ws + o_bs + up((size_t)G * 8));
         ka.tsum[0] = reinterpret_cast<long long*>(ws + o_ts);
-        ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)G * max_tiles * 8));
+        ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)G * max_tiles * KM_WARPS * 8));
         ka.max_tiles = max_tiles;
         ka.chunk = chunk;
         ka.amax = amax;
@@ -821,7 +829,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
     const size_t o_bs = off; off += 2 * up((size_t)G * 8);
-    const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * 8);
+    const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * KM_WARPS * 8);
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
     const size_t o_seed = off; off += up((size_t)k * 8);
@@ -845,7 +853,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     ka.bsum[0] = reinterpret_cast<long long*>(ws + o_bs);
     ka.bsum[1] = reinterpret_cast<long long*>(ws + o_bs + up((size_t)G * 8));
     ka.tsum[0] = reinterpret_cast<long long*>(ws + o_ts);
-    ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)G * max_tiles * 8));
+    ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)G * max_tiles * KM_WARPS * 8));
     ka.max_tiles = max_tiles;
     ka.chunk = chunk;
     ka.amax = amax;
