@@ -333,6 +333,27 @@ def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
         out[name] = rec
     if params is None:
         out["learned_filter"] = "weights file missing"
+    # k-means++ draws decide which local optimum Lloyd reaches, so one clustering per variant says
+    # little about the embedding: ARI over 8 seeds (median) and of the best of 8 by inertia
+    G = fsc.Graph(rp, col, wt)
+    planted = torch.as_tensor(g.labels.astype(np.int32), device=rp.device)
+    kp = int(g.labels.max()) + 1
+    embs = {"plain_f32": lambda: fsc.embed(G, l, t, seed),
+            "plain_bf16": lambda: fsc.embed(G, l, t, seed, store=fsc.BF16, rescale=True)}
+    if params is not None:
+        embs["learned_filter_f32"] = lambda: fsc.filter_embed(G, l, k, seed, params=params, store=fsc.F32)[0]
+        embs["learned_filter_f16"] = lambda: fsc.filter_embed(G, l, k, seed, params=params, store=fsc.F16)[0]
+    for name, mk in embs.items():
+        E = mk()
+        aris = []
+        for s in range(8):
+            lab, _, _, _ = fsc.kmeans(E, l, k, seed + s)
+            aris.append(fsc.partition_scores(lab, planted, k, kp)[0])
+        lab, _, _, _, _ = fsc.kmeans_best(E, l, k, seed, 8)
+        rec = out.setdefault(name, {})
+        rec["ari_median_8_seeds"] = round(float(np.median(aris)), 4)
+        rec["ari_best_of_8"] = round(fsc.partition_scores(lab, planted, k, kp)[0], 4)
+    G.close()
     return out
 
 
