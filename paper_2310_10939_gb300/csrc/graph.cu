@@ -129,6 +129,15 @@ fsc_status status_from_bits(int bits) {
 // the float64 degree (correctly rounded sqrt and division, within 1-2 ulp of the exact values);
 // float64 arithmetic stays out of the unit-weight path, which it would slow down on this GPU.
 constexpr int kDegLanes = 8;
+
+// float64 value of an integer below 2^53, built with integer operations only (the float64 pipe
+// is a small fraction of the integer one on this GPU, and it bounded the unit-weight kernel).
+__device__ __forceinline__ double exact_u64_to_f64(unsigned long long c) {
+    if (c == 0) return 0.0;
+    const int e = 63 - __clzll((long long)c);
+    const unsigned long long mant = (c << (52 - e)) & ((1ull << 52) - 1);
+    return __longlong_as_double((long long)((((unsigned long long)(1023 + e)) << 52) | mant));
+}
 __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                                 const int32_t* __restrict__ col, const float* __restrict__ w,
                                                 int check_sorted, double* __restrict__ deg,
@@ -145,6 +154,7 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
     unsigned iso = 0;
     double vsum = 0.0, vsq = 0.0, vmax = 0.0;
     long long cnt_total = 0;
+    unsigned long long usq = 0, umax = 0;   // unit weights: sum of d^2 and max d as integers
     for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {   // warp-uniform trip count
         const int64_t i = base + grp;
         const bool active = i < n;
@@ -178,13 +188,25 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
 #pragma unroll
             for (int off = G / 2; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
         }
-        if (active && sub == 0) {
-            if (!w) {
-                d = (double)cnt;
-                cnt_total += cnt;
+        if (active && sub == 0 && !w) {
+            // unit weights: d is the exact count; everything stays in integer registers
+            const unsigned long long c = (unsigned long long)cnt;
+            cnt_total += cnt;
+            deg[i] = exact_u64_to_f64(c);
+            if (c < (1ull << 26)) usq += c * c;          // a thread's few rows cannot overflow
+            else vsq += (double)c * (double)c;            // only with repeated entries
+            umax = umax > c ? umax : c;
+            if (c) {
+                const float df = (float)c;
+                dinv[i] = 1.0f / sqrtf(df);
+                invdeg[i] = 1.0f / df;
             } else {
-                vsum += d;
+                dinv[i] = 0.0f;
+                invdeg[i] = 0.0f;
+                ++iso;
             }
+        } else if (active && sub == 0) {
+            vsum += d;
             deg[i] = d;
             vsq += d * d;
             vmax = fmax(vmax, d);
@@ -206,6 +228,10 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
     }
     if (w) {
         for (int off = 16; off > 0; off >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
+    }
+    if (!w) {   // fold the integer statistics in once per thread
+        vsq += (double)usq;
+        vmax = (double)umax;
     }
     for (int off = 16; off > 0; off >>= 1) {
         vsq += __shfl_xor_sync(0xffffffffu, vsq, off);
