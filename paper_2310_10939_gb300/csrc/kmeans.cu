@@ -37,11 +37,13 @@ struct KppArgs {
     int n, l, k;
     unsigned long long seed;
     float* d2[2];
-    long long* bsum[2];
-    long long* tsum[2];
+    long long* bsum[2];  // per block: exact D^2 total of its tiles
+    long long* tsum[2];  // per (tile, warp): exact D^2 total of its 128 points
+    long long* ttot[3];  // per tile: exact D^2 total (warp atomics), three in rotation
     int max_tiles;
     long long chunk;     // points per block, a multiple of KM_PPT
     unsigned* amax;      // max |x| (float bits), output for the Lloyd launch
+    int* near;           // per point: index (selection order) of its nearest chosen centre
     int64_t* seeds;
     float* c32;
     GridBarrier* bar;
@@ -50,14 +52,19 @@ struct KppArgs {
     int stall;
 };
 
+// A point whose D^2 = |x - c_a|^2 (c_a its nearest chosen centre) satisfies
+// sqrt(D^2) < |c - c_a| / 2 cannot move closer to a new centre c (triangle inequality:
+// |x - c| >= |c - c_a| - |x - c_a| > sqrt(D^2)), so its D^2 is carried over without loading
+// the point.  Both sides of the test are widened by KPP_EPS relative, far above float32
+// rounding of the distances, so a skipped point is one whose min(D^2, d) is D^2 exactly.
+constexpr float KPP_EPS = 1e-5f;
+
 template <int LP>
 __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     unsigned epoch = 0;   // grid barriers passed
-    extern __shared__ int s_chosen[];   // k entries
+    extern __shared__ int s_chosen[];   // k entries, then k floats: (|c_new - c_j| / 2)^2 shrunk
     __shared__ float s_c[LP];
     __shared__ long long s_red[KM_WARPS];
-    __shared__ long long s_pref[KM_MAX_BLOCKS];
-    __shared__ long long s_tiles[KM_THREADS];
     __shared__ long long s_T, s_base;
     __shared__ unsigned s_amax;
     __shared__ int s_bstar, s_tile, s_idx;
@@ -96,131 +103,163 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     }
     __syncthreads();
 
+    float* s_half2 = reinterpret_cast<float*>(s_chosen + a.k);
+    const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
     for (int r = 1; r < a.k; ++r) {
         const int cur = s_chosen[r - 1];
         if (tid < LP) s_c[tid] = tid < a.l ? a.X[(size_t)cur * LP + tid] : 0.f;
         __syncthreads();
+        // squared half-distances from the new centre to the earlier ones, shrunk by the margin
+        for (int j = tid; j < r - 1; j += KM_THREADS) {
+            float cj[LP];
+            load_point<LP>(a.X, s_chosen[j], a.l, cj);
+            const float h = 0.5f * sqrtf(sqdist<LP>(cj, s_c)) * (1.0f - KPP_EPS);
+            s_half2[j] = h * h;
+        }
+        __syncthreads();
         float* d2n = a.d2[r & 1];
         const float* d2o = a.d2[(r - 1) & 1];
         long long* bs = a.bsum[r & 1];
-        // ---- phase A: D^2 update, KM_PPT consecutive points per thread.  Exact partial sums are
-        // kept per (tile, warp) - 128 consecutive points - so no block barrier is needed per tile
-        // and the loads of successive tiles overlap; one block reduction forms the block total.
-        long long* ts = a.tsum[r & 1] + (size_t)b * a.max_tiles * KM_WARPS;
+        long long* tt = a.ttot[r % 3];              // exact D^2 total per tile (atomics)
+        long long* tz = a.ttot[(r + 1) % 3];        // cleared here for round r + 1
+        long long* wp = a.tsum[r & 1];              // exact D^2 total per (tile, warp)
+        // ---- phase A: D^2 update.  Tiles of KM_TILE points are dealt round-robin (block b takes
+        // b, b + G, ...): the points that cannot skip the new centre are that centre's
+        // neighbourhood, a contiguous run of vertices in a clustered graph, and dealing tiles
+        // spreads them over the blocks instead of loading one block while the others wait at the
+        // barrier.  The next tile's D^2 and nearest-centre indices load while this tile computes.
         long long wacc = 0;
-        int tile = 0;
-        for (long long t0 = lo; t0 < hi; t0 += KM_TILE, ++tile) {
+        float old_n[KM_PPT];
+        int na_n[KM_PPT];
+#pragma unroll
+        for (int u = 0; u < KM_PPT; ++u) {
+            const long long i = (long long)b * KM_TILE + (long long)KM_PPT * tid + u;
+            old_n[u] = (r > 1 && i < n) ? d2o[i] : 0.f;
+            na_n[u] = (r > 1 && i < n) ? a.near[i] : 0;
+        }
+        for (long long tile = b; tile < ntiles; tile += G) {
+            const long long t0 = tile * KM_TILE;
             const long long i0 = t0 + (long long)KM_PPT * tid;
-            float x[KM_PPT][LP];
             float old[KM_PPT];
+            int na[KM_PPT];
+            bool need[KM_PPT];
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
-                if (i0 + u < hi) load_point<LP>(a.X, i0 + u, a.l, x[u]);
-                old[u] = (r > 1 && i0 + u < hi) ? d2o[i0 + u] : 0.f;
+                old[u] = old_n[u];
+                na[u] = na_n[u];
+                const long long inext = i0 + (long long)G * KM_TILE + u;
+                old_n[u] = (r > 1 && inext < n) ? d2o[inext] : 0.f;
+                na_n[u] = (r > 1 && inext < n) ? a.near[inext] : 0;
             }
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                const bool in = i0 + u < n;
+                need[u] = in && (r == 1 || old[u] * (1.0f + KPP_EPS) * (1.0f + KPP_EPS) >= s_half2[na[u]]);
+            }
+            float x[KM_PPT][LP];
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u)
+                if (need[u]) load_point<LP>(a.X, i0 + u, a.l, x[u]);
             long long v = 0;
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
-                if (i0 + u < hi) {
-                    float dd = sqdist<LP>(x[u], s_c);
-                    if (r > 1) dd = fminf(dd, old[u]);
+                if (i0 + u < n) {
+                    float dd = old[u];
+                    if (need[u]) {
+                        const float dn = sqdist<LP>(x[u], s_c);
+                        if (r == 1 || dn < old[u]) {
+                            dd = dn;
+                            a.near[i0 + u] = r - 1;
+                        }
+                    }
                     d2n[i0 + u] = dd;
                     v += fixq(dd, sc.Sd);
                 }
             }
             v = warp_sum_ll(v);
-            if (lane == 0) ts[(size_t)tile * KM_WARPS + wid] = v;
+            if (lane == 0) {
+                wp[tile * KM_WARPS + wid] = v;
+                if (v) atomicAdd(reinterpret_cast<unsigned long long*>(tt + tile), (unsigned long long)v);
+                if (wid == 0) tz[tile] = 0;
+            }
             wacc += v;
         }
         const long long bacc = block_sum_ll(lane == 0 ? wacc : 0ll, s_red);
         if (tid == 0) bs[b] = bacc;
         if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
 
-        // ---- selection (identical in every block, exact integer arithmetic)
-        for (int q = tid; q < G; q += KM_THREADS) s_pref[q] = __ldcg(bs + q);
-        __syncthreads();
+        // ---- selection (identical in every block, exact integer arithmetic): the total from the
+        // block totals, then the tile, the warp segment and the point that hold the target
         if (wid == 0) {
-            const int per = (G + 31) / 32;
-            const int q0 = min(G, lane * per), q1 = min(G, q0 + per);
-            long long seg = 0;
-            for (int q = q0; q < q1; ++q) seg += s_pref[q];
-            long long incl = seg;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const long long u = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += u;
-            }
-            long long run = incl - seg;
-            for (int q = q0; q < q1; ++q) {
-                run += s_pref[q];
-                s_pref[q] = run;
-            }
-            __syncwarp();
-            const long long total = s_pref[G - 1];
-            if (total <= 0) {
-                if (lane == 0) s_bstar = -1;
-            } else {
-                const U64x4 rr = philox4x64_10(U64x4{(unsigned long long)r, 0ull, 0ull, 0ull}, a.seed, STREAM_KMEANSPP);
-                const unsigned long long U = rr.x >> 11, P = (unsigned long long)total;
-                const unsigned long long hi64 = __umul64hi(U, P), lo64 = U * P;
-                const long long T = (long long)((hi64 << 11) | (lo64 >> 53));   // floor(U * P / 2^53) < P
-                int found = -1;
-                for (int q = q0; q < q1; ++q)
-                    if (s_pref[q] > T) { found = q; break; }
-                const unsigned m = __ballot_sync(0xffffffffu, found >= 0);
-                const int bstar = m ? __shfl_sync(0xffffffffu, found, __ffs(m) - 1) : G - 1;
-                if (lane == 0) {
-                    s_bstar = bstar;
-                    s_base = bstar > 0 ? s_pref[bstar - 1] : 0;
-                    s_T = T;
+            long long t = 0;
+            for (int q = lane; q < G; q += 32) t += __ldcg(bs + q);
+            t = warp_sum_ll(t);
+            if (lane == 0) {
+                if (t <= 0) {
+                    s_bstar = -1;
+                } else {
+                    const U64x4 rr = philox4x64_10(U64x4{(unsigned long long)r, 0ull, 0ull, 0ull}, a.seed,
+                                                   STREAM_KMEANSPP);
+                    const unsigned long long U = rr.x >> 11, P = (unsigned long long)t;
+                    const unsigned long long hi64 = __umul64hi(U, P), lo64 = U * P;
+                    s_T = (long long)((hi64 << 11) | (lo64 >> 53));   // floor(U * P / 2^53) < P
+                    s_bstar = 0;
                 }
+                s_base = 0;
+                s_tile = -1;
+                s_idx = INT_MAX;
             }
         }
         __syncthreads();
         if (s_bstar < 0) {
             if (tid == 0) s_idx = lowest_unchosen(s_chosen, r);   // sum(D^2) = 0
         } else {
-            const int bq = s_bstar;
-            const long long blo = min(n, (long long)bq * chunk), bhi = min(n, blo + chunk);
-            const int nseg = (int)((bhi - blo + KM_TILE - 1) / KM_TILE) * KM_WARPS;   // (tile, warp) segments
-            const long long* tsb = a.tsum[r & 1] + (size_t)bq * a.max_tiles * KM_WARPS;
-            if (tid == 0) {
-                s_tile = -1;
-                s_idx = INT_MAX;
-            }
-            // the segment holding the target: block-parallel prefix over the block's segments
-            for (int q0 = 0; q0 < nseg; q0 += KM_THREADS) {
+            // the tile: block-parallel prefix over the tile totals in point order
+            for (long long q0 = 0; q0 < ntiles; q0 += KM_THREADS) {
                 __syncthreads();
                 const long long base = s_base;
-                const long long v = q0 + tid < nseg ? __ldcg(tsb + q0 + tid) : 0ll;
+                const long long v = q0 + tid < ntiles ? __ldcg(tt + q0 + tid) : 0ll;
                 const long long incl = block_scan_ll(v, s_red);
                 if (v > 0 && base + incl > s_T && base + incl - v <= s_T) {
-                    s_tile = q0 + tid;
+                    s_tile = (int)(q0 + tid);
                     s_base = base + incl - v;
                 }
                 __syncthreads();
                 if (s_tile >= 0) break;
                 if (tid == KM_THREADS - 1) s_base = base + incl;
             }
-            if (tid == 0 && s_tile < 0) s_tile = nseg - 1;   // defensive only (exact sums always cross)
+            if (tid == 0 && s_tile < 0) s_tile = (int)(ntiles - 1);   // defensive only (exact sums always cross)
             __syncthreads();
-            if (wid == 0) {   // the point within the segment: 32 lanes x KM_PPT consecutive points
-                const int tq = s_tile / KM_WARPS, wq = s_tile % KM_WARPS;
-                const long long i0 = blo + (long long)tq * KM_TILE + (long long)KM_PPT * (wq * 32 + lane);
-                long long q[KM_PPT];
-                long long v = 0;
-#pragma unroll
-                for (int u = 0; u < KM_PPT; ++u) {
-                    q[u] = i0 + u < bhi ? fixq(__ldcg(d2n + i0 + u), sc.Sd) : 0;
-                    v += q[u];
-                }
-                long long incl = v;
+            if (wid == 0) {
+                const long long tq = s_tile;
+                // the warp segment of the tile (KM_WARPS <= 32 partials, one per lane)
+                const long long wv = lane < KM_WARPS ? __ldcg(wp + tq * KM_WARPS + lane) : 0ll;
+                long long incl = wv;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
                     const long long t = __shfl_up_sync(0xffffffffu, incl, off);
                     if (lane >= off) incl += t;
                 }
-                long long run = incl - v + s_base;   // exclusive prefix of this lane
+                const long long base = s_base;
+                const unsigned m = __ballot_sync(0xffffffffu, wv > 0 && base + incl > s_T);
+                const int wq = m ? __ffs(m) - 1 : KM_WARPS - 1;
+                const long long wbase = base + __shfl_sync(0xffffffffu, incl - wv, wq);
+                // the point within the segment: 32 lanes x KM_PPT consecutive points
+                const long long i0 = tq * KM_TILE + (long long)KM_PPT * (wq * 32 + lane);
+                long long q[KM_PPT];
+                long long v = 0;
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    q[u] = i0 + u < n ? fixq(__ldcg(d2n + i0 + u), sc.Sd) : 0;
+                    v += q[u];
+                }
+                long long pin = v;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const long long t = __shfl_up_sync(0xffffffffu, pin, off);
+                    if (lane >= off) pin += t;
+                }
+                long long run = pin - v + wbase;   // exclusive prefix of this lane
 #pragma unroll
                 for (int u = 0; u < KM_PPT; ++u) {
                     run += q[u];
@@ -537,7 +576,7 @@ static int coop_blocks(K kern, size_t smem) {
 template <int LP>
 static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed, int max_iter, int32_t* labels,
                             double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats, cudaStream_t s) {
-    const size_t kpp_smem = (size_t)k * sizeof(int);
+    const size_t kpp_smem = (size_t)k * (sizeof(int) + sizeof(float));
     // private accumulation tables: as many as fit in 64 KB (at least one, at most one per warp)
     const size_t tab_bytes = (size_t)k * (LP + 1) * 8;
     int ntab = (int)(65536 / tab_bytes);
@@ -556,7 +595,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     long long chunk = ((long long)n + G - 1) / G;
     chunk = (chunk + KM_PPT - 1) / KM_PPT * KM_PPT;
     G = (int)(((long long)n + chunk - 1) / chunk);
-    const int max_tiles = (int)((chunk + KM_TILE - 1) / KM_TILE);
+    const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;   // k-means++ deals these round-robin
 
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
@@ -566,10 +605,12 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
     const size_t o_bs = off; off += 2 * up((size_t)G * 8);
-    const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * KM_WARPS * 8);
+    const size_t o_ts = off; off += 2 * up((size_t)ntiles * KM_WARPS * 8);
+    const size_t o_tt = off; off += 3 * up((size_t)ntiles * 8);
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
     const size_t o_seed = off; off += up((size_t)k * 8);
+    const size_t o_near = off; off += up((size_t)n * 4);
     char* ws = nullptr;
     cudaError_t e = pool_malloc(reinterpret_cast<void**>(&ws), off, s);
     if (e != cudaSuccess) return cuda_status(e);
@@ -592,11 +633,14 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         ka.bsum[0] = reinterpret_cast<long long*>(ws + o_bs);
         ka.bsum[1] = reinterpret_cast<long long*>(ws + o_bs + up((size_t)G * 8));
         ka.tsum[0] = reinterpret_cast<long long*>(ws + o_ts);
-        ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)G * max_tiles * KM_WARPS * 8));
-        ka.max_tiles = max_tiles;
+        ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)ntiles * KM_WARPS * 8));
+        for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(ws + o_tt + q * up((size_t)ntiles * 8));
+        ka.max_tiles = (int)ntiles;
+        if ((e = cudaMemsetAsync(ws + o_tt, 0, 3 * up((size_t)ntiles * 8), s)) != cudaSuccess) break;
         ka.chunk = chunk;
         ka.amax = amax;
         ka.seeds = reinterpret_cast<int64_t*>(ws + o_seed);
+        ka.near = reinterpret_cast<int*>(ws + o_near);
         ka.c32 = reinterpret_cast<float*>(ws + o_c32);
         ka.bar = bar;
         ka.status = call_status;
@@ -802,7 +846,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     char* ws = static_cast<char*>(basep);
     if (!ws) return FSC_ERR_CUDA;
 
-    const size_t kpp_smem = (size_t)k * sizeof(int);
+    const size_t kpp_smem = (size_t)k * (sizeof(int) + sizeof(float));
     const size_t tab_bytes = (size_t)k * (LP + 1) * 8;
     int ntab = (int)(65536 / tab_bytes);
     if (ntab > KM_WARPS) ntab = KM_WARPS;
@@ -819,7 +863,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     long long chunk = ((long long)n + G - 1) / G;
     chunk = (chunk + KM_PPT - 1) / KM_PPT * KM_PPT;
     G = (int)(((long long)n + chunk - 1) / chunk);
-    const int max_tiles = (int)((chunk + KM_TILE - 1) / KM_TILE);
+    const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;   // k-means++ deals these round-robin
 
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
@@ -829,10 +873,12 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
     const size_t o_bs = off; off += 2 * up((size_t)G * 8);
-    const size_t o_ts = off; off += 2 * up((size_t)G * max_tiles * KM_WARPS * 8);
+    const size_t o_ts = off; off += 2 * up((size_t)ntiles * KM_WARPS * 8);
+    const size_t o_tt = off; off += 3 * up((size_t)ntiles * 8);
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
     const size_t o_seed = off; off += up((size_t)k * 8);
+    const size_t o_near = off; off += up((size_t)n * 4);
     if (off > (size_t)FSC_KMEANS_STATIC_SCRATCH_BYTES) return FSC_ERR_TOO_LARGE;
 
     KmDevStats* st = reinterpret_cast<KmDevStats*>(ws + o_hdr);
@@ -853,11 +899,14 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     ka.bsum[0] = reinterpret_cast<long long*>(ws + o_bs);
     ka.bsum[1] = reinterpret_cast<long long*>(ws + o_bs + up((size_t)G * 8));
     ka.tsum[0] = reinterpret_cast<long long*>(ws + o_ts);
-    ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)G * max_tiles * KM_WARPS * 8));
-    ka.max_tiles = max_tiles;
+    ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)ntiles * KM_WARPS * 8));
+    for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(ws + o_tt + q * up((size_t)ntiles * 8));
+    ka.max_tiles = (int)ntiles;
+    FSC_CUDA(cudaMemsetAsync(ws + o_tt, 0, 3 * up((size_t)ntiles * 8), s));
     ka.chunk = chunk;
     ka.amax = amax;
     ka.seeds = reinterpret_cast<int64_t*>(ws + o_seed);
+    ka.near = reinterpret_cast<int*>(ws + o_near);
     ka.c32 = reinterpret_cast<float*>(ws + o_c32);
     ka.bar = bar;
     ka.status = call_status;
