@@ -306,7 +306,10 @@ def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
     def plain(G):
         return fsc.cluster(G, k, l, t, seed, store=fsc.BF16, rescale=True)[0], None
 
-    runs = {"plain_bf16": plain}
+    def orthogonal(G):   # the same l columns kept D-orthonormal (every 4 steps)
+        return fsc.kmeans(fsc.embed_orthogonal(G, l, t, seed, every=4), l, k, seed)[0], None
+
+    runs = {"plain_bf16": plain, "orthogonal_f32": orthogonal}
     if params is not None:
         runs["learned_filter_f32"] = lambda G: fsc.cluster_filtered(G, k, l, seed, params, store=fsc.F32)
         runs["learned_filter_f16"] = lambda G: fsc.cluster_filtered(G, k, l, seed, params, store=fsc.F16)
@@ -339,7 +342,8 @@ def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
     planted = torch.as_tensor(g.labels.astype(np.int32), device=rp.device)
     kp = int(g.labels.max()) + 1
     embs = {"plain_f32": lambda: fsc.embed(G, l, t, seed),
-            "plain_bf16": lambda: fsc.embed(G, l, t, seed, store=fsc.BF16, rescale=True)}
+            "plain_bf16": lambda: fsc.embed(G, l, t, seed, store=fsc.BF16, rescale=True),
+            "orthogonal_f32": lambda: fsc.embed_orthogonal(G, l, t, seed, every=4)}
     if params is not None:
         embs["learned_filter_f32"] = lambda: fsc.filter_embed(G, l, k, seed, params=params, store=fsc.F32)[0]
         embs["learned_filter_f16"] = lambda: fsc.filter_embed(G, l, k, seed, params=params, store=fsc.F16)[0]

@@ -206,6 +206,18 @@ fsc_status fsc_kmeans_static(const float* emb, int64_t n, int l, int ld, int k, 
                              void* stream);
 
 /*
+ * fsc_embed_orthogonal - orthogonal iteration: t power steps of M (Algorithm 1) on a block of l
+ * vectors that is D-orthonormalised after every `every` steps and after the last (CholeskyQR2,
+ * the unique basis with positive-diagonal R).  With l = k it is the "PM k Vectors" variant the
+ * paper compares against (Sec. 4); the span after t steps is that of M^t X0, so only the basis,
+ * not the subspace, differs from fsc_embed.  emb: n x fsc_pad_l(l) floats = D^-1/2 Q (columns
+ * orthonormal in x-space).  Float32 only; opts->flags must be 0.  A column linearly dependent on
+ * the earlier ones comes out zero.  Same start block as fsc_embed(seed).  Asynchronous.
+ */
+fsc_status fsc_embed_orthogonal(const fsc_graph* g, int l, int t, int every, uint64_t seed, float* emb,
+                                const fsc_embed_opts* opts, void* stream);
+
+/*
  * fsc_kmeans_best - k-means with restarts (not in the paper; the usual library practice of
  * keeping the best of several k-means runs).  Run r (r = 0 .. n_init-1) is fsc_kmeans with
  * seed + r (its own k-means++ draws); the run of lowest inertia is kept, ties going to the

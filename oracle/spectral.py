@@ -90,6 +90,30 @@ def embed(g, l: int, t: int, seed: int, x0: np.ndarray | None = None) -> np.ndar
     return inv_sqrt_degrees(degrees(g))[:, None] * Y
 
 
+def orthonormal_basis(Y: np.ndarray) -> np.ndarray:
+    """Q with orthonormal columns and Y = Q R, R upper triangular with positive diagonal (the
+    unique thin QR factor of a full-rank Y; numpy's Householder QR with the signs fixed)."""
+    Q, R = np.linalg.qr(Y)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s
+
+
+def orthogonal_iteration(g, l: int, t: int, every: int, seed: int, x0: np.ndarray | None = None) -> np.ndarray:
+    """The power method on a block of l vectors kept orthonormal (orthogonal iteration; with
+    l = k it is the "PM k Vectors" variant compared in Sec. 4): Y <- M Y for t steps, Y replaced by
+    its orthonormal basis (above) after every `every` steps and after the last; returns the
+    embedding D^-1/2 Y (n x l)."""
+    from .rng import gaussian_block
+    M = signless_laplacian(g)
+    Y = gaussian_block(g.n, l, seed) if x0 is None else np.array(x0, dtype=np.float64)
+    for it in range(t):
+        Y = M @ Y
+        if (it + 1) % every == 0 or it == t - 1:
+            Y = orthonormal_basis(Y)
+    return inv_sqrt_degrees(degrees(g))[:, None] * Y
+
+
 def dense_signless(g) -> np.ndarray:
     """M as a dense float64 matrix (small graphs)."""
     return signless_laplacian(g).toarray()

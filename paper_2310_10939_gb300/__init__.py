@@ -22,7 +22,7 @@ __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
     "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
     "F32", "BF16", "F16", "FILTER_NO_FALLBACK", "release_cached_memory", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
-    "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
+    "embed_orthogonal", "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
@@ -98,6 +98,8 @@ def lib() -> C.CDLL:
         L.fsc_power_step.argtypes = [vp, i32, i32, vp, vp, i32, vp]
         L.fsc_kmeans.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
         L.fsc_kmeans_static.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
+        L.fsc_embed_orthogonal.argtypes = [vp, i32, i32, i32, u64, vp, C.POINTER(EmbedOpts), vp]
+        L.fsc_embed_orthogonal.restype = i32
         L.fsc_kmeans_best.argtypes = [vp, i64, i32, i32, i32, u64, i32, i32, vp, vp, vp, C.POINTER(KmeansStats),
                                       C.POINTER(i32), vp]
         L.fsc_kmeans_best.restype = i32
@@ -313,6 +315,20 @@ def kmeans(emb, l: int, k: int, seed: int, max_iter: int = 100, labels=None, wan
                             _ptr(labels), _ptr(cen), _ptr(sd), C.byref(st) if sync else None, _stream(stream)),
            "fsc_kmeans")
     return labels, (st.as_dict() if sync else None), cen, sd
+
+
+def embed_orthogonal(g: Graph, l: int, t: int, seed: int, every: int = 1, out=None, threads_per_row: int = 0,
+                     events=None, stream=None):
+    """fsc_embed_orthogonal: orthogonal iteration (the power method on a block kept D-orthonormal);
+    returns (or fills) the n x pad_l(l) float32 embedding D^-1/2 Q."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=g.row_ptr.device)
+    _require_cuda(out, torch.float32, "out")
+    o = _opts(False, threads_per_row, events)
+    _check(lib().fsc_embed_orthogonal(g.handle, int(l), int(t), int(every), int(seed) & (2**64 - 1), _ptr(out),
+                                      C.byref(o), _stream(stream)), "fsc_embed_orthogonal")
+    return out
 
 
 def kmeans_best(emb, l: int, k: int, seed: int, n_init: int, max_iter: int = 100, labels=None,

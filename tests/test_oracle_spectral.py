@@ -157,3 +157,28 @@ def test_power_method_t0_is_identity_and_embed_scales():
     assert np.array_equal(spectral.power_method(spectral.signless_laplacian(g), X, 0), X)
     d = spectral.degrees(g)
     assert np.allclose(spectral.embed(g, 2, 0, 1), X / np.sqrt(d)[:, None], rtol=1e-15)
+
+
+def test_orthogonal_iteration_spans_the_power_method_block():
+    """Orthonormalising never changes the span, so orthogonal iteration with any interval gives
+    the orthonormal basis (positive-diagonal R) of M^t X0 itself: the same Q as one QR at the end."""
+    g = W.sbm([40, 50, 60], 0.3, 0.02, 3)
+    X0 = gaussian_block(g.n, 3, 11)
+    Y = spectral.power_method(spectral.signless_laplacian(g), X0, 9)
+    Q_end = spectral.inv_sqrt_degrees(spectral.degrees(g))[:, None] * spectral.orthonormal_basis(Y)
+    for every in (1, 2, 4, 9):
+        Z = spectral.orthogonal_iteration(g, 3, 9, every, 11)
+        assert np.allclose(Z, Q_end, atol=1e-10), every
+
+
+def test_orthogonal_iteration_converges_to_the_top_eigenvectors():
+    """On a graph with a clear gap after the top l eigenvalues of M, the basis converges to that
+    eigenspace (dense eigendecomposition), and its columns are orthonormal in x-space."""
+    g = W.sbm([60, 60, 60, 60], 0.5, 0.01, 5)
+    l = 4
+    Z = spectral.orthogonal_iteration(g, l, 200, 5, 2)
+    Q = Z / spectral.inv_sqrt_degrees(spectral.degrees(g))[:, None]
+    assert np.allclose(Q.T @ Q, np.eye(l), atol=1e-10)
+    w, V = np.linalg.eigh(spectral.dense_signless(g))
+    P = V[:, np.argsort(-w)[:l]]
+    assert np.linalg.norm(P @ P.T - Q @ Q.T, 2) < 1e-6
