@@ -218,6 +218,22 @@ fsc_status fsc_embed_orthogonal(const fsc_graph* g, int l, int t, int every, uin
                                 const fsc_embed_opts* opts, void* stream);
 
 /*
+ * fsc_knn_graph - the k-nearest-neighbour graph of a point set (the Sec. 4.2 pre-processing,
+ * where the paper clusters the 10-NN graph of each dataset).  points: device float32 n x dim,
+ * row-major; dim <= 64, 1 <= knn <= 16, knn < n, n * knn < 2^31.  Distances: float32
+ * sum over columns in order of (x_i[c] - x_j[c])^2, no fused multiply-add; neighbours of i: the
+ * knn points j != i of smallest distance, ties to the lower index; symmetrised by union; weight
+ * of {i, j}: exp(-d2 / sigma^2), sigma = median (mean of the two middle values for an even
+ * count) of the n * knn directed distances sqrt(d2), found exactly.  Output CSR (both
+ * directions, columns increasing in each row): row_ptr (device int64, n + 1), col (device
+ * int32) and w (device float32, may be NULL) with room for capacity >= 2 * n * knn entries;
+ * *nnz (host) receives the entry count, *sigma (host, optional) sigma.  Synchronous.  The
+ * result can be passed to fsc_create_graph (FSC_VALIDATE_SYMMETRY accepts it).
+ */
+fsc_status fsc_knn_graph(const float* points, int64_t n, int dim, int knn, int64_t* row_ptr, int32_t* col, float* w,
+                         int64_t capacity, int64_t* nnz, double* sigma, void* stream);
+
+/*
  * fsc_kmeans_best - k-means with restarts (not in the paper; the usual library practice of
  * keeping the best of several k-means runs).  Run r (r = 0 .. n_init-1) is fsc_kmeans with
  * seed + r (its own k-means++ draws); the run of lowest inertia is kept, ties going to the

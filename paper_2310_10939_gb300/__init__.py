@@ -22,7 +22,7 @@ __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
     "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
     "F32", "BF16", "F16", "FILTER_NO_FALLBACK", "release_cached_memory", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
-    "embed_orthogonal", "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
+    "knn_graph", "embed_orthogonal", "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
@@ -98,6 +98,8 @@ def lib() -> C.CDLL:
         L.fsc_power_step.argtypes = [vp, i32, i32, vp, vp, i32, vp]
         L.fsc_kmeans.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
         L.fsc_kmeans_static.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
+        L.fsc_knn_graph.argtypes = [vp, i64, i32, i32, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(C.c_double), vp]
+        L.fsc_knn_graph.restype = i32
         L.fsc_embed_orthogonal.argtypes = [vp, i32, i32, i32, u64, vp, C.POINTER(EmbedOpts), vp]
         L.fsc_embed_orthogonal.restype = i32
         L.fsc_kmeans_best.argtypes = [vp, i64, i32, i32, i32, u64, i32, i32, vp, vp, vp, C.POINTER(KmeansStats),
@@ -315,6 +317,24 @@ def kmeans(emb, l: int, k: int, seed: int, max_iter: int = 100, labels=None, wan
                             _ptr(labels), _ptr(cen), _ptr(sd), C.byref(st) if sync else None, _stream(stream)),
            "fsc_kmeans")
     return labels, (st.as_dict() if sync else None), cen, sd
+
+
+def knn_graph(points, knn: int, weighted: bool = True, stream=None):
+    """fsc_knn_graph: the union-symmetrised kNN graph of float32 CUDA points (n x dim).
+    Returns (row_ptr int64, col int32, w float32 or None, sigma) CUDA tensors (col, w trimmed)."""
+    torch = _torch()
+    _require_cuda(points, torch.float32, "points")
+    n, dim = points.shape
+    cap = 2 * n * int(knn)
+    rp = torch.empty(n + 1, dtype=torch.int64, device=points.device)
+    col = torch.empty(cap, dtype=torch.int32, device=points.device)
+    w = torch.empty(cap, dtype=torch.float32, device=points.device) if weighted else None
+    nnz = C.c_int64(0)
+    sig = C.c_double(0.0)
+    _check(lib().fsc_knn_graph(_ptr(points), int(n), int(dim), int(knn), _ptr(rp), _ptr(col), _ptr(w), int(cap),
+                               C.byref(nnz), C.byref(sig), _stream(stream)), "fsc_knn_graph")
+    m = int(nnz.value)
+    return rp, col[:m], (w[:m] if w is not None else None), float(sig.value)
 
 
 def embed_orthogonal(g: Graph, l: int, t: int, seed: int, every: int = 1, out=None, threads_per_row: int = 0,

@@ -1,0 +1,61 @@
+"""kNN-graph construction on the GPU against the oracle's plain definition."""
+import numpy as np
+import pytest
+
+import workloads as W
+from _helpers import require_cuda
+from oracle import knn as ok
+from oracle import metrics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+@pytest.mark.parametrize("n,dim,knn", [(3000, 8, 10), (4000, 32, 10), (1500, 20, 16), (600, 3, 1)])
+def test_knn_graph_matches_oracle(torch, n, dim, knn):
+    import paper_2310_10939_gb300 as fsc
+    X, _ = W.mixture_points(n, dim, 6, seed=n + dim)
+    X = X.astype(np.float32)
+    rp, col, w, sigma = fsc.knn_graph(torch.as_tensor(X, device="cuda"), knn)
+    r_rp, r_col, r_w, r_sigma, _, _ = ok.knn_graph(X, knn)
+    assert np.array_equal(rp.cpu().numpy(), r_rp)
+    assert np.array_equal(col.cpu().numpy(), r_col)
+    assert abs(sigma - r_sigma) <= 1e-12 * r_sigma
+    # w = exp(-a) with a = d2 / sigma^2 formed in float32: its rounding (a few 2^-24 relative)
+    # becomes an absolute error of the exponent, so the relative bound grows with a
+    a = -np.log(r_w)
+    assert (np.abs(w.cpu().numpy() - r_w) <= r_w * (1e-6 + 3e-7 * a)).all()
+
+
+def test_knn_graph_full_size_sampled(torch):
+    """2e5 points in R^32 (the kNN workload): sampled rows against brute force, and the graph
+    passes the library's own symmetry validation."""
+    import paper_2310_10939_gb300 as fsc
+    X, lab = W.mixture_points(200_000, 32, 10, seed=5)
+    X = X.astype(np.float32)
+    rp, col, w, sigma = fsc.knn_graph(torch.as_tensor(X, device="cuda"), 10)
+    rp_h, col_h = rp.cpu().numpy(), col.cpu().numpy()
+    rng = np.random.default_rng(1)
+
+    def own(i):
+        d = ok.sqdist32(X[i], X)
+        d[i] = np.inf
+        return set(np.lexsort((np.arange(X.shape[0]), d))[:10].tolist())
+
+    for i in rng.choice(X.shape[0], 12, replace=False):
+        row = set(col_h[rp_h[i]:rp_h[i + 1]].tolist())
+        oi = own(i)
+        assert oi <= row
+        for j in row - oi:                      # every other entry is a reverse neighbour
+            assert i in own(j)
+    G = fsc.Graph(rp, col, w, validate_symmetry=True)
+    labels, _ = fsc.cluster(G, 10, 4, 20, 5)
+    # the input generator's graph of the same points (float64 weights, its own neighbour search)
+    ref = fsc.Graph.from_workload(W.knn_mixture(200_000, 32, 10, 10, seed=5, device="cuda"))
+    ref_labels, _ = fsc.cluster(ref, 10, 4, 20, 5)
+    a, a_ref = metrics.ari(labels.cpu().numpy(), lab), metrics.ari(ref_labels.cpu().numpy(), lab)
+    assert abs(a - a_ref) <= 0.02, (a, a_ref)

@@ -13,6 +13,7 @@ from .graphs import (
     cycle,
     complete,
     knn_mixture,
+    mixture_points,
     image_grid,
     from_edges,
     with_isolated,
@@ -32,6 +33,7 @@ __all__ = [
     "cycle",
     "complete",
     "knn_mixture",
+    "mixture_points",
     "image_grid",
     "from_edges",
     "with_isolated",

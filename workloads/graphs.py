@@ -209,6 +209,16 @@ def _weighted_edges(n, u, v, w64, labels, name, meta):
     return from_edges(n, u[keep], v[keep], w32[keep], labels, name, meta)
 
 
+def mixture_points(npts: int, dim: int, ncomp: int, seed: int):
+    """The points of knn_mixture: ``ncomp`` equally likely unit-variance Gaussian components with
+    means drawn from N(0, 4 I).  Returns (points float64 npts x dim, component labels)."""
+    rng = np.random.default_rng(seed)
+    means = rng.normal(0.0, 2.0, size=(ncomp, dim))
+    labels = rng.integers(0, ncomp, size=npts)
+    x = means[labels] + rng.normal(0.0, 1.0, size=(npts, dim))
+    return x, labels
+
+
 def knn_mixture(npts: int, dim: int, ncomp: int, knn: int, seed: int, device: str = "cpu",
                 name: str = "knn") -> Graph:
     """k-nearest-neighbour graph of a Gaussian mixture (the Sec. 4.2 pre-processing).
@@ -221,10 +231,7 @@ def knn_mixture(npts: int, dim: int, ncomp: int, knn: int, seed: int, device: st
     neighbours with torch on the GPU (for large point sets); the weights are
     always computed in float64 on the host.
     """
-    rng = np.random.default_rng(seed)
-    means = rng.normal(0.0, 2.0, size=(ncomp, dim))
-    labels = rng.integers(0, ncomp, size=npts)
-    x = means[labels] + rng.normal(0.0, 1.0, size=(npts, dim))
+    x, labels = mixture_points(npts, dim, ncomp, seed)
     nbr = _knn_indices(x, knn, device)                   # npts x knn, excludes self
     d_dir = np.sqrt(((x[:, None, :] - x[nbr]) ** 2).sum(-1)) if npts * knn * dim <= 5e7 else \
         np.concatenate([np.sqrt(((x[s:s + 4096, None, :] - x[nbr[s:s + 4096]]) ** 2).sum(-1))
