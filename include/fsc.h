@@ -234,6 +234,17 @@ fsc_status fsc_knn_graph(const float* points, int64_t n, int dim, int knn, int64
                          int64_t capacity, int64_t* nnz, double* sigma, void* stream);
 
 /*
+ * fsc_top_eigenvectors - Rayleigh-Ritz on the fsc_embed_orthogonal basis: with Q that basis
+ * (x-space, orthonormal), H = Q^T M Q (one more power step and a D-weighted Gram), H = V diag(theta)
+ * V^T by cyclic Jacobi (float64, l <= 8), and emb <- D^-1/2 Q V, columns in decreasing theta, each
+ * column's largest entry of V positive.  For t large enough the pairs converge to the top l
+ * eigenpairs of M: the "k Eigs" embedding of the paper's comparison (Sec. 4) when l = k <= 8.
+ * values: host double[l] <- theta.  Synchronous.
+ */
+fsc_status fsc_top_eigenvectors(const fsc_graph* g, int l, int t, int every, uint64_t seed, float* emb,
+                                double* values, const fsc_embed_opts* opts, void* stream);
+
+/*
  * fsc_kmeans_best - k-means with restarts (not in the paper; the usual library practice of
  * keeping the best of several k-means runs).  Run r (r = 0 .. n_init-1) is fsc_kmeans with
  * seed + r (its own k-means++ draws); the run of lowest inertia is kept, ties going to the

@@ -114,6 +114,19 @@ def orthogonal_iteration(g, l: int, t: int, every: int, seed: int, x0: np.ndarra
     return inv_sqrt_degrees(degrees(g))[:, None] * Y
 
 
+def ritz_vectors(g, l: int, t: int, every: int, seed: int):
+    """Rayleigh-Ritz on the orthogonal-iteration basis: with Q its x-space basis (orthonormal),
+    H = Q^T M Q, H = V diag(theta) V^T (theta descending); returns (theta, D^-1/2 Q V).  For t
+    large enough the pairs converge to the top l eigenpairs of M (the "k Eigs" embedding of the
+    paper's comparison when l = k)."""
+    dm = inv_sqrt_degrees(degrees(g))[:, None]
+    Q = orthogonal_iteration(g, l, t, every, seed) / np.where(dm > 0, dm, 1.0)
+    H = Q.T @ (signless_laplacian(g) @ Q)
+    theta, V = np.linalg.eigh(0.5 * (H + H.T))
+    order = np.argsort(-theta, kind="stable")
+    return theta[order], dm * (Q @ V[:, order])
+
+
 def dense_signless(g) -> np.ndarray:
     """M as a dense float64 matrix (small graphs)."""
     return signless_laplacian(g).toarray()

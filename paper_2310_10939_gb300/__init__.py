@@ -22,7 +22,7 @@ __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
     "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
     "F32", "BF16", "F16", "FILTER_NO_FALLBACK", "release_cached_memory", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
-    "knn_graph", "embed_orthogonal", "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
+    "knn_graph", "embed_orthogonal", "top_eigenvectors", "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
 ]
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
@@ -102,6 +102,8 @@ def lib() -> C.CDLL:
         L.fsc_knn_graph.restype = i32
         L.fsc_embed_orthogonal.argtypes = [vp, i32, i32, i32, u64, vp, C.POINTER(EmbedOpts), vp]
         L.fsc_embed_orthogonal.restype = i32
+        L.fsc_top_eigenvectors.argtypes = [vp, i32, i32, i32, u64, vp, C.POINTER(C.c_double), C.POINTER(EmbedOpts), vp]
+        L.fsc_top_eigenvectors.restype = i32
         L.fsc_kmeans_best.argtypes = [vp, i64, i32, i32, i32, u64, i32, i32, vp, vp, vp, C.POINTER(KmeansStats),
                                       C.POINTER(i32), vp]
         L.fsc_kmeans_best.restype = i32
@@ -349,6 +351,22 @@ def embed_orthogonal(g: Graph, l: int, t: int, seed: int, every: int = 1, out=No
     _check(lib().fsc_embed_orthogonal(g.handle, int(l), int(t), int(every), int(seed) & (2**64 - 1), _ptr(out),
                                       C.byref(o), _stream(stream)), "fsc_embed_orthogonal")
     return out
+
+
+def top_eigenvectors(g: Graph, l: int, t: int, seed: int, every: int = 4, out=None, threads_per_row: int = 0,
+                     stream=None):
+    """fsc_top_eigenvectors: Ritz pairs of M from orthogonal iteration.  Returns (values (l,) numpy,
+    embedding n x pad_l(l) = D^-1/2 [Ritz vectors])."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=g.row_ptr.device)
+    _require_cuda(out, torch.float32, "out")
+    vals = (C.c_double * int(l))()
+    o = _opts(False, threads_per_row, None)
+    _check(lib().fsc_top_eigenvectors(g.handle, int(l), int(t), int(every), int(seed) & (2**64 - 1), _ptr(out), vals,
+                                      C.byref(o), _stream(stream)), "fsc_top_eigenvectors")
+    import numpy as _np
+    return _np.array(vals[:]), out
 
 
 def kmeans_best(emb, l: int, k: int, seed: int, n_init: int, max_iter: int = 100, labels=None,

@@ -160,9 +160,201 @@ static cudaError_t orthonormalize(int LP, int n, int l, float* z, const double* 
     }
 }
 
+// ---- Rayleigh-Ritz ---------------------------------------------------------------------------
+// Per-block partial sums of the cross Gram sum_v d(v) a_v b_v^T (full LP x LP, row-major).
+template <int LP>
+__global__ void __launch_bounds__(kOrthoThreads) k_gram2(int n, const float* __restrict__ za,
+                                                         const float* __restrict__ zb, const double* __restrict__ deg,
+                                                         double* __restrict__ part) {
+    constexpr int NT = LP * LP;
+    __shared__ float s_w[kOrthoThreads / 32][NT];
+    float acc[NT];
+#pragma unroll
+    for (int e = 0; e < NT; ++e) acc[e] = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float a[LP], b[LP];
+        load_row<LP, float>(za + (size_t)i * LP, a);
+        load_row<LP, float>(zb + (size_t)i * LP, b);
+        const float d = (float)deg[i];
+#pragma unroll
+        for (int x = 0; x < LP; ++x) {
+            const float dx = d * a[x];
+#pragma unroll
+            for (int y = 0; y < LP; ++y) acc[x * LP + y] = fmaf(dx, b[y], acc[x * LP + y]);
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int e = 0; e < NT; ++e) {
+        float x = acc[e];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) s_w[wid][e] = x;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NT; e += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < kOrthoThreads / 32; ++w) t += (double)s_w[w][e];
+        part[(size_t)blockIdx.x * NT + e] = t;
+    }
+}
+
+// One block: H = (G + G^T) / 2 over the leading l x l, eigenpairs by cyclic Jacobi (float64),
+// sorted by decreasing value; each vector's sign fixed so that its largest component is
+// positive.  Writes V (LP x LP floats, identity on the padding) and the values.
+template <int LP>
+__global__ void k_ritz(const double* __restrict__ part, int nb, int l, float* __restrict__ vout,
+                       double* __restrict__ values) {
+    constexpr int NT = LP * LP;
+    __shared__ double s_g[NT];
+    for (int e = threadIdx.x; e < NT; e += blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < nb; ++q) t += part[(size_t)q * NT + e];
+        s_g[e] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double A[LP][LP], V[LP][LP];
+    for (int a = 0; a < LP; ++a)
+        for (int b = 0; b < LP; ++b) {
+            A[a][b] = (a < l && b < l) ? 0.5 * (s_g[a * LP + b] + s_g[b * LP + a]) : 0.0;
+            V[a][b] = a == b ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int a = 0; a < l; ++a)
+            for (int b = 0; b < l; ++b) {
+                tot += A[a][b] * A[a][b];
+                if (a != b) off += A[a][b] * A[a][b];
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < l - 1; ++p)
+            for (int q = p + 1; q < l; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
+                for (int r = 0; r < l; ++r) {   // A <- J^T A J, V <- V J
+                    const double arp = A[r][p], arq = A[r][q];
+                    A[r][p] = c * arp - sn * arq;
+                    A[r][q] = sn * arp + c * arq;
+                }
+                for (int r = 0; r < l; ++r) {
+                    const double apr = A[p][r], aqr = A[q][r];
+                    A[p][r] = c * apr - sn * aqr;
+                    A[q][r] = sn * apr + c * aqr;
+                }
+                for (int r = 0; r < l; ++r) {
+                    const double vrp = V[r][p], vrq = V[r][q];
+                    V[r][p] = c * vrp - sn * vrq;
+                    V[r][q] = sn * vrp + c * vrq;
+                }
+            }
+    }
+    int order[LP];
+    for (int a = 0; a < LP; ++a) order[a] = a;
+    for (int a = 0; a < l; ++a)   // selection sort by decreasing eigenvalue (stable in index)
+        for (int b = a + 1; b < l; ++b)
+            if (A[order[b]][order[b]] > A[order[a]][order[a]]) {
+                const int t = order[a];
+                order[a] = order[b];
+                order[b] = t;
+            }
+    for (int a = 0; a < LP; ++a)
+        for (int b = 0; b < LP; ++b) vout[a * LP + b] = (a == b && a >= l) ? 1.f : 0.f;
+    for (int c = 0; c < l; ++c) {
+        const int src = order[c];
+        int big = 0;
+        for (int r = 1; r < l; ++r)
+            if (fabs(V[r][src]) > fabs(V[big][src])) big = r;
+        const double sgn = V[big][src] < 0 ? -1.0 : 1.0;
+        for (int r = 0; r < l; ++r) vout[r * LP + c] = (float)(sgn * V[r][src]);
+        values[c] = A[src][src];
+    }
+}
+
+// z_v <- z_v V for every row (full LP x LP matrix), in place.
+template <int LP>
+__global__ void __launch_bounds__(kOrthoThreads) k_apply_full(int n, float* __restrict__ z, const float* __restrict__ m) {
+    __shared__ float s_m[LP * LP];
+    for (int q = threadIdx.x; q < LP * LP; q += blockDim.x) s_m[q] = m[q];
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float v[LP], o[LP];
+        load_row<LP, float>(z + (size_t)i * LP, v);
+#pragma unroll
+        for (int c = 0; c < LP; ++c) {
+            float t = 0.f;
+#pragma unroll
+            for (int a = 0; a < LP; ++a) t = fmaf(v[a], s_m[a * LP + c], t);
+            o[c] = t;
+        }
+        store_row<LP, float>(z + (size_t)i * LP, o);
+    }
+}
+
+template <int LP>
+static cudaError_t ritz_lp(int n, int l, float* z, const float* mz, const double* deg, double* part, int nb,
+                           float* vmat, double* values, cudaStream_t s) {
+    k_gram2<LP><<<nb, kOrthoThreads, 0, s>>>(n, z, mz, deg, part);
+    k_ritz<LP><<<1, 64, 0, s>>>(part, nb, l, vmat, values);
+    k_apply_full<LP><<<nb, kOrthoThreads, 0, s>>>(n, z, vmat);
+    return cudaGetLastError();
+}
+
 }  // namespace fsc
 
 using namespace fsc;
+
+extern "C" fsc_status fsc_embed_orthogonal(const fsc_graph* gc, int l, int t, int every, uint64_t seed, float* emb,
+                                           const fsc_embed_opts* opts, void* stream);
+
+extern "C" fsc_status fsc_top_eigenvectors(const fsc_graph* gc, int l, int t, int every, uint64_t seed, float* emb,
+                                           double* values, const fsc_embed_opts* opts, void* stream) {
+    fsc_graph* g = const_cast<fsc_graph*>(gc);
+    if (!g || !emb || !values || l < 1 || l > 8 || t < 0 || every < 1) return FSC_ERR_INVALID_ARG;
+    fsc_status rc = fsc_embed_orthogonal(gc, l, t, every, seed, emb, opts, stream);
+    if (rc != FSC_OK) return rc;
+    const int LP = pad_l(l);
+    const int n = (int)g->n;
+    cudaStream_t s = as_stream(stream);
+    long long nb = ((long long)n + kOrthoThreads - 1) / kOrthoThreads;
+    const long long cap = (long long)device_props().num_sms * 8;
+    if (nb > cap) nb = cap;
+    if (nb < 1) nb = 1;
+    const size_t part_bytes = ((size_t)nb * 64 * 8 + 255) & ~(size_t)255;
+    char* scratch = nullptr;
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&scratch), part_bytes + 512, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    double* part = reinterpret_cast<double*>(scratch);
+    float* vmat = reinterpret_cast<float*>(scratch + part_bytes);
+    double* dvals = reinterpret_cast<double*>(scratch + part_bytes + 256);
+    do {
+        // M Q in embedding coordinates: one power step of the basis into the workspace
+        StepArgs a{};
+        a.n = n;
+        a.rp = g->row_ptr;
+        a.col = g->col;
+        a.w = g->w;
+        a.invdeg = g->invdeg;
+        a.col_off = g->col_off;
+        a.zin = emb;
+        a.zout = g->ws;
+        const int G = choose_threads_per_row(g, opts ? opts->threads_per_row : 0, LP, (int)FSC_F32);
+        if ((e = launch_step_f32(LP, G, g->w != nullptr, a, s)) != cudaSuccess) break;
+        const float* mz = static_cast<const float*>(g->ws);
+        switch (LP) {
+            case 1: e = ritz_lp<1>(n, l, emb, mz, g->deg, part, (int)nb, vmat, dvals, s); break;
+            case 2: e = ritz_lp<2>(n, l, emb, mz, g->deg, part, (int)nb, vmat, dvals, s); break;
+            case 4: e = ritz_lp<4>(n, l, emb, mz, g->deg, part, (int)nb, vmat, dvals, s); break;
+            default: e = ritz_lp<8>(n, l, emb, mz, g->deg, part, (int)nb, vmat, dvals, s); break;
+        }
+        if (e != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(values, dvals, sizeof(double) * l, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(s);
+    } while (0);
+    pool_free(scratch, s);
+    return e == cudaSuccess ? FSC_OK : cuda_status(e);
+}
 
 extern "C" fsc_status fsc_embed_orthogonal(const fsc_graph* gc, int l, int t, int every, uint64_t seed, float* emb,
                                            const fsc_embed_opts* opts, void* stream) {

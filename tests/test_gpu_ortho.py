@@ -59,3 +59,37 @@ def test_pm_k_vectors_clusters_an_sbm(torch):
     a_gpu = metrics.ari(lab.cpu().numpy(), g.labels)
     a_ref = metrics.ari(ref["labels"], g.labels)
     assert a_gpu >= a_ref - 0.01, (a_gpu, a_ref)
+
+
+def test_ritz_pairs_match_dense_eigenpairs(torch):
+    """Rayleigh-Ritz on the orthogonal-iteration basis: values and vectors (up to sign) against a
+    dense float64 eigendecomposition of M on a graph with a clear gap."""
+    import paper_2310_10939_gb300 as fsc
+    g = W.sbm([150, 200, 250, 300], 0.2, 0.01, 17)
+    G = fsc.Graph.from_workload(g)
+    l = 4
+    vals, emb = fsc.top_eigenvectors(G, l, 200, 17, every=5)
+    w, V = np.linalg.eigh(spectral.dense_signless(g))
+    order = np.argsort(-w)[:l]
+    assert np.allclose(vals, w[order], atol=1e-5)
+    dm = spectral.inv_sqrt_degrees(spectral.degrees(g))[:, None]
+    Q = emb.cpu().numpy()[:, :l].astype(np.float64) / dm
+    for a in range(l):
+        assert abs(float(Q[:, a] @ V[:, order[a]])) > 1 - 1e-3, a
+    ref_vals, ref_Z = spectral.ritz_vectors(g, l, 200, 5, 17)
+    assert np.allclose(vals, ref_vals, atol=1e-5)
+
+
+def test_k_eigs_embedding_clusters_an_sbm(torch):
+    """The paper's "k Eigs" baseline for k <= 8: k-means on the top-k Ritz vectors."""
+    import paper_2310_10939_gb300 as fsc
+    g = W.sbm_by_degree(30_000, 8, 20.0, 2.0, seed=23)
+    G = fsc.Graph.from_workload(g)
+    k = 8
+    _, emb = fsc.top_eigenvectors(G, k, 60, 23, every=5)
+    lab, _, _, _ = fsc.kmeans(emb, k, k, 23)
+    _, ref_Z = spectral.ritz_vectors(g, k, 60, 5, 23)
+    ref = km.kmeans(ref_Z.astype(np.float32), k, 23)
+    a_gpu = metrics.ari(lab.cpu().numpy(), g.labels)
+    a_ref = metrics.ari(ref["labels"], g.labels)
+    assert a_gpu >= a_ref - 0.01, (a_gpu, a_ref)

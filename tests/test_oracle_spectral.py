@@ -182,3 +182,18 @@ def test_orthogonal_iteration_converges_to_the_top_eigenvectors():
     w, V = np.linalg.eigh(spectral.dense_signless(g))
     P = V[:, np.argsort(-w)[:l]]
     assert np.linalg.norm(P @ P.T - Q @ Q.T, 2) < 1e-6
+
+
+def test_ritz_pairs_converge_to_the_top_eigenpairs():
+    """Rayleigh-Ritz on the orthogonal-iteration basis recovers the top l eigenpairs of M
+    (dense eigendecomposition): values to 1e-9, vectors up to sign."""
+    g = W.sbm([50, 60, 70, 80], 0.4, 0.02, 7)
+    l = 4
+    theta, Z = spectral.ritz_vectors(g, l, 300, 10, 3)
+    w, V = np.linalg.eigh(spectral.dense_signless(g))
+    order = np.argsort(-w)[:l]
+    assert np.allclose(theta, w[order], atol=1e-9)
+    Q = Z / spectral.inv_sqrt_degrees(spectral.degrees(g))[:, None]
+    for a in range(l):
+        c = abs(float(Q[:, a] @ V[:, order[a]]))
+        assert c > 1 - 1e-8, (a, c)
