@@ -123,122 +123,30 @@ fsc_status status_from_bits(int bits) {
     return FSC_ERR_CUDA;
 }
 
-// Validation and degrees, kDegLanes lanes per row: the lanes of a row read its entries side by
-// side (coalesced), each keeps a partial count (unit weights, exact) or a float64 partial sum
-// (weights), and the partials meet in a shuffle tree.  D^-1/2 and 1/d are formed in float32 from
-// the float64 degree (correctly rounded sqrt and division, within 1-2 ulp of the exact values);
-// float64 arithmetic stays out of the unit-weight path, which it would slow down on this GPU.
-constexpr int kDegLanes = 8;
-
 // float64 value of an integer below 2^53, built with integer operations only (the float64 pipe
-// is a small fraction of the integer one on this GPU, and it bounded the unit-weight kernel).
+// is a small fraction of the integer one on this GPU).
 __device__ __forceinline__ double exact_u64_to_f64(unsigned long long c) {
     if (c == 0) return 0.0;
     const int e = 63 - __clzll((long long)c);
     const unsigned long long mant = (c << (52 - e)) & ((1ull << 52) - 1);
     return __longlong_as_double((long long)((((unsigned long long)(1023 + e)) << 52) | mant));
 }
-__global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
-                                                const int32_t* __restrict__ col, const float* __restrict__ w,
-                                                int check_sorted, double* __restrict__ deg,
-                                                float* __restrict__ dinv, float* __restrict__ invdeg,
-                                                unsigned long long* __restrict__ n_iso, double* __restrict__ vol,
-                                                int* __restrict__ status, double* __restrict__ sumsq,
-                                                unsigned long long* __restrict__ dmax_bits) {
-    constexpr int G = kDegLanes, RPW = 32 / G;
-    const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
-    int bad = 0;
-    unsigned iso = 0;
-    double vsum = 0.0, vsq = 0.0, vmax = 0.0;
-    long long cnt_total = 0;
-    unsigned long long usq = 0, umax = 0;   // unit weights: sum of d^2 and max d as integers
-    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {   // warp-uniform trip count
-        const int64_t i = base + grp;
-        const bool active = i < n;
-        int64_t s = 0, e = 0;
-        if (active) {
-            s = rp[i];
-            e = rp[i + 1];
-            if (s < 0 || e < s || e > nnz) {
-                bad |= ST_BAD_ROWPTR;
-                s = e = 0;
-            }
-        }
-        double d = 0.0;
-        long long cnt = 0;
-        for (int64_t p = s + sub; p < e; p += G) {
-            const int j = col[p];
-            if (j < 0 || (int64_t)j >= n) { bad |= ST_INDEX_RANGE; continue; }
-            if ((int64_t)j == i) { bad |= ST_SELF_LOOP; continue; }
-            if (check_sorted && p > s && col[p - 1] >= j) bad |= ST_UNSORTED;
-            if (w) {
-                const float wv = w[p];
-                if (!(wv >= 0.0f) || isinf(wv)) { bad |= ST_BAD_WEIGHT; continue; }
-                d += (double)wv;
-            } else {
-                ++cnt;
-            }
-        }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
-        if (w) {
-#pragma unroll
-            for (int off = G / 2; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-        }
-        if (active && sub == 0 && !w) {
-            // unit weights: d is the exact count; everything stays in integer registers
-            const unsigned long long c = (unsigned long long)cnt;
-            cnt_total += cnt;
-            deg[i] = exact_u64_to_f64(c);
-            if (c < (1ull << 26)) usq += c * c;          // a thread's few rows cannot overflow
-            else vsq += (double)c * (double)c;            // only with repeated entries
-            umax = umax > c ? umax : c;
-            if (c) {
-                const float df = (float)c;
-                dinv[i] = 1.0f / sqrtf(df);
-                invdeg[i] = 1.0f / df;
-            } else {
-                dinv[i] = 0.0f;
-                invdeg[i] = 0.0f;
-                ++iso;
-            }
-        } else if (active && sub == 0) {
-            vsum += d;
-            deg[i] = d;
-            vsq += d * d;
-            vmax = fmax(vmax, d);
-            if (d > 0.0) {
-                const float df = (float)d;
-                dinv[i] = 1.0f / sqrtf(df);
-                invdeg[i] = 1.0f / df;
-            } else {
-                dinv[i] = 0.0f;
-                invdeg[i] = 0.0f;
-                ++iso;
-            }
-        }
-    }
+
+// Per-thread degree statistics to the graph header: warp shuffles, then the block's warps through
+// shared memory, then one atomic per block and statistic (per-warp atomics on five single
+// addresses serialised at L2 and dominated the kernel).  Blocks of 256 threads.
+__device__ __forceinline__ void degree_block_totals(int bad, unsigned iso, double vol_part, double vsq,
+                                                    double vmax, unsigned long long* n_iso, double* vol,
+                                                    int* status, double* sumsq,
+                                                    unsigned long long* dmax_bits) {
+    const int lane = threadIdx.x & 31;
     for (int off = 16; off > 0; off >>= 1) {
         bad |= __shfl_xor_sync(0xffffffffu, bad, off);
         iso += __shfl_xor_sync(0xffffffffu, iso, off);
-        cnt_total += __shfl_xor_sync(0xffffffffu, cnt_total, off);
-    }
-    if (w) {
-        for (int off = 16; off > 0; off >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
-    }
-    if (!w) {   // fold the integer statistics in once per thread
-        vsq += (double)usq;
-        vmax = (double)umax;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
+        vol_part += __shfl_xor_sync(0xffffffffu, vol_part, off);
         vsq += __shfl_xor_sync(0xffffffffu, vsq, off);
         vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
     }
-    // block totals first: one atomic per block and statistic (per-warp atomics on five single
-    // addresses serialised at L2 and dominated the kernel)
     __shared__ double s_sq[8], s_mx[8], s_vol[8];
     __shared__ int s_bad[8];
     __shared__ unsigned s_iso[8];
@@ -246,7 +154,7 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
     if (lane == 0) {
         s_sq[wid] = vsq;
         s_mx[wid] = vmax;
-        s_vol[wid] = w ? vsum : (double)cnt_total;
+        s_vol[wid] = vol_part;
         s_bad[wid] = bad;
         s_iso[wid] = iso;
     }
@@ -268,6 +176,203 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
         if (tiso) atomicAdd(n_iso, (unsigned long long)tiso);
         if (tvol != 0.0) atomicAdd(vol, tvol);
     }
+}
+
+// Weighted graphs: validation and degrees, kDegLanes lanes per row.  The lanes of a row read its
+// entries side by side (coalesced), each keeps a float64 partial sum, and the partials meet in a
+// shuffle tree.  D^-1/2 and 1/d are formed in float32 from the float64 degree (correctly rounded
+// sqrt and division, within 1-2 ulp of the exact values).
+constexpr int kDegLanes = 8;
+
+__global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, const float* __restrict__ w,
+                                                int check_sorted, double* __restrict__ deg,
+                                                float* __restrict__ dinv, float* __restrict__ invdeg,
+                                                unsigned long long* __restrict__ n_iso, double* __restrict__ vol,
+                                                int* __restrict__ status, double* __restrict__ sumsq,
+                                                unsigned long long* __restrict__ dmax_bits) {
+    constexpr int G = kDegLanes, RPW = 32 / G;
+    const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
+    int bad = 0;
+    unsigned iso = 0;
+    double vsum = 0.0, vsq = 0.0, vmax = 0.0;
+    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {   // warp-uniform trip count
+        const int64_t i = base + grp;
+        const bool active = i < n;
+        int64_t s = 0, e = 0;
+        if (active) {
+            s = rp[i];
+            e = rp[i + 1];
+            if (s < 0 || e < s || e > nnz) {
+                bad |= ST_BAD_ROWPTR;
+                s = e = 0;
+            }
+        }
+        double d = 0.0;
+        for (int64_t p = s + sub; p < e; p += G) {
+            const int j = col[p];
+            if (j < 0 || (int64_t)j >= n) { bad |= ST_INDEX_RANGE; continue; }
+            if ((int64_t)j == i) { bad |= ST_SELF_LOOP; continue; }
+            if (check_sorted && p > s && col[p - 1] >= j) bad |= ST_UNSORTED;
+            const float wv = w[p];
+            if (!(wv >= 0.0f) || isinf(wv)) { bad |= ST_BAD_WEIGHT; continue; }
+            d += (double)wv;
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+        if (active && sub == 0) {
+            vsum += d;
+            deg[i] = d;
+            vsq += d * d;
+            vmax = fmax(vmax, d);
+            if (d > 0.0) {
+                const float df = (float)d;
+                dinv[i] = 1.0f / sqrtf(df);
+                invdeg[i] = 1.0f / df;
+            } else {
+                dinv[i] = 0.0f;
+                invdeg[i] = 0.0f;
+                ++iso;
+            }
+        }
+    }
+    degree_block_totals(bad, iso, vsum, vsq, vmax, n_iso, vol, status, sumsq, dmax_bits);
+}
+
+// Unit weights: d(v) is the row length, so the degrees come from row_ptr alone and col is read
+// only to validate it.  A block takes a tile of `rows` consecutive rows (dynamic shared memory
+// holds the tile's rows + 1 row_ptr values): one thread per row writes the degrees (coalesced),
+// then the block streams the tile's entries as one flat range of VEC-entry vectors, kDegUnroll
+// independent loads in flight per thread.  An entry's row (a binary search in the shared row_ptr)
+// is looked up only where the checks need it: when its column lies in the tile's own rows (a
+// possible self-loop) or, with the sortedness check, when it is not above its predecessor.  On a
+// graph without locality that is a fraction rows / n of the entries, so the scan costs a few
+// instructions per entry.  The tile size is chosen so the grid is about one wave of resident
+// blocks; HBM traffic is row_ptr, col and the three n-vectors once.
+constexpr int kDegUnroll = 4;
+
+template <int VEC>
+__device__ __forceinline__ void load_entries(const int32_t* __restrict__ col, long long v, long long nnz,
+                                             int32_t (&x)[VEC]) {
+    const long long base = v * VEC;
+    if (VEC == 4 && base + 3 < nnz) {
+        const int4 t = __ldg(reinterpret_cast<const int4*>(col) + v);
+        x[0] = t.x;
+        x[VEC > 1 ? 1 : 0] = t.y;
+        x[VEC > 2 ? 2 : 0] = t.z;
+        x[VEC > 3 ? 3 : 0] = t.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) x[u] = base + u < nnz ? __ldg(col + base + u) : 0;
+    }
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) k_degree_unit(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, int rows, int check_sorted,
+                                                     double* __restrict__ deg, float* __restrict__ dinv,
+                                                     float* __restrict__ invdeg,
+                                                     unsigned long long* __restrict__ n_iso,
+                                                     double* __restrict__ vol, int* __restrict__ status,
+                                                     double* __restrict__ sumsq,
+                                                     unsigned long long* __restrict__ dmax_bits) {
+    extern __shared__ long long s_rp[];   // rows + 1
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
+    int bad = 0;
+    unsigned iso = 0;
+    long long cnt_total = 0;
+    double vsq = 0.0;
+    unsigned long long usq = 0, umax = 0;   // sum of d^2 (below 2^64: it is at most nnz * max d) and max d
+    const int64_t ntiles = (n + rows - 1) / rows;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * rows;
+        const int nr = (int)(n - r0 < rows ? n - r0 : rows);
+        for (int q = threadIdx.x; q <= nr; q += blockDim.x) s_rp[q] = rp[r0 + q];
+        __syncthreads();
+        int tile_bad = 0;
+        for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+            const long long s = s_rp[q], e = s_rp[q + 1];
+            if (s < 0 || e < s || e > nnz) {
+                tile_bad = 1;
+                continue;
+            }
+            const unsigned long long c = (unsigned long long)(e - s);
+            const int64_t i = r0 + q;
+            deg[i] = exact_u64_to_f64(c);
+            cnt_total += (long long)c;
+            if (c < (1ull << 26)) usq += c * c;
+            else vsq += (double)c * (double)c;
+            umax = umax > c ? umax : c;
+            if (c) {
+                const float df = (float)c;
+                dinv[i] = 1.0f / sqrtf(df);
+                invdeg[i] = 1.0f / df;
+            } else {
+                dinv[i] = 0.0f;
+                invdeg[i] = 0.0f;
+                ++iso;
+            }
+        }
+        // a tile with a bad row_ptr is not scanned (its rows would not be monotone); the barrier
+        // also ends every read of s_rp before the next tile overwrites it
+        if (__syncthreads_or(tile_bad)) {
+            bad |= ST_BAD_ROWPTR;
+            continue;
+        }
+        const long long P0 = s_rp[0], P1 = s_rp[nr];   // 0 <= P0 <= P1 <= nnz, rows non-decreasing
+        const long long v0 = P0 / VEC, v1 = (P1 + VEC - 1) / VEC;
+        const int r0i = (int)r0;                        // r0 < n <= 2^31 - 1
+        for (long long v = v0 + threadIdx.x; v < v1; v += (long long)kDegUnroll * blockDim.x) {
+            int32_t x[kDegUnroll][VEC];
+#pragma unroll
+            for (int h = 0; h < kDegUnroll; ++h) {
+                const long long vv = v + (long long)h * blockDim.x;
+                if (vv < v1) load_entries<VEC>(col, vv, nnz, x[h]);
+            }
+#pragma unroll
+            for (int h = 0; h < kDegUnroll; ++h) {
+                const long long vv = v + (long long)h * blockDim.x;
+                if (vv >= v1) break;
+                const long long base = vv * VEC;
+                const bool interior = base >= P0 && base + VEC <= P1;
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) {
+                    const long long p = base + u;
+                    if (!interior && (p < P0 || p >= P1)) continue;
+                    const int j = x[h][u];
+                    if ((unsigned)j >= (unsigned)n) {   // also j < 0
+                        bad |= ST_INDEX_RANGE;
+                        continue;
+                    }
+                    // the row of p is needed only where it can matter: a self-loop (i, i) has i in
+                    // this tile's rows, and an inversion col[p-1] >= col[p] is either a row start
+                    // or an unsorted row
+                    bool need_row = (unsigned)(j - r0i) < (unsigned)nr;
+                    int prev = 0;
+                    if (check_sorted && p > P0) {
+                        prev = u > 0 ? x[h][u > 0 ? u - 1 : 0] : __ldg(col + p - 1);
+                        need_row |= prev >= j;
+                    }
+                    if (need_row) {
+                        int lo = 0, hi = nr - 1;   // last row whose start is <= p (s_rp[nr] = P1 > p)
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_rp[mid] <= p) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        if (j == r0i + lo) bad |= ST_SELF_LOOP;
+                        if (check_sorted && p > s_rp[lo] && prev >= j) bad |= ST_UNSORTED;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    degree_block_totals(bad, iso, (double)cnt_total, vsq + (double)usq, (double)umax, n_iso, vol, status,
+                        sumsq, dmax_bits);
 }
 
 // One warp per row: each entry (i, j, w) must have its mirror (j, i, w) (binary search, sorted rows).
@@ -342,23 +447,47 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
         if ((e = cudaMemsetAsync(base + n8, 0, 256, s)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(base + n8 + 256 + 2 * n4, 0, 256, s)) != cudaSuccess) break;
         const int threads = 256;
-        constexpr int rows_per_block = threads / 32 * (32 / kDegLanes);
-        const int64_t want = (n + rows_per_block - 1) / rows_per_block;
-        // enough warps that each walks only a few rows: every row is a dependent row_ptr -> col
-        // load chain, so the kernel is latency-bound with fewer warps in flight
-        const int64_t cap = (int64_t)device_props().num_sms * 32;
-        const int blocks = (int)(want < cap ? want : cap);
         const int check_sorted = (flags & FSC_VALIDATE_SYMMETRY) ? 1 : 0;
-        k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,
-                                            g->invdeg, &hdr->niso, &hdr->vol, &hdr->status, &hdr->sumsq,
-                                            &hdr->dmax_bits);
+        if (w == nullptr) {
+            // tiles of 64 .. 2048 rows, sized so the grid is about one wave of resident blocks
+            const bool vec4 = (reinterpret_cast<uintptr_t>(col_idx) & 15) == 0;
+            const void* fn = vec4 ? (const void*)k_degree_unit<4> : (const void*)k_degree_unit<1>;
+            constexpr int64_t kMaxRows = 2048, kMinRows = 64;
+            int per_sm = kernel_occupancy(fn, threads, (size_t)(kMaxRows + 1) * 8);
+            if (per_sm < 1) per_sm = 1;
+            const int64_t slots = (int64_t)device_props().num_sms * per_sm;
+            int64_t rows = ((n + slots - 1) / slots + 31) / 32 * 32;
+            rows = rows < kMinRows ? kMinRows : (rows > kMaxRows ? kMaxRows : rows);
+            const int64_t ntiles = (n + rows - 1) / rows;
+            const int blocks = (int)(ntiles < slots ? ntiles : slots);
+            const size_t smem = (size_t)(rows + 1) * 8;
+            if (vec4)
+                k_degree_unit<4><<<blocks, threads, smem, s>>>(n, nnz, row_ptr, col_idx, (int)rows, check_sorted,
+                                                               g->deg, g->dinv, g->invdeg, &hdr->niso, &hdr->vol,
+                                                               &hdr->status, &hdr->sumsq, &hdr->dmax_bits);
+            else
+                k_degree_unit<1><<<blocks, threads, smem, s>>>(n, nnz, row_ptr, col_idx, (int)rows, check_sorted,
+                                                               g->deg, g->dinv, g->invdeg, &hdr->niso, &hdr->vol,
+                                                               &hdr->status, &hdr->sumsq, &hdr->dmax_bits);
+        } else {
+            constexpr int rows_per_block = threads / 32 * (32 / kDegLanes);
+            const int64_t want = (n + rows_per_block - 1) / rows_per_block;
+            // enough warps that each walks only a few rows: every row is a dependent row_ptr -> col
+            // load chain, so the kernel is latency-bound with fewer warps in flight
+            const int64_t cap = (int64_t)device_props().num_sms * 32;
+            const int blocks = (int)(want < cap ? want : cap);
+            k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,
+                                                g->invdeg, &hdr->niso, &hdr->vol, &hdr->status, &hdr->sumsq,
+                                                &hdr->dmax_bits);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         Header h{};
         if ((e = cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
         int bits = h.status;
         if (bits == 0 && check_sorted) {
-            k_symmetry<<<blocks, threads, 0, s>>>(n, row_ptr, col_idx, w, &hdr->status);
+            const int64_t want = (n + threads / 32 - 1) / (threads / 32), cap = (int64_t)device_props().num_sms * 32;
+            k_symmetry<<<(int)(want < cap ? want : cap), threads, 0, s>>>(n, row_ptr, col_idx, w, &hdr->status);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
             if ((e = cudaMemcpyAsync(&bits, &hdr->status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;

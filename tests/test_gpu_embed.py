@@ -187,3 +187,105 @@ def test_graph_validation_errors(torch):
     assert e.value.name == "FSC_ERR_INDEX_RANGE"
     make(g.row_ptr, g.col, validate_symmetry=True)   # the valid graph passes
     del r0
+
+
+def _unit_csr(torch, row_ptr, col, offset=0):
+    """row_ptr and col on the device, col starting ``offset`` int32 elements into a larger buffer
+    (offset 0: a 16-byte aligned start; 1-3: the unaligned starts a caller's view can have)."""
+    rp = torch.as_tensor(row_ptr, device="cuda")
+    buf = torch.zeros(col.size + offset, dtype=torch.int32, device="cuda")
+    buf[offset:] = torch.as_tensor(col, device="cuda")
+    return rp, buf[offset:]
+
+
+@pytest.mark.parametrize("offset", [0, 1, 2, 3])
+def test_unit_degrees_many_tiles_any_alignment(torch, offset):
+    """Unit-weight degrees and header statistics (Sec. 2: d(v) is the row length) on a graph of
+    hundreds of row tiles with isolated vertices scattered through it, for a col array at each
+    4-byte offset from a 16-byte boundary (the vector scan and the scalar scan)."""
+    import paper_2310_10939_gb300 as fsc
+    g = W.permuted(W.with_isolated(W.sbm([20000, 13001, 7000], 0.0008, 0.00005, 11), 311), 12)
+    rp, col = _unit_csr(torch, g.row_ptr, g.col, offset)
+    assert (col.data_ptr() % 16 == 0) == (offset == 0)
+    G = fsc.Graph(rp, col)
+    ref = spectral.degrees(g)
+    assert np.array_equal(G.degrees().cpu().numpy(), ref)
+    info = G.info()
+    assert info["n_isolated"] == int((ref == 0).sum()) >= 311
+    assert info["volume"] == float(ref.sum())
+    assert info["deg_max"] == float(ref.max())
+    assert info["deg_sumsq"] == float((ref * ref).sum())
+    assert np.array_equal(G.dinv().cpu().numpy() == 0, ref == 0)
+    # the same power step as from the aligned copy (the SpMM reads col one entry at a time)
+    if offset:
+        G0 = fsc.Graph(*_unit_csr(torch, g.row_ptr, g.col, 0))
+        z = torch.as_tensor(np.random.default_rng(3).normal(size=(g.n, 4)).astype(np.float32), device="cuda")
+        a, b = torch.empty_like(z), torch.empty_like(z)
+        fsc.power_step(G, 4, z, a)
+        fsc.power_step(G0, 4, z, b)
+        assert torch.equal(a, b)
+
+
+def _graph_with_nnz_mod4(want: int):
+    for seed in range(40, 200):
+        g = W.sbm([300, 301], 0.05, 0.005, seed)
+        if g.nnz % 4 == want:
+            return g
+    raise AssertionError("no seed gives the wanted nnz mod 4")
+
+
+@pytest.mark.parametrize("lane", [0, 1, 2, 3])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_validation_at_each_vector_position(torch, lane, offset):
+    """A self-loop, an out-of-range index and an unsorted pair (with the symmetry check) are each
+    found wherever they sit in a 4-entry vector, for aligned and unaligned col."""
+    import paper_2310_10939_gb300 as fsc
+    g = _graph_with_nnz_mod4(2)
+    rp = g.row_ptr
+
+    def entry_in_middle_row(need_next=False):
+        for i in range(g.n // 2, g.n):
+            for p in range(rp[i], rp[i + 1] - (1 if need_next else 0)):
+                if (p - offset) % 4 == lane and (not need_next or p > rp[i]):
+                    return i, p
+        raise AssertionError
+
+    def status(col, sym=False):
+        with pytest.raises(fsc.FscError) as e:
+            fsc.Graph(*_unit_csr(torch, rp, col, offset), validate_symmetry=sym)
+        return e.value.name
+
+    i, p = entry_in_middle_row()
+    col = g.col.copy()
+    col[p] = i
+    assert status(col) == "FSC_ERR_SELF_LOOP"
+    for bad in (g.n, -1, 2**31 - 1):
+        col = g.col.copy()
+        col[p] = bad
+        assert status(col) == "FSC_ERR_INDEX_RANGE"
+    # unsorted: the pair (p - 1, p) inverted, found at p, whose predecessor is in the same vector
+    # (lane > 0) or in the previous one (lane 0)
+    i, p = entry_in_middle_row(need_next=True)
+    col = g.col.copy()
+    col[p - 1], col[p] = col[p], col[p - 1]
+    assert status(col, sym=True) == "FSC_ERR_UNSORTED"
+    fsc.Graph(*_unit_csr(torch, rp, col, offset))   # accepted when sortedness is not asked for
+
+
+def test_validation_tail_and_middle_row_ptr(torch):
+    """The last entry of a col array whose length is not a multiple of 4 (the scalar tail), and a
+    row_ptr that decreases in a middle tile, are both reported."""
+    import paper_2310_10939_gb300 as fsc
+    g = _graph_with_nnz_mod4(2)
+    col = g.col.copy()
+    col[-1] = g.n
+    with pytest.raises(fsc.FscError) as e:
+        fsc.Graph(*_unit_csr(torch, g.row_ptr, col))
+    assert e.value.name == "FSC_ERR_INDEX_RANGE"
+    big = W.sbm([20000, 20000], 0.0006, 0.00004, 13)
+    rp = big.row_ptr.copy()
+    mid = big.n // 2 + 17
+    rp[mid] = rp[mid + 1] + 1
+    with pytest.raises(fsc.FscError) as e:
+        fsc.Graph(*_unit_csr(torch, rp, big.col))
+    assert e.value.name == "FSC_ERR_INDEX_RANGE"
