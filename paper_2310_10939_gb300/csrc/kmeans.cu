@@ -294,7 +294,7 @@ struct LloydArgs {
     float* c32;                 // in: the k-means++ centres; out: the final centroids (float32)
     double* c64;                // out: the final centroids (float64)
     unsigned long long* tot;    // 3 accumulators of k*(LP+1) exact sums (coordinates, count), zeroed
-    unsigned long long* cnt3;   // 3 x (inertia sum, changed count, 2 unused), zeroed
+    unsigned long long* cnt3;   // 3 x (inertia sum, changed count, 2 unused), then the final inertia; zeroed
     const unsigned* amax;
     long long chunk;            // points per block (a multiple of KM_PPT)
     int ntab;
@@ -316,19 +316,11 @@ struct LloydArgs {
 constexpr float PRUNE_EPS = 1e-5f;
 constexpr float PRUNE_GROW2 = (1.0f + PRUNE_EPS) * (1.0f + PRUNE_EPS);   // the test runs on squares
 
-// Settles point i: new label, lower bound, changed count, its float32 distance in the inertia and
-// its coordinates in the centroid sums (two-slot run cache in front of the warp's shared table;
-// slot 0 holds the most recent label).  Labels are written only when they change.
+// Adds sign * q (a point's exact coordinates) and sign to cluster lab through the two-slot run
+// cache in front of the warp's shared table (slot 0 holds the most recent label).
 template <int LP>
-__device__ __forceinline__ void lloyd_commit(const LloydArgs& a, long long i, const float (&x)[LP], int oldl, int lab,
-                                             float dist, float lbn, const Scales& sc, Slot<LP> (&sl)[2],
-                                             unsigned long long* tab, long long& inert, int& changed) {
-    if (a.prune) a.lbound[i] = lbn;
-    if (oldl != lab) {
-        ++changed;
-        a.labels[i] = lab;
-    }
-    inert += fixq(dist, sc.Sd);
+__device__ __forceinline__ void slot_add(Slot<LP> (&sl)[2], int lab, const long long (&q)[LP], bool minus,
+                                         unsigned long long* tab) {
     if (sl[0].j != lab) {
         if (sl[1].j == lab) {
             const Slot<LP> t = sl[0];
@@ -344,8 +336,30 @@ __device__ __forceinline__ void lloyd_commit(const LloydArgs& a, long long i, co
         }
     }
 #pragma unroll
-    for (int c = 0; c < LP; ++c) sl[0].s[c] += fixq(x[c], sc.Sx);
-    ++sl[0].cnt;
+    for (int c = 0; c < LP; ++c) sl[0].s[c] += minus ? -q[c] : q[c];
+    sl[0].cnt += minus ? -1 : 1;
+}
+
+// Settles a point that went through the k-way scan: lower bound, label, changed count and, in the
+// first iteration, its distance in the inertia.  The centroid sums are running totals, so only a
+// point whose label changes contributes: its coordinates leave the old cluster and join the new
+// one (in the first iteration every label changes from -1).  Labels are written only when they
+// change.
+template <int LP>
+__device__ __forceinline__ void lloyd_commit(const LloydArgs& a, long long i, const float (&x)[LP], int oldl, int lab,
+                                             float dist, float lbn, bool first, const Scales& sc, Slot<LP> (&sl)[2],
+                                             unsigned long long* tab, long long& inert, int& changed) {
+    if (a.prune) a.lbound[i] = lbn;
+    if (first) inert += fixq(dist, sc.Sd);
+    if (oldl != lab) {
+        ++changed;
+        a.labels[i] = lab;
+        long long q[LP];
+#pragma unroll
+        for (int c = 0; c < LP; ++c) q[c] = fixq(x[c], sc.Sx);
+        slot_add<LP>(sl, lab, q, false, tab);
+        if (oldl >= 0) slot_add<LP>(sl, oldl, q, true, tab);
+    }
 }
 
 template <int LP>
@@ -359,6 +373,8 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
     unsigned long long* s_tab =
         reinterpret_cast<unsigned long long*>(km_smem + (((size_t)k * LP * 4 + 15) & ~(size_t)15));
     float* s_sep = reinterpret_cast<float*>(s_tab + (size_t)ntab * rowlen);   // k floats
+    // running exact sums and counts of every cluster (the same in every block)
+    long long* s_S = reinterpret_cast<long long*>(s_tab + (size_t)ntab * rowlen + (((size_t)k + 1) / 2));
     float* s_cn = reinterpret_cast<float*>(s_tab);   // new centroids, staged in the tables once they are summed
     __shared__ long long s_red[KM_WARPS];
     __shared__ int s_redi[KM_WARPS];
@@ -378,11 +394,14 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
         s_c[q] = v;
         if (b == 0) a.c64[q] = (double)v;   // float64 masters of the k-means++ centres
     }
+    for (size_t q = tid; q < rowlen; q += KM_THREADS) s_S[q] = 0;
     if (tid == 0) s_pmax = 0u;
     __syncthreads();
-    // One grid barrier per iteration: blocks add their exact sums into the iteration's accumulator
-    // (one of three, used in rotation), and after the barrier every block forms all k centroids
-    // from it itself, so the centroids never travel through global memory between blocks.
+    // One grid barrier per iteration: blocks add the changes of their clusters' exact sums into
+    // the iteration's accumulator (one of three, used in rotation), and after the barrier every
+    // block adds them to its running totals and forms all k centroids itself, so the centroids
+    // never travel through global memory between blocks.  A point whose bounds prove its label
+    // unchanged costs one distance and one store.
     for (int it = 1; it <= a.max_iter; ++it) {
         const int cur = it % 3;
         unsigned long long* T = a.tot + (size_t)cur * rowlen;
@@ -454,7 +473,7 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
                     const float lw = fmaxf(0.f, lbv[u] - pmax);
                     const float bnd = fmaxf(s_sep[ca], lw);
                     if (da * PRUNE_GROW2 < bnd * bnd) {
-                        lloyd_commit<LP>(a, i0 + u, x[u], ca, ca, da, lw, sc, sl, my_tab, inert, changed);
+                        a.lbound[i0 + u] = lw;
                         need = false;
                     }
                 }
@@ -486,8 +505,8 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
                         sec = d;
                     }
                 }
-                if (act) lloyd_commit<LP>(a, i, xv, qold[q], bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), sc, sl, my_tab,
-                                          inert, changed);
+                if (act) lloyd_commit<LP>(a, i, xv, qold[q], bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), it == 1, sc, sl,
+                                          my_tab, inert, changed);
             }
             __syncwarp();
         }
@@ -507,14 +526,17 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
             if (changed) atomicAdd(a.cnt3 + 4 * cur + 1, (unsigned long long)changed);
         }
         if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
-        // ---- update, in every block: c_j = (exact sum of its points) / count, rounded to float64
-        // then float32; an empty cluster keeps its centroid
+        // ---- update, in every block: running totals += this iteration's changes (exact integer
+        // adds, so every block holds the same totals); c_j = (exact sum of its points) / count,
+        // rounded to float64 then float32; an empty cluster keeps its centroid
+        for (size_t q = tid; q < rowlen; q += KM_THREADS) s_S[q] += (long long)__ldcg(T + q);
+        __syncthreads();
         for (int q = tid; q < k * LP; q += KM_THREADS) {
             const int j = q / LP, c = q - j * LP;
-            const long long cntj = (long long)__ldcg(T + (size_t)j * (LP + 1) + LP);
+            const long long cntj = s_S[(size_t)j * (LP + 1) + LP];
             float v = s_c[q];
             if (cntj > 0) {
-                const long long sj = (long long)__ldcg(T + (size_t)j * (LP + 1) + c);
+                const long long sj = s_S[(size_t)j * (LP + 1) + c];
                 const double m = ((double)sj * pow2d(-sc.Sx)) / (double)cntj;
                 v = (float)m;
                 if (b == 0) a.c64[q] = m;
@@ -536,7 +558,7 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
                 mv = __fadd_rn(mv, __fmul_rn(dlt, dlt));
             }
             atomicMax(&s_pmax, __float_as_uint(sqrtf(mv) * (1.0f + PRUNE_EPS)));
-            if (b == 0 && __ldcg(T + (size_t)j * (LP + 1) + LP) == 0ull) atomicAdd(&a.st->empty_events, 1);
+            if (b == 0 && s_S[(size_t)j * (LP + 1) + LP] == 0) atomicAdd(&a.st->empty_events, 1);
         }
         // the accumulator of iteration it+2 was last read after the previous barrier: clear it
         if (b == 0) {
@@ -545,25 +567,52 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
             if (tid < 4) a.cnt3[4 * ((it + 2) % 3) + tid] = 0ull;
         }
         if (b == 0 && tid == 0) {
-            const double iv = (double)s_inert * pow2d(-sc.Sd);
-            a.st->inertia = iv;
-            if (it == 1) a.st->potential = iv;
+            if (it == 1) a.st->potential = (double)s_inert * pow2d(-sc.Sd);
             a.st->iterations = it;
             a.st->changed = s_changed;
         }
         __syncthreads();
-        for (int q = tid; q < k * LP; q += KM_THREADS) s_c[q] = s_cn[q];
+        // on the last iteration s_c keeps the centroids its assignment used (for the inertia)
         const bool stop = s_changed == 0 || it == a.max_iter;
+        if (!stop)
+            for (int q = tid; q < k * LP; q += KM_THREADS) s_c[q] = s_cn[q];
         __syncthreads();
         if (stop) break;
     }
+    // ---- inertia of the last assignment: each point's float32 distance to the centroid it was
+    // assigned to (the same value the assignment computed), summed exactly in fixed point
+    long long inert = 0;
+    for (long long t0 = lo; t0 < hi; t0 += KM_TILE) {
+        const long long i0 = t0 + (long long)KM_PPT * tid;
+#pragma unroll
+        for (int u = 0; u < KM_PPT; ++u) {
+            if (i0 + u < hi) {
+                float x[LP];
+                load_point<LP>(a.X, i0 + u, a.l, x);
+                const int lab = a.labels[i0 + u];
+                inert += fixq(sqdist<LP>(x, s_c + lab * LP), sc.Sd);
+            }
+        }
+    }
+    inert = block_sum_ll(inert, s_red);
+    if (tid == 0 && inert) atomicAdd(a.cnt3 + 12, (unsigned long long)inert);
+    if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
     if (b == 0) {
-        for (int q = tid; q < k * LP; q += KM_THREADS) a.c32[q] = s_c[q];
+        if (tid == 0) a.st->inertia = (double)(long long)__ldcg(a.cnt3 + 12) * pow2d(-sc.Sd);
+        for (int q = tid; q < k * LP; q += KM_THREADS) a.c32[q] = s_cn[q];
     }
 }
 
 __global__ void k_merge_status(const int* __restrict__ call_status, int* __restrict__ dev_status) {
     if (*call_status) atomicOr(dev_status, *call_status);
+}
+
+// k_lloyd's dynamic shared memory: centroids (16-byte aligned), ntab private tables, half the
+// separation of each centroid (k floats, padded to 8 bytes), the running totals k (LP + 1).
+static size_t lloyd_smem_bytes(int k, int LP, int ntab) {
+    const size_t rowlen = (size_t)k * (LP + 1);
+    return (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * rowlen * 8 + (((size_t)k + 1) / 2) * 8 +
+           rowlen * 8;
 }
 
 template <typename K>
@@ -582,8 +631,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     int ntab = (int)(65536 / tab_bytes);
     if (ntab > KM_WARPS) ntab = KM_WARPS;
     if (ntab < 1) ntab = 1;
-    const size_t lloyd_smem =
-        (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes + (size_t)k * 4;
+    const size_t lloyd_smem = lloyd_smem_bytes(k, LP, ntab);
     auto kpp = k_kmeanspp<LP>;
     auto lly = k_lloyd<LP>;
     int G = coop_blocks(kpp, kpp_smem);
@@ -600,7 +648,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
     size_t off = 0;
-    const size_t acc = up((size_t)3 * k * (LP + 1) * 8 + 12 * 8);   // Lloyd accumulators, zeroed with the header
+    const size_t acc = up((size_t)3 * k * (LP + 1) * 8 + 16 * 8);   // Lloyd accumulators, zeroed with the header
     const size_t o_hdr = off; off += hdr;
     const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
@@ -851,8 +899,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     int ntab = (int)(65536 / tab_bytes);
     if (ntab > KM_WARPS) ntab = KM_WARPS;
     if (ntab < 1) ntab = 1;
-    const size_t lloyd_smem =
-        (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * tab_bytes + (size_t)k * 4;
+    const size_t lloyd_smem = lloyd_smem_bytes(k, LP, ntab);
     auto kpp = k_kmeanspp<LP>;
     auto lly = k_lloyd<LP>;
     int G = coop_blocks(kpp, kpp_smem);
@@ -868,7 +915,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
     size_t off = 0;
-    const size_t acc = up((size_t)3 * k * (LP + 1) * 8 + 12 * 8);   // Lloyd accumulators, zeroed with the header
+    const size_t acc = up((size_t)3 * k * (LP + 1) * 8 + 16 * 8);   // Lloyd accumulators, zeroed with the header
     const size_t o_hdr = off; off += hdr;
     const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);

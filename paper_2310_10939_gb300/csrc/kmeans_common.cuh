@@ -144,9 +144,11 @@ struct Slot {
     long long s[LP];
 };
 
+// A slot may hold signed contributions (a point leaving a cluster subtracts its coordinates), so
+// a zero count does not mean zero sums: only an unused slot (j < 0) is skipped.
 template <int LP>
 __device__ __forceinline__ void slot_flush(const Slot<LP>& sl, unsigned long long* tab) {
-    if (sl.j < 0 || sl.cnt == 0) return;
+    if (sl.j < 0) return;
     unsigned long long* row = tab + (size_t)sl.j * (LP + 1);
 #pragma unroll
     for (int c = 0; c < LP; ++c) atomicAdd(row + c, (unsigned long long)sl.s[c]);
@@ -159,7 +161,7 @@ __device__ __forceinline__ void slot_flush_warp(const Slot<LP>& sl, unsigned lon
     // label after another, and the label's lowest lane adds the totals (one set of shared
     // atomics per label present instead of one per lane)
     const int lane = threadIdx.x & 31;
-    unsigned pending = __ballot_sync(0xffffffffu, sl.j >= 0 && sl.cnt != 0);
+    unsigned pending = __ballot_sync(0xffffffffu, sl.j >= 0);
     while (pending) {
         const int src = __ffs(pending) - 1;
         const int jj = __shfl_sync(0xffffffffu, sl.j, src);
