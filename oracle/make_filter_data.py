@@ -12,9 +12,11 @@ With --large the graphs are SBMs with n = 10^5 .. 2^21 and k = 2 .. 24 (written 
 train_data_large.npz): there n / k, the number of bulk eigen-directions per signal one, reaches
 10^5, the range in which the filter must suppress the bulk by 10^-3 or more.  With --many-k
 they are SBMs with n = 10^5 .. 6 10^5, k = 25 .. 100 and mean degree 20 .. 40
-(train_data_many_k.npz), for many clusters at large n.
+(train_data_many_k.npz), for many clusters at large n.  With --large-knn they are 10-NN graphs of
+Gaussian mixtures with 2 10^4 .. 8 10^4 points (train_data_large_knn.npz).
 
-Usage: python -m oracle.make_filter_data [--graphs 3000] [--workers 8] [--large]
+Usage: python -m oracle.make_filter_data [--graphs 3000] [--workers 8] [--large | --many-k | --large-knn]
+(the committed files: defaults; --large --graphs 360; --many-k --graphs 72; --large-knn --graphs 90)
 """
 from __future__ import annotations
 
@@ -30,6 +32,7 @@ OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "paper_2310_10939_gb300", "filter", "train_data.npz")
 OUT_LARGE = OUT.replace("train_data.npz", "train_data_large.npz")
 OUT_MANY_K = OUT.replace("train_data.npz", "train_data_many_k.npz")
+OUT_LARGE_KNN = OUT.replace("train_data.npz", "train_data_large_knn.npz")
 
 
 def _draw(i: int, base_seed: int):
@@ -66,6 +69,14 @@ def _draw_many_k(i: int, base_seed: int):
     return ("sbm", n, k, deg_in, deg_out, int(rng.integers(1, 2**31)))
 
 
+def _draw_large_knn(i: int, base_seed: int):
+    rng = np.random.default_rng(base_seed * 1_000_003 + 700_000_000 + i)
+    npts = int(round(math.exp(rng.uniform(math.log(20_000), math.log(80_000)))))
+    k = int(rng.integers(3, 21))
+    dim = int(rng.choice([8, 16, 32]))
+    return ("knn", npts, k, dim, 10, int(rng.integers(1, 2**31)))
+
+
 def _record(spec):
     import workloads as W
     from oracle import filter as fl
@@ -98,16 +109,20 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--large", action="store_true")
     ap.add_argument("--many-k", action="store_true")
+    ap.add_argument("--large-knn", action="store_true")
     args = ap.parse_args()
+    big = args.large or args.many_k or args.large_knn
     if args.out is None:
-        args.out = OUT_MANY_K if args.many_k else (OUT_LARGE if args.large else OUT)
-    draw = _draw_many_k if args.many_k else (_draw_large if args.large else _draw)
+        args.out = (OUT_LARGE_KNN if args.large_knn else OUT_MANY_K if args.many_k else
+                    OUT_LARGE if args.large else OUT)
+    draw = (_draw_large_knn if args.large_knn else _draw_many_k if args.many_k else
+            _draw_large if args.large else _draw)
     specs = [draw(i, args.seed) for i in range(args.graphs)]
-    if args.large or args.many_k:   # largest first, so the pool ends on short jobs
+    if big:   # largest first, so the pool ends on short jobs
         specs.sort(key=lambda sp: -sp[1])
     t0 = time.time()
     with mp.get_context("spawn").Pool(args.workers) as pool:
-        recs = pool.map(_record, specs, chunksize=1 if (args.large or args.many_k) else 4)
+        recs = pool.map(_record, specs, chunksize=1 if big else 4)
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     np.savez_compressed(
         args.out,

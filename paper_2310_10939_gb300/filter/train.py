@@ -1,8 +1,10 @@
 """Train the filter MLP on the GPU with the library's own forward/backward/Adam kernels.
 
-Input: train_data.npz and train_data_large.npz next to this file (features, and per graph the
-normalised quadratic (Gn, bn) of the loss ||sum_j c_j T_j(A_hat) X - P X||^2 / ||P X||^2;
-written by the oracle's data script; the second file holds SBMs with n up to 2^21).  Output: mlp_weights.npz (5833 float32 parameters that take the raw features)
+Input: the train_data*.npz files next to this file (features, and per graph the normalised
+quadratic (Gn, bn) of the loss ||sum_j c_j T_j(A_hat) X - P X||^2 / ||P X||^2; written by the
+oracle's data script): train_data.npz (SBMs and kNN graphs, n = 10^3 .. 10^5),
+train_data_large.npz (SBMs with n up to 2^21), train_data_many_k.npz (SBMs with k = 25 .. 100)
+and train_data_large_knn.npz (kNN graphs with 2 10^4 .. 8 10^4 points).  Output: mlp_weights.npz (5833 float32 parameters that take the raw features)
 and train_summary.json.
 
 Features are standardised for training (mean / std of the training split) and the affine map is
@@ -33,7 +35,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--data", default=",".join(p for p in (os.path.join(HERE, "train_data.npz"),
                                                             os.path.join(HERE, "train_data_large.npz"),
-                                                            os.path.join(HERE, "train_data_many_k.npz"))
+                                                            os.path.join(HERE, "train_data_many_k.npz"),
+                                                            os.path.join(HERE, "train_data_large_knn.npz"))
                                                if os.path.exists(p)))
     ap.add_argument("--out", default=HERE)
     ap.add_argument("--epochs", type=int, default=300)
