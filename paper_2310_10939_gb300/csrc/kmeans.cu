@@ -37,8 +37,6 @@ struct KppArgs {
     int n, l, k;
     unsigned long long seed;
     float* d2[2];
-    long long* bsum[2];  // per block: exact D^2 total of its tiles
-    long long* tsum[2];  // per (tile, warp): exact D^2 total of its 128 points
     long long* ttot[3];  // per tile: exact D^2 total (warp atomics), three in rotation
     int max_tiles;
     long long chunk;     // points per block, a multiple of KM_PPT
@@ -62,12 +60,12 @@ constexpr float KPP_EPS = 1e-5f;
 template <int LP>
 __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     unsigned epoch = 0;   // grid barriers passed
-    extern __shared__ int s_chosen[];   // k entries, then k floats: (|c_new - c_j| / 2)^2 shrunk
-    __shared__ float s_c[LP];
+    // k chosen indices, k floats (|c_new - c_j| / 2)^2 shrunk, the chosen centres (k x LP floats)
+    extern __shared__ int s_chosen[];
     __shared__ long long s_red[KM_WARPS];
-    __shared__ long long s_T, s_base;
+    __shared__ long long s_T, s_base, s_tile;
     __shared__ unsigned s_amax;
-    __shared__ int s_bstar, s_tile, s_idx;
+    __shared__ int s_bstar, s_idx;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
     const long long chunk = a.chunk;                 // multiple of KM_PPT
@@ -94,6 +92,8 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     const float A = __uint_as_float(__ldcg(a.amax));
     const Scales sc = scales_for(A, n, a.l);
 
+    float* s_half2 = reinterpret_cast<float*>(s_chosen + a.k);
+    float* s_cent = s_half2 + a.k;   // centre j at s_cent[j * LP], unused columns 0
     if (tid == 0) {
         const U64x4 r = philox4x64_10(U64x4{0ull, 0ull, 0ull, 0ull}, a.seed, STREAM_KMEANSPP);
         long long i0 = (long long)floor(uniform53(r.x) * (double)n);
@@ -102,33 +102,30 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         if (b == 0) a.seeds[0] = i0;
     }
     __syncthreads();
+    if (tid < LP) s_cent[tid] = tid < a.l ? a.X[(size_t)s_chosen[0] * LP + tid] : 0.f;
+    __syncthreads();
 
-    float* s_half2 = reinterpret_cast<float*>(s_chosen + a.k);
     const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
     for (int r = 1; r < a.k; ++r) {
-        const int cur = s_chosen[r - 1];
-        if (tid < LP) s_c[tid] = tid < a.l ? a.X[(size_t)cur * LP + tid] : 0.f;
-        __syncthreads();
+        const float* s_c = s_cent + (size_t)(r - 1) * LP;   // the centre chosen last round
         // squared half-distances from the new centre to the earlier ones, shrunk by the margin
         for (int j = tid; j < r - 1; j += KM_THREADS) {
             float cj[LP];
-            load_point<LP>(a.X, s_chosen[j], a.l, cj);
+#pragma unroll
+            for (int c = 0; c < LP; ++c) cj[c] = s_cent[(size_t)j * LP + c];
             const float h = 0.5f * sqrtf(sqdist<LP>(cj, s_c)) * (1.0f - KPP_EPS);
             s_half2[j] = h * h;
         }
         __syncthreads();
         float* d2n = a.d2[r & 1];
         const float* d2o = a.d2[(r - 1) & 1];
-        long long* bs = a.bsum[r & 1];
         long long* tt = a.ttot[r % 3];              // exact D^2 total per tile (atomics)
         long long* tz = a.ttot[(r + 1) % 3];        // cleared here for round r + 1
-        long long* wp = a.tsum[r & 1];              // exact D^2 total per (tile, warp)
         // ---- phase A: D^2 update.  Tiles of KM_TILE points are dealt round-robin (block b takes
         // b, b + G, ...): the points that cannot skip the new centre are that centre's
         // neighbourhood, a contiguous run of vertices in a clustered graph, and dealing tiles
         // spreads them over the blocks instead of loading one block while the others wait at the
         // barrier.  The next tile's D^2 and nearest-centre indices load while this tile computes.
-        long long wacc = 0;
         float old_n[KM_PPT];
         int na_n[KM_PPT];
 #pragma unroll
@@ -178,112 +175,87 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             }
             v = warp_sum_ll(v);
             if (lane == 0) {
-                wp[tile * KM_WARPS + wid] = v;
                 if (v) atomicAdd(reinterpret_cast<unsigned long long*>(tt + tile), (unsigned long long)v);
                 if (wid == 0) tz[tile] = 0;
             }
-            wacc += v;
         }
-        const long long bacc = block_sum_ll(lane == 0 ? wacc : 0ll, s_red);
-        if (tid == 0) bs[b] = bacc;
         if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
 
-        // ---- selection (identical in every block, exact integer arithmetic): the total from the
-        // block totals, then the tile, the warp segment and the point that hold the target
-        if (wid == 0) {
-            long long t = 0;
-            for (int q = lane; q < G; q += 32) t += __ldcg(bs + q);
-            t = warp_sum_ll(t);
-            if (lane == 0) {
-                if (t <= 0) {
-                    s_bstar = -1;
-                } else {
-                    const U64x4 rr = philox4x64_10(U64x4{(unsigned long long)r, 0ull, 0ull, 0ull}, a.seed,
-                                                   STREAM_KMEANSPP);
-                    const unsigned long long U = rr.x >> 11, P = (unsigned long long)t;
-                    const unsigned long long hi64 = __umul64hi(U, P), lo64 = U * P;
-                    s_T = (long long)((hi64 << 11) | (lo64 >> 53));   // floor(U * P / 2^53) < P
-                    s_bstar = 0;
-                }
-                s_base = 0;
-                s_tile = -1;
-                s_idx = INT_MAX;
+        // ---- selection (identical in every block, exact integer arithmetic).  The tile: every
+        // thread sums a contiguous range of the tile totals, one block scan gives the total (which
+        // sets the target) and each range's offset, and the thread whose range holds the target
+        // walks it.  The point: the tile's D^2 in point order, one block scan.
+        const long long per = (ntiles + KM_THREADS - 1) / KM_THREADS;
+        const long long q_lo = min(ntiles, per * tid), q_hi = min(ntiles, q_lo + per);
+        long long rsum = 0;
+        for (long long q = q_lo; q < q_hi; ++q) rsum += __ldcg(tt + q);
+        const long long rincl = block_scan_ll(rsum, s_red);
+        const long long total = s_red[KM_WARPS - 1];
+        if (tid == 0) {
+            if (total <= 0) {
+                s_bstar = -1;
+            } else {
+                const U64x4 rr = philox4x64_10(U64x4{(unsigned long long)r, 0ull, 0ull, 0ull}, a.seed,
+                                               STREAM_KMEANSPP);
+                const unsigned long long U = rr.x >> 11, P = (unsigned long long)total;
+                const unsigned long long hi64 = __umul64hi(U, P), lo64 = U * P;
+                s_T = (long long)((hi64 << 11) | (lo64 >> 53));   // floor(U * P / 2^53) < P
+                s_bstar = 0;
             }
+            s_tile = -1;
+            s_idx = INT_MAX;
         }
         __syncthreads();
-        if (s_bstar < 0) {
-            if (tid == 0) s_idx = lowest_unchosen(s_chosen, r);   // sum(D^2) = 0
-        } else {
-            // the tile: block-parallel prefix over the tile totals in point order
-            for (long long q0 = 0; q0 < ntiles; q0 += KM_THREADS) {
-                __syncthreads();
-                const long long base = s_base;
-                const long long v = q0 + tid < ntiles ? __ldcg(tt + q0 + tid) : 0ll;
-                const long long incl = block_scan_ll(v, s_red);
-                if (v > 0 && base + incl > s_T && base + incl - v <= s_T) {
-                    s_tile = (int)(q0 + tid);
-                    s_base = base + incl - v;
+        if (s_bstar == 0) {
+            const long long T = s_T;
+            const long long rex = rincl - rsum;
+            if (rsum > 0 && rex <= T && T < rincl) {   // exactly one thread
+                long long base = rex;
+                for (long long q = q_lo; q < q_hi; ++q) {
+                    const long long v = __ldcg(tt + q);
+                    if (v > 0 && base + v > T) {
+                        s_tile = q;
+                        s_base = base;
+                        break;
+                    }
+                    base += v;
                 }
-                __syncthreads();
-                if (s_tile >= 0) break;
-                if (tid == KM_THREADS - 1) s_base = base + incl;
             }
-            if (tid == 0 && s_tile < 0) s_tile = (int)(ntiles - 1);   // defensive only (exact sums always cross)
             __syncthreads();
-            if (wid == 0) {
-                const long long tq = s_tile;
-                // the warp segment of the tile (KM_WARPS <= 32 partials, one per lane)
-                const long long wv = lane < KM_WARPS ? __ldcg(wp + tq * KM_WARPS + lane) : 0ll;
-                long long incl = wv;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const long long t = __shfl_up_sync(0xffffffffu, incl, off);
-                    if (lane >= off) incl += t;
-                }
-                const long long base = s_base;
-                const unsigned m = __ballot_sync(0xffffffffu, wv > 0 && base + incl > s_T);
-                const int wq = m ? __ffs(m) - 1 : KM_WARPS - 1;
-                const long long wbase = base + __shfl_sync(0xffffffffu, incl - wv, wq);
-                // the point within the segment: 32 lanes x KM_PPT consecutive points
-                const long long i0 = tq * KM_TILE + (long long)KM_PPT * (wq * 32 + lane);
-                long long q[KM_PPT];
+            const long long tq = s_tile;
+            if (tq >= 0) {   // always (exact sums cross the target); block-uniform
+                const long long i0 = tq * KM_TILE + (long long)KM_PPT * tid;
+                long long qv[KM_PPT];
                 long long v = 0;
 #pragma unroll
                 for (int u = 0; u < KM_PPT; ++u) {
-                    q[u] = i0 + u < n ? fixq(__ldcg(d2n + i0 + u), sc.Sd) : 0;
-                    v += q[u];
+                    qv[u] = i0 + u < n ? fixq(__ldcg(d2n + i0 + u), sc.Sd) : 0;
+                    v += qv[u];
                 }
-                long long pin = v;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const long long t = __shfl_up_sync(0xffffffffu, pin, off);
-                    if (lane >= off) pin += t;
-                }
-                long long run = pin - v + wbase;   // exclusive prefix of this lane
+                const long long incl = block_scan_ll(v, s_red);
+                long long run = s_base + incl - v;   // exclusive prefix of this thread's points
 #pragma unroll
                 for (int u = 0; u < KM_PPT; ++u) {
-                    run += q[u];
-                    if (q[u] > 0 && run > s_T) {
+                    run += qv[u];
+                    if (qv[u] > 0 && run > T) {
                         atomicMin(&s_idx, (int)(i0 + u));
                         break;
                     }
                 }
             }
-            __syncthreads();
-            if (tid == 0 && s_idx == INT_MAX) s_idx = lowest_unchosen(s_chosen, r);   // defensive only
         }
+        __syncthreads();
+        if (tid == 0 && s_idx == INT_MAX) s_idx = lowest_unchosen(s_chosen, r);   // sum(D^2) = 0
         __syncthreads();
         if (tid == 0) {
             s_chosen[r] = s_idx;
             if (b == 0) a.seeds[r] = s_idx;
         }
+        if (tid < LP) s_cent[(size_t)r * LP + tid] = tid < a.l ? a.X[(size_t)s_idx * LP + tid] : 0.f;
         __syncthreads();
     }
     if (b == 0) {
-        for (int q = tid; q < a.k * LP; q += KM_THREADS) {
-            const int j = q / LP, c = q % LP;
-            a.c32[q] = c < a.l ? a.X[(size_t)s_chosen[j] * LP + c] : 0.f;
-        }
+        for (int q = tid; q < a.k * LP; q += KM_THREADS) a.c32[q] = s_cent[q];
     }
 }
 
@@ -625,7 +597,7 @@ static int coop_blocks(K kern, size_t smem) {
 template <int LP>
 static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed, int max_iter, int32_t* labels,
                             double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats, cudaStream_t s) {
-    const size_t kpp_smem = (size_t)k * (sizeof(int) + sizeof(float));
+    const size_t kpp_smem = (size_t)k * (sizeof(int) + sizeof(float) + LP * sizeof(float));
     // private accumulation tables: as many as fit in 64 KB (at least one, at most one per warp)
     const size_t tab_bytes = (size_t)k * (LP + 1) * 8;
     int ntab = (int)(65536 / tab_bytes);
@@ -652,8 +624,6 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     const size_t o_hdr = off; off += hdr;
     const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
-    const size_t o_bs = off; off += 2 * up((size_t)G * 8);
-    const size_t o_ts = off; off += 2 * up((size_t)ntiles * KM_WARPS * 8);
     const size_t o_tt = off; off += 3 * up((size_t)ntiles * 8);
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
@@ -678,10 +648,6 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         ka.seed = seed;
         ka.d2[0] = reinterpret_cast<float*>(ws + o_d2);
         ka.d2[1] = reinterpret_cast<float*>(ws + o_d2 + up((size_t)n * 4));
-        ka.bsum[0] = reinterpret_cast<long long*>(ws + o_bs);
-        ka.bsum[1] = reinterpret_cast<long long*>(ws + o_bs + up((size_t)G * 8));
-        ka.tsum[0] = reinterpret_cast<long long*>(ws + o_ts);
-        ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)ntiles * KM_WARPS * 8));
         for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(ws + o_tt + q * up((size_t)ntiles * 8));
         ka.max_tiles = (int)ntiles;
         if ((e = cudaMemsetAsync(ws + o_tt, 0, 3 * up((size_t)ntiles * 8), s)) != cudaSuccess) break;
@@ -894,7 +860,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     char* ws = static_cast<char*>(basep);
     if (!ws) return FSC_ERR_CUDA;
 
-    const size_t kpp_smem = (size_t)k * (sizeof(int) + sizeof(float));
+    const size_t kpp_smem = (size_t)k * (sizeof(int) + sizeof(float) + LP * sizeof(float));
     const size_t tab_bytes = (size_t)k * (LP + 1) * 8;
     int ntab = (int)(65536 / tab_bytes);
     if (ntab > KM_WARPS) ntab = KM_WARPS;
@@ -919,8 +885,6 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     const size_t o_hdr = off; off += hdr;
     const size_t o_acc = off; off += acc;
     const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
-    const size_t o_bs = off; off += 2 * up((size_t)G * 8);
-    const size_t o_ts = off; off += 2 * up((size_t)ntiles * KM_WARPS * 8);
     const size_t o_tt = off; off += 3 * up((size_t)ntiles * 8);
     const size_t o_c64 = off; off += up((size_t)k * LP * 8);
     const size_t o_c32 = off; off += up((size_t)k * LP * 4);
@@ -943,10 +907,6 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     ka.seed = seed;
     ka.d2[0] = reinterpret_cast<float*>(ws + o_d2);
     ka.d2[1] = reinterpret_cast<float*>(ws + o_d2 + up((size_t)n * 4));
-    ka.bsum[0] = reinterpret_cast<long long*>(ws + o_bs);
-    ka.bsum[1] = reinterpret_cast<long long*>(ws + o_bs + up((size_t)G * 8));
-    ka.tsum[0] = reinterpret_cast<long long*>(ws + o_ts);
-    ka.tsum[1] = reinterpret_cast<long long*>(ws + o_ts + up((size_t)ntiles * KM_WARPS * 8));
     for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(ws + o_tt + q * up((size_t)ntiles * 8));
     ka.max_tiles = (int)ntiles;
     FSC_CUDA(cudaMemsetAsync(ws + o_tt, 0, 3 * up((size_t)ntiles * 8), s));
