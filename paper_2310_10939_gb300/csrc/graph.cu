@@ -246,12 +246,12 @@ __global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const in
 // only to validate it.  A block takes a tile of `rows` consecutive rows (dynamic shared memory
 // holds the tile's rows + 1 row_ptr values): one thread per row writes the degrees (coalesced),
 // then the block streams the tile's entries as one flat range of VEC-entry vectors, kDegUnroll
-// independent loads in flight per thread.  An entry's row (a binary search in the shared row_ptr)
-// is looked up only where the checks need it: when its column lies in the tile's own rows (a
-// possible self-loop) or, with the sortedness check, when it is not above its predecessor.  On a
-// graph without locality that is a fraction rows / n of the entries, so the scan costs a few
-// instructions per entry.  The tile size is chosen so the grid is about one wave of resident
-// blocks; HBM traffic is row_ptr, col and the three n-vectors once.
+// independent loads in flight per thread.  No entry needs its own row: a self-loop (i, i) has i
+// in the tile, and then the entry's position lies in row i's range, two shared-memory reads
+// away.  Only the optional sortedness check looks a row up (a binary search in the shared
+// row_ptr), and only at an inversion col[p-1] >= col[p], which is a row start or an unsorted
+// row.  The tile size is chosen so the grid is about one wave of resident blocks; HBM traffic
+// is row_ptr, col and the three n-vectors once.
 constexpr int kDegUnroll = 4;
 
 template <int VEC>
@@ -343,28 +343,22 @@ __global__ void __launch_bounds__(256) k_degree_unit(int64_t n, int64_t nnz, con
                     const long long p = base + u;
                     if (!interior && (p < P0 || p >= P1)) continue;
                     const int j = x[h][u];
-                    if ((unsigned)j >= (unsigned)n) {   // also j < 0
-                        bad |= ST_INDEX_RANGE;
-                        continue;
-                    }
-                    // the row of p is needed only where it can matter: a self-loop (i, i) has i in
-                    // this tile's rows, and an inversion col[p-1] >= col[p] is either a row start
-                    // or an unsorted row
-                    bool need_row = (unsigned)(j - r0i) < (unsigned)nr;
-                    int prev = 0;
+                    const int jl = j - r0i;   // j's row within the tile, if it is one
+                    // a self-loop (i, i) needs i in the tile: then p lies in row i's range
+                    if ((unsigned)j >= (unsigned)n) bad |= ST_INDEX_RANGE;
+                    else if ((unsigned)jl < (unsigned)nr && s_rp[jl] <= p && p < s_rp[jl + 1]) bad |= ST_SELF_LOOP;
                     if (check_sorted && p > P0) {
-                        prev = u > 0 ? x[h][u > 0 ? u - 1 : 0] : __ldg(col + p - 1);
-                        need_row |= prev >= j;
-                    }
-                    if (need_row) {
-                        int lo = 0, hi = nr - 1;   // last row whose start is <= p (s_rp[nr] = P1 > p)
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (s_rp[mid] <= p) lo = mid;
-                            else hi = mid - 1;
+                        // an inversion col[p-1] >= col[p] is either a row start or an unsorted row
+                        const int prev = u > 0 ? x[h][u > 0 ? u - 1 : 0] : __ldg(col + p - 1);
+                        if (prev >= j) {
+                            int lo = 0, hi = nr - 1;   // last row whose start is <= p (s_rp[nr] = P1 > p)
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (s_rp[mid] <= p) lo = mid;
+                                else hi = mid - 1;
+                            }
+                            if (p > s_rp[lo]) bad |= ST_UNSORTED;
                         }
-                        if (j == r0i + lo) bad |= ST_SELF_LOOP;
-                        if (check_sorted && p > s_rp[lo] && prev >= j) bad |= ST_UNSORTED;
                     }
                 }
             }
