@@ -125,14 +125,21 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         // b, b + G, ...): the points that cannot skip the new centre are that centre's
         // neighbourhood, a contiguous run of vertices in a clustered graph, and dealing tiles
         // spreads them over the blocks instead of loading one block while the others wait at the
-        // barrier.  The next tile's D^2 and nearest-centre indices load while this tile computes.
+        // barrier.  The next tile's D^2 and nearest-centre indices load while this tile computes,
+        // and for l_pad <= 4 its points too (all of them: the skip then saves no latency, only L2
+        // reads, and the registers of the l_pad = 8 kernel are spent).
+        constexpr bool kPre = LP <= 4;
         float old_n[KM_PPT];
         int na_n[KM_PPT];
+        float x_n[KM_PPT][LP];
 #pragma unroll
         for (int u = 0; u < KM_PPT; ++u) {
             const long long i = (long long)b * KM_TILE + (long long)KM_PPT * tid + u;
             old_n[u] = (r > 1 && i < n) ? d2o[i] : 0.f;
             na_n[u] = (r > 1 && i < n) ? a.near[i] : 0;
+            if constexpr (kPre) {
+                if (i < n) load_point<LP>(a.X, i, a.l, x_n[u]);
+            }
         }
         for (long long tile = b; tile < ntiles; tile += G) {
             const long long t0 = tile * KM_TILE;
@@ -140,6 +147,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             float old[KM_PPT];
             int na[KM_PPT];
             bool need[KM_PPT];
+            float x[KM_PPT][LP];
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
                 old[u] = old_n[u];
@@ -147,16 +155,22 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                 const long long inext = i0 + (long long)G * KM_TILE + u;
                 old_n[u] = (r > 1 && inext < n) ? d2o[inext] : 0.f;
                 na_n[u] = (r > 1 && inext < n) ? a.near[inext] : 0;
+                if constexpr (kPre) {
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) x[u][c] = x_n[u][c];
+                    if (inext < n) load_point<LP>(a.X, inext, a.l, x_n[u]);
+                }
             }
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
                 const bool in = i0 + u < n;
                 need[u] = in && (r == 1 || old[u] * (1.0f + KPP_EPS) * (1.0f + KPP_EPS) >= s_half2[na[u]]);
             }
-            float x[KM_PPT][LP];
+            if constexpr (!kPre) {
 #pragma unroll
-            for (int u = 0; u < KM_PPT; ++u)
-                if (need[u]) load_point<LP>(a.X, i0 + u, a.l, x[u]);
+                for (int u = 0; u < KM_PPT; ++u)
+                    if (need[u]) load_point<LP>(a.X, i0 + u, a.l, x[u]);
+            }
             long long v = 0;
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
@@ -357,7 +371,11 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
     __shared__ int s_qold[KM_WARPS][KM_PPT * 32];
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
-    const long long lo = min(n, (long long)b * a.chunk), hi = min(n, lo + a.chunk);   // this block's points
+    // tiles of KM_TILE points dealt round-robin (block b takes b, b + G, ...): the points that
+    // need the k-way scan or change cluster sit where planted clusters meet, a contiguous vertex
+    // range, and dealing spreads them over the blocks
+    const long long ntl = (n + KM_TILE - 1) / KM_TILE;
+    const int G = gridDim.x;
     const Scales sc = scales_for(__uint_as_float(__ldcg(a.amax)), n, a.l);
     unsigned long long* my_tab = s_tab + (size_t)(wid % ntab) * rowlen;
 
@@ -417,7 +435,8 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
         }
         int* qoff = s_qoff[wid];
         int* qold = s_qold[wid];
-        for (long long t0 = lo; t0 < hi; t0 += KM_TILE) {
+        for (long long tile = b; tile < ntl; tile += G) {
+            const long long t0 = tile * KM_TILE, hi = min(n, t0 + KM_TILE);
             const long long i0 = t0 + (long long)KM_PPT * tid;
             float x[KM_PPT][LP];
             int old[KM_PPT];
@@ -452,7 +471,7 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
                 const unsigned m = __ballot_sync(0xffffffffu, need);
                 if (need) {
                     const int pos = qn + __popc(m & ((1u << lane) - 1u));
-                    qoff[pos] = (int)(i0 + u - lo);
+                    qoff[pos] = (int)(i0 + u - t0);
                     qold[pos] = old[u];
                 }
                 qn += __popc(m);
@@ -461,7 +480,7 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
             for (int q0 = 0; q0 < qn; q0 += 32) {
                 const int q = q0 + lane;
                 const bool act = q < qn;
-                const long long i = act ? lo + qoff[q] : lo;
+                const long long i = act ? t0 + qoff[q] : t0;
                 float xv[LP];
                 load_point<LP>(a.X, i, a.l, xv);
                 float best = __int_as_float(0x7f800000), sec = __int_as_float(0x7f800000);
@@ -554,7 +573,8 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
     // ---- inertia of the last assignment: each point's float32 distance to the centroid it was
     // assigned to (the same value the assignment computed), summed exactly in fixed point
     long long inert = 0;
-    for (long long t0 = lo; t0 < hi; t0 += KM_TILE) {
+    for (long long tile = b; tile < ntl; tile += G) {
+        const long long t0 = tile * KM_TILE, hi = min(n, t0 + KM_TILE);
         const long long i0 = t0 + (long long)KM_PPT * tid;
 #pragma unroll
         for (int u = 0; u < KM_PPT; ++u) {
@@ -611,11 +631,13 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     if (G2 < G) G = G2;
     if (G < 1) return FSC_ERR_CUDA;
     if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
-    // contiguous chunks (multiples of KM_PPT points); drop blocks that would get no point
+    // both kernels deal tiles of KM_TILE points round-robin: no more blocks than tiles; the
+    // k-means++ maximum pass takes contiguous chunks (multiples of KM_PPT points)
+    const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;
+    if (G > ntiles) G = (int)ntiles;
     long long chunk = ((long long)n + G - 1) / G;
     chunk = (chunk + KM_PPT - 1) / KM_PPT * KM_PPT;
     G = (int)(((long long)n + chunk - 1) / chunk);
-    const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;   // k-means++ deals these round-robin
 
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
@@ -873,10 +895,11 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     if (G2 < G) G = G2;
     if (G < 1) return FSC_ERR_CUDA;
     if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
+    const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;   // both kernels deal these round-robin
+    if (G > ntiles) G = (int)ntiles;
     long long chunk = ((long long)n + G - 1) / G;
     chunk = (chunk + KM_PPT - 1) / KM_PPT * KM_PPT;
     G = (int)(((long long)n + chunk - 1) / chunk);
-    const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;   // k-means++ deals these round-robin
 
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
