@@ -188,8 +188,9 @@ extern "C" fsc_status fsc_batch_create(const fsc_batch_desc* d, void* stream, fs
             const size_t tab = (size_t)x.k * (x.LP + 1) * 8;
             int ntab = (int)(32768 / tab);
             x.ntab = ntab < 1 ? 1 : (ntab > KM_WARPS ? KM_WARPS : ntab);
+            // centroids (float32, float64), chosen indices, ntab tables and the running totals
             const size_t need = (((size_t)x.k * x.LP * 4 + 15) & ~(size_t)15) + (size_t)x.k * x.LP * 8 +
-                                (((size_t)x.k * 4 + 15) & ~(size_t)15) + (size_t)x.ntab * tab;
+                                (((size_t)x.k * 4 + 15) & ~(size_t)15) + (size_t)(x.ntab + 1) * tab;
             smem = std::max(smem, need);
             // every per-graph base is rounded to 64 elements (>= 128 bytes), so the row vectors of
             // any LP stay aligned whatever the previous graphs' sizes were

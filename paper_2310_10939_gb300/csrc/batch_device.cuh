@@ -85,11 +85,80 @@ __device__ void init_block(const BatchGraph& g, const float* __restrict__ dinv, 
     }
 }
 
+// row_gather (spmm.cuh) for R rows at once, their loads interleaved: one block per SM has a third
+// of the warps the single-graph kernel keeps in flight, so each lane group carries R rows to keep
+// as many gathers outstanding.  Each row's sum is formed exactly as row_gather forms it (the same
+// passes, entries and order; a row adds nothing in the passes after its own last one).
+template <int LP, typename TI, int G, int U, bool W, int R>
+__device__ __forceinline__ void rows_gather(const bool (&active)[R], const long long (&row)[R], int sub,
+                                            const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                            const float* __restrict__ w, const TI* zin, long long col_off,
+                                            float (&acc)[R][LP]) {
+    int64_t p[R], e[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int c = 0; c < LP; ++c) acc[r][c] = 0.f;
+        p[r] = active[r] ? rp[row[r]] + sub : 0;
+        e[r] = active[r] ? rp[row[r] + 1] : 0;
+    }
+    for (;;) {
+        bool live[R], any = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            live[r] = p[r] < e[r];
+            any |= live[r];
+        }
+        if (!any) break;
+        long long j[R][U];
+        float wv[R][U];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t q = p[r] + (int64_t)u * G;
+                const bool ok = live[r] && q < e[r];
+                j[r][u] = ok ? (long long)__ldg(col + q) - col_off : -1;
+                if (W) wv[r][u] = ok ? __ldg(w + q) : 0.f;
+            }
+        float v[R][U][LP];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j[r][u] >= 0) {
+                    load_z<LP, TI, false>(zin + (size_t)j[r][u] * LP, v[r][u]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) v[r][u][c] = 0.f;
+                }
+            }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (live[r]) {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int c = 0; c < LP; ++c)
+                        acc[r][c] = W ? fmaf(wv[r][u], v[r][u][c], acc[r][c]) : acc[r][c] + v[r][u][c];
+            }
+            p[r] += (int64_t)G * U;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < LP; ++c) acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], off);
+}
+
 template <int LP, typename TS, int G, bool W>
 __device__ void power_block(const BatchGraph& g, const BatchArgs& a, TS* zA, TS* zB, float* emb, float* s_cm,
                             int* s_E) {
     constexpr int U = G <= 8 ? 4 : 2;
     constexpr int RPW = 32 / G;
+    constexpr int R = 2;   // rows in flight per lane group
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, sub = lane % G, grp = lane / G;
     const int64_t* rp = a.row_ptr + g.v0;
     const float* invdeg = a.invdeg + g.v0;
@@ -110,19 +179,29 @@ __device__ void power_block(const BatchGraph& g, const BatchArgs& a, TS* zA, TS*
         float cmx[LP];
 #pragma unroll
         for (int c = 0; c < LP; ++c) cmx[c] = 0.f;
-        for (long long base = (long long)wid * RPW; base < g.n; base += (long long)KM_WARPS * RPW) {
-            const long long row = base + grp;
-            float y[LP];
-            bool wrote;
-            if (last)
-                wrote = power_row<LP, TS, float, G, U, W, false>(row < g.n, row, sub, rp, a.col, a.w, invdeg, zin,
-                                                                 emb, g.v0, scale, y);
-            else
-                wrote = power_row<LP, TS, TS, G, U, W, false>(row < g.n, row, sub, rp, a.col, a.w, invdeg, zin,
-                                                              zout, g.v0, scale, y);
-            if (wrote) {
+        for (long long base = (long long)wid * RPW * R; base < g.n; base += (long long)KM_WARPS * RPW * R) {
+            long long row[R];
+            bool act[R];
 #pragma unroll
-                for (int c = 0; c < LP; ++c) cmx[c] = fmaxf(cmx[c], fabsf(y[c]));
+            for (int r = 0; r < R; ++r) {
+                row[r] = base + (long long)r * RPW + grp;
+                act[r] = row[r] < g.n;
+            }
+            float acc[R][LP];
+            rows_gather<LP, TS, G, U, W, R>(act, row, sub, rp, a.col, a.w, zin, g.v0, acc);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (act[r] && sub == 0) {   // the same epilogue as power_row
+                    float self[LP], y[LP];
+                    load_z<LP, TS, false>(zin + (size_t)row[r] * LP, self);
+                    const float id = invdeg[row[r]];
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) y[c] = scale[c] * (0.5f * fmaf(id, acc[r][c], self[c]));
+                    if (last) store_row<LP, float>(emb + (size_t)row[r] * LP, y);
+                    else store_row<LP, TS>(zout + (size_t)row[r] * LP, y);
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) cmx[c] = fmaxf(cmx[c], fabsf(y[c]));
+                }
             }
         }
         if (!last) {
@@ -262,9 +341,14 @@ __device__ void kpp_block(const float* X, int n, int l, int k, unsigned long lon
     __syncthreads();
 }
 
+// Lloyd in one CTA with the same exact arithmetic as k_lloyd: the cluster sums are running
+// totals (s_S) that only points changing cluster update, and the inertia is taken in the first
+// iteration and, for the last assignment, by one pass after the loop with the centroids that
+// assignment used.
 template <int LP>
 __device__ void lloyd_block(const float* X, int n, int l, int k, int max_iter, const Scales& sc, int32_t* labels,
-                            float* s_c, double* s_c64, unsigned long long* s_tab, int ntab, KmDevStats* st) {
+                            float* s_c, double* s_c64, unsigned long long* s_tab, int ntab, long long* s_S,
+                            KmDevStats* st) {
     __shared__ long long s_red[KM_WARPS];
     __shared__ int s_redi[KM_WARPS];
     const int tid = threadIdx.x, wid = tid >> 5;
@@ -272,6 +356,7 @@ __device__ void lloyd_block(const float* X, int n, int l, int k, int max_iter, c
     unsigned long long* my_tab = s_tab + (size_t)(wid % ntab) * rowlen;
     for (long long i = tid; i < n; i += KM_THREADS) labels[i] = -1;
     for (int q = tid; q < k * LP; q += KM_THREADS) s_c64[q] = (double)s_c[q];
+    for (size_t q = tid; q < rowlen; q += KM_THREADS) s_S[q] = 0;
     int empty = 0;
     const int ntiles = (n + KM_TILE - 1) / KM_TILE;
     for (int it = 1; it <= max_iter; ++it) {
@@ -323,29 +408,16 @@ __device__ void lloyd_block(const float* X, int n, int l, int k, int max_iter, c
             for (int u = 0; u < KM_PPT; ++u) {
                 if (i0 + u >= n) break;
                 const int lab = bj[u];
-                changed += old[u] != lab;
-                labels[i0 + u] = lab;
-                inert += fixq(best[u], sc.Sd);
-                int q;
-                if (sl[0].j == lab) q = 0;
-                else if (sl[1].j == lab) q = 1;
-                else {
-                    slot_flush<LP>(sl[1], my_tab);
-                    sl[1] = sl[0];
-                    sl[0].j = lab;
-                    sl[0].cnt = 0;
+                if (it == 1) inert += fixq(best[u], sc.Sd);
+                if (old[u] != lab) {   // leaves its old cluster (none in iteration 1), joins the new
+                    ++changed;
+                    labels[i0 + u] = lab;
+                    long long qx[LP];
 #pragma unroll
-                    for (int c = 0; c < LP; ++c) sl[0].s[c] = 0;
-                    q = 0;
+                    for (int c = 0; c < LP; ++c) qx[c] = fixq(x[u][c], sc.Sx);
+                    slot_add<LP>(sl, lab, qx, false, my_tab);
+                    if (old[u] >= 0) slot_add<LP>(sl, old[u], qx, true, my_tab);
                 }
-                if (q == 1) {
-                    const Slot<LP> t = sl[0];
-                    sl[0] = sl[1];
-                    sl[1] = t;
-                }
-#pragma unroll
-                for (int c = 0; c < LP; ++c) sl[0].s[c] += fixq(x[u][c], sc.Sx);
-                ++sl[0].cnt;
             }
         }
         slot_flush_warp<LP>(sl[0], my_tab);
@@ -354,34 +426,51 @@ __device__ void lloyd_block(const float* X, int n, int l, int k, int max_iter, c
         for (size_t q = tid; q < rowlen; q += KM_THREADS) {
             unsigned long long v = s_tab[q];
             for (int t = 1; t < ntab; ++t) v += s_tab[(size_t)t * rowlen + q];
-            s_tab[q] = v;
+            s_S[q] += (long long)v;   // exact running totals
         }
         inert = block_sum_ll(inert, s_red);
         changed = block_sum_i(changed, s_redi);
         __syncthreads();
+        // on the last iteration s_c keeps the centroids its assignment used (for the inertia)
+        const bool stop = changed == 0 || it == max_iter;
         for (int q = tid; q < k * LP; q += KM_THREADS) {
             const int j = q / LP, c = q % LP;
-            const long long cnt = (long long)s_tab[(size_t)j * (LP + 1) + LP];
+            const long long cnt = s_S[(size_t)j * (LP + 1) + LP];
             if (cnt > 0) {
-                const double m = ((double)(long long)s_tab[(size_t)j * (LP + 1) + c] * pow2d(-sc.Sx)) / (double)cnt;
+                const double m = ((double)s_S[(size_t)j * (LP + 1) + c] * pow2d(-sc.Sx)) / (double)cnt;
                 s_c64[q] = m;
-                s_c[q] = (float)m;
+                if (!stop) s_c[q] = (float)m;
             } else if (c == 0) {
                 ++empty;
             }
         }
         __syncthreads();
         if (tid == 0) {
-            const double iv = (double)inert * pow2d(-sc.Sd);
-            st->inertia = iv;
-            if (it == 1) st->potential = iv;
+            if (it == 1) st->potential = (double)inert * pow2d(-sc.Sd);
             st->iterations = it;
             st->changed = changed;
         }
-        if (changed == 0 || it == max_iter) break;
+        if (stop) break;
     }
+    long long inert = 0;
+    for (int tl = 0; tl < ntiles; ++tl) {
+        const long long i0 = (long long)tl * KM_TILE + (long long)KM_PPT * tid;
+#pragma unroll
+        for (int u = 0; u < KM_PPT; ++u) {
+            if (i0 + u < n) {
+                float x[LP];
+                load_point_cg<LP>(X, i0 + u, l, x);
+                const int lab = __ldcg(labels + i0 + u);
+                inert += fixq(sqdist<LP>(x, s_c + lab * LP), sc.Sd);
+            }
+        }
+    }
+    inert = block_sum_ll(inert, s_red);
     const int e = block_sum_i(empty, s_redi);
-    if (tid == 0) st->empty_events = e;
+    if (tid == 0) {
+        st->empty_events = e;
+        st->inertia = (double)inert * pow2d(-sc.Sd);
+    }
     __syncthreads();
 }
 
@@ -424,7 +513,8 @@ __device__ void run_graph(const BatchArgs& a, const BatchGraph& g, unsigned char
     KmDevStats* st = a.stats + g.gid;
     kpp_block<LP>(emb, g.n, g.l, g.k, g.seed, sc, a.darena + g.doff, a.tarena + g.toff, s_chosen, s_c,
                   a.seeds + g.soff);
-    lloyd_block<LP>(emb, g.n, g.l, g.k, a.max_iter, sc, a.labels + g.v0, s_c, s_c64, s_tab, g.ntab, st);
+    long long* s_S = reinterpret_cast<long long*>(s_tab + (size_t)g.ntab * g.k * (LP + 1));
+    lloyd_block<LP>(emb, g.n, g.l, g.k, a.max_iter, sc, a.labels + g.v0, s_c, s_c64, s_tab, g.ntab, s_S, st);
     for (int q = tid; q < g.k * LP; q += KM_THREADS) a.cents[g.coff + q] = s_c64[q];
     __syncthreads();
 }

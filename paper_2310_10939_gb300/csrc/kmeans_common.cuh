@@ -155,6 +155,30 @@ __device__ __forceinline__ void slot_flush(const Slot<LP>& sl, unsigned long lon
     atomicAdd(row + LP, (unsigned long long)sl.cnt);
 }
 
+// Adds sign * q (a point's exact coordinates) and sign to cluster lab through the two-slot run
+// cache in front of the warp's shared table (slot 0 holds the most recent label).
+template <int LP>
+__device__ __forceinline__ void slot_add(Slot<LP> (&sl)[2], int lab, const long long (&q)[LP], bool minus,
+                                         unsigned long long* tab) {
+    if (sl[0].j != lab) {
+        if (sl[1].j == lab) {
+            const Slot<LP> t = sl[0];
+            sl[0] = sl[1];
+            sl[1] = t;
+        } else {
+            slot_flush<LP>(sl[1], tab);   // evict the older run
+            sl[1] = sl[0];
+            sl[0].j = lab;
+            sl[0].cnt = 0;
+#pragma unroll
+            for (int c = 0; c < LP; ++c) sl[0].s[c] = 0;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < LP; ++c) sl[0].s[c] += minus ? -q[c] : q[c];
+    sl[0].cnt += minus ? -1 : 1;
+}
+
 template <int LP>
 __device__ __forceinline__ void slot_flush_warp(const Slot<LP>& sl, unsigned long long* tab) {
     // all 32 lanes call this: lanes holding the same label are summed by warp reductions, one
