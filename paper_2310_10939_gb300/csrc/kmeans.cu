@@ -273,6 +273,18 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     }
 }
 
+// k_lloyd's dynamic shared memory: centroids (16-byte aligned), ntab private tables, half the
+// separation of each centroid (k floats, padded to 8 bytes), the running totals k (LP + 1), the
+// last move of each centroid (k floats), then (16-byte aligned) the per-warp point queues of
+// KM_QUEUE entries (index, old label, lower bound).
+constexpr int KM_QUEUE = 256;
+__host__ __device__ inline size_t lloyd_queue_offset(int k, int LP, int ntab) {
+    const size_t rowlen = (size_t)k * (LP + 1);
+    const size_t end = (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * rowlen * 8 +
+                       (((size_t)k + 1) / 2) * 8 + rowlen * 8 + (size_t)k * 4;
+    return (end + 15) & ~(size_t)15;
+}
+
 struct LloydArgs {
     const float* X;
     int n, l, k, max_iter;
@@ -285,6 +297,7 @@ struct LloydArgs {
     long long chunk;            // points per block (a multiple of KM_PPT)
     int ntab;
     float* lbound;       // per point: lower bound on the distance to every other centroid (pruning)
+    float* ubound;       // per point: upper bound on the distance to its own centroid (pruning)
     int prune;           // 1: skip the k-way scan of points whose bounds prove the label unchanged
     KmDevStats* st;
     GridBarrier* bar;
@@ -301,6 +314,10 @@ struct LloydArgs {
 // skipped point is exactly one the full scan would leave in place (no tie is possible).
 constexpr float PRUNE_EPS = 1e-5f;
 constexpr float PRUNE_GROW2 = (1.0f + PRUNE_EPS) * (1.0f + PRUNE_EPS);   // the test runs on squares
+// The upper bound u on a point's distance to its own centroid is carried from one iteration to
+// the next by adding that centroid's movement (itself computed with a PRUNE_EPS margin), and the
+// sum is grown by 4 ulp so its own float rounding can only raise it.
+constexpr float UBOUND_GROW = 1.0f + 4.0f / 8388608.0f;
 
 // Settles a point that went through the k-way scan: lower bound, label, changed count and, in the
 // first iteration, its distance in the inertia.  The centroid sums are running totals, so only a
@@ -325,7 +342,7 @@ __device__ __forceinline__ void lloyd_commit(const LloydArgs& a, long long i, co
 }
 
 template <int LP>
-__global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydArgs a) {
+__global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
     extern __shared__ __align__(16) unsigned char km_smem[];
     unsigned epoch = 0;   // grid barriers passed
     const int k = a.k;
@@ -337,14 +354,18 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
     float* s_sep = reinterpret_cast<float*>(s_tab + (size_t)ntab * rowlen);   // k floats
     // running exact sums and counts of every cluster (the same in every block)
     long long* s_S = reinterpret_cast<long long*>(s_tab + (size_t)ntab * rowlen + (((size_t)k + 1) / 2));
+    float* s_mv = reinterpret_cast<float*>(s_S + rowlen);   // k floats: each centroid's last move, grown
+    // per-warp queues of points whose loose test failed: index, old label, decayed lower bound
+    int* s_qidx = reinterpret_cast<int*>(km_smem + lloyd_queue_offset(k, LP, ntab));
+    int* s_qold = s_qidx + KM_WARPS * KM_QUEUE;
+    float* s_qlw = reinterpret_cast<float*>(s_qold + KM_WARPS * KM_QUEUE);
     float* s_cn = reinterpret_cast<float*>(s_tab);   // new centroids, staged in the tables once they are summed
     __shared__ long long s_red[KM_WARPS];
     __shared__ int s_redi[KM_WARPS];
     __shared__ long long s_inert;
     __shared__ int s_changed;
     __shared__ unsigned s_pmax;
-    __shared__ int s_qoff[KM_WARPS][KM_PPT * 32];
-    __shared__ int s_qold[KM_WARPS][KM_PPT * 32];
+
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
     // tiles of KM_TILE points dealt round-robin (block b takes b, b + G, ...): the points that
@@ -397,10 +418,14 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
         const float pmax = pr ? __uint_as_float(s_pmax) * (1.0f + PRUNE_EPS) : 0.f;
         long long inert = 0;
         int changed = 0;
-        // ---- phase A.  Each thread takes KM_PPT consecutive points of a tile and settles those
-        // its bounds prove unchanged; the others go to a per-warp queue that the warp then scans
-        // against all k centroids one point per lane, so no lane idles behind a neighbour's scan.
-        // Centroid sums are exact integers, so which lane adds a point changes no result.
+        // ---- phase A.  Each thread takes KM_PPT consecutive points of a tile and settles, from
+        // its label and bounds alone, those whose upper bound u (carried forward by the centroid's
+        // move) is below max(s(a), lower bound): Hamerly's test, without loading the point.  The
+        // others go to a per-warp queue that the warp then works one point per lane: the exact
+        // distance to the own centroid first (the same test, tight), the k-way scan only if that
+        // fails, so no lane idles behind a neighbour's scan.  Centroid sums are exact integers,
+        // so which lane adds a point changes no result.  The next tile's labels and bounds load
+        // while this tile is settled.
         Slot<LP> sl[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -409,74 +434,110 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
 #pragma unroll
             for (int c = 0; c < LP; ++c) sl[q].s[c] = 0;
         }
-        int* qoff = s_qoff[wid];
-        int* qold = s_qold[wid];
+        int* qidx = s_qidx + wid * KM_QUEUE;
+        int* qold = s_qold + wid * KM_QUEUE;
+        float* qlw = s_qlw + wid * KM_QUEUE;
+        int qn = 0;   // queue length (warp-uniform)
+        // works the queued points, 32 at a time (one per lane)
+        auto flush = [&]() {
+            __syncwarp();
+            for (int q0 = 0; q0 < qn; q0 += 32) {
+                const int q = q0 + lane;
+                const bool act = q < qn;
+                const long long i = act ? qidx[q] : 0;
+                const int oldl = act ? qold[q] : 0;
+                const float lw = act ? qlw[q] : 0.f;
+                float xv[LP];
+                load_point<LP>(a.X, i, a.l, xv);
+                // the tight test: the exact distance to the own centroid
+                bool settled = false;
+                float da = 0.f;
+                if (pr && act) {
+                    da = sqdist<LP>(xv, s_c + oldl * LP);
+                    const float bnd = fmaxf(s_sep[oldl], lw);
+                    settled = da * PRUNE_GROW2 < bnd * bnd;
+                }
+                float best = __int_as_float(0x7f800000), sec = __int_as_float(0x7f800000);
+                int bj = 0;
+                if (__any_sync(0xffffffffu, act && !settled)) {
+#pragma unroll 4
+                    for (int j = 0; j < k; ++j) {
+                        const float d = sqdist<LP>(xv, s_c + j * LP);
+                        if (d < best) {
+                            sec = best;
+                            best = d;
+                            bj = j;
+                        } else if (d < sec) {
+                            sec = d;
+                        }
+                    }
+                }
+                if (act) {
+                    if (settled) {
+                        a.lbound[i] = lw;
+                        a.ubound[i] = sqrtf(da) * (1.0f + PRUNE_EPS);
+                    } else {
+                        lloyd_commit<LP>(a, i, xv, oldl, bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), it == 1, sc, sl,
+                                         my_tab, inert, changed);
+                        if (a.prune) a.ubound[i] = sqrtf(best) * (1.0f + PRUNE_EPS);
+                    }
+                }
+            }
+            __syncwarp();
+            qn = 0;
+        };
+        int old_n[KM_PPT];
+        float lbv_n[KM_PPT], ubv_n[KM_PPT];
+        auto fetch = [&](long long tile) {
+            const long long i0 = tile * KM_TILE + (long long)KM_PPT * tid;
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                const bool in = tile < ntl && i0 + u < n;
+                old_n[u] = in ? a.labels[i0 + u] : 0;
+                lbv_n[u] = in && pr ? a.lbound[i0 + u] : 0.f;
+                ubv_n[u] = in && pr ? a.ubound[i0 + u] : 0.f;
+            }
+        };
+        fetch(b);
         for (long long tile = b; tile < ntl; tile += G) {
             const long long t0 = tile * KM_TILE, hi = min(n, t0 + KM_TILE);
             const long long i0 = t0 + (long long)KM_PPT * tid;
-            float x[KM_PPT][LP];
             int old[KM_PPT];
-            float lbv[KM_PPT];
+            float lbv[KM_PPT], ubv[KM_PPT];
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
-                if (i0 + u < hi) {
-                    load_point<LP>(a.X, i0 + u, a.l, x[u]);
-                    old[u] = a.labels[i0 + u];
-                    lbv[u] = pr ? a.lbound[i0 + u] : 0.f;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < LP; ++c) x[u][c] = 0.f;
-                    old[u] = 0;
-                    lbv[u] = 0.f;
-                }
+                old[u] = old_n[u];
+                lbv[u] = lbv_n[u];
+                ubv[u] = ubv_n[u];
             }
-            int qn = 0;   // queue length (warp-uniform)
+            fetch(tile + G);
+            if (qn > KM_QUEUE - KM_PPT * 32) flush();   // room for this tile's points
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
                 bool need = i0 + u < hi;
+                float lw = 0.f;
                 if (pr && need) {
                     const int ca = old[u];
-                    const float da = sqdist<LP>(x[u], s_c + ca * LP);
-                    const float lw = fmaxf(0.f, lbv[u] - pmax);
+                    lw = fmaxf(0.f, lbv[u] - pmax);
                     const float bnd = fmaxf(s_sep[ca], lw);
-                    if (da * PRUNE_GROW2 < bnd * bnd) {
+                    const float ub = (ubv[u] + s_mv[ca]) * UBOUND_GROW;
+                    if (ub < bnd) {
                         a.lbound[i0 + u] = lw;
+                        a.ubound[i0 + u] = ub;
                         need = false;
                     }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, need);
                 if (need) {
                     const int pos = qn + __popc(m & ((1u << lane) - 1u));
-                    qoff[pos] = (int)(i0 + u - t0);
+                    qidx[pos] = (int)(i0 + u);
                     qold[pos] = old[u];
+                    qlw[pos] = lw;
                 }
                 qn += __popc(m);
             }
-            __syncwarp();
-            for (int q0 = 0; q0 < qn; q0 += 32) {
-                const int q = q0 + lane;
-                const bool act = q < qn;
-                const long long i = act ? t0 + qoff[q] : t0;
-                float xv[LP];
-                load_point<LP>(a.X, i, a.l, xv);
-                float best = __int_as_float(0x7f800000), sec = __int_as_float(0x7f800000);
-                int bj = 0;
-#pragma unroll 4
-                for (int j = 0; j < k; ++j) {
-                    const float d = sqdist<LP>(xv, s_c + j * LP);
-                    if (d < best) {
-                        sec = best;
-                        best = d;
-                        bj = j;
-                    } else if (d < sec) {
-                        sec = d;
-                    }
-                }
-                if (act) lloyd_commit<LP>(a, i, xv, qold[q], bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), it == 1, sc, sl,
-                                          my_tab, inert, changed);
-            }
-            __syncwarp();
         }
+        flush();
         slot_flush_warp<LP>(sl[0], my_tab);
         slot_flush_warp<LP>(sl[1], my_tab);
         __syncthreads();
@@ -524,7 +585,8 @@ __global__ void __launch_bounds__(KM_THREADS, (LP >= 4 ? 1 : 2)) k_lloyd(LloydAr
                 const float dlt = __fsub_rn(s_cn[j * LP + c], s_c[j * LP + c]);
                 mv = __fadd_rn(mv, __fmul_rn(dlt, dlt));
             }
-            atomicMax(&s_pmax, __float_as_uint(sqrtf(mv) * (1.0f + PRUNE_EPS)));
+            s_mv[j] = sqrtf(mv) * (1.0f + PRUNE_EPS);
+            atomicMax(&s_pmax, __float_as_uint(s_mv[j]));
             if (b == 0 && s_S[(size_t)j * (LP + 1) + LP] == 0) atomicAdd(&a.st->empty_events, 1);
         }
         // the accumulator of iteration it+2 was last read after the previous barrier: clear it
@@ -575,12 +637,8 @@ __global__ void k_merge_status(const int* __restrict__ call_status, int* __restr
     if (*call_status) atomicOr(dev_status, *call_status);
 }
 
-// k_lloyd's dynamic shared memory: centroids (16-byte aligned), ntab private tables, half the
-// separation of each centroid (k floats, padded to 8 bytes), the running totals k (LP + 1).
 static size_t lloyd_smem_bytes(int k, int LP, int ntab) {
-    const size_t rowlen = (size_t)k * (LP + 1);
-    return (((size_t)k * LP * 4 + 15) & ~(size_t)15) + (size_t)ntab * rowlen * 8 + (((size_t)k + 1) / 2) * 8 +
-           rowlen * 8;
+    return lloyd_queue_offset(k, LP, ntab) + (size_t)KM_WARPS * KM_QUEUE * 12;
 }
 
 template <typename K>
@@ -676,6 +734,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.amax = amax;
         la.ntab = ntab;
         la.lbound = ka.d2[0];          // the k-means++ D^2 buffers are free once seeding is done
+        la.ubound = ka.d2[1];
         la.prune = k <= 256 ? 1 : 0;
         la.st = st;
         la.bar = bar;
@@ -936,6 +995,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     la.amax = amax;
     la.ntab = ntab;
     la.lbound = ka.d2[0];
+    la.ubound = ka.d2[1];
     la.prune = k <= 256 ? 1 : 0;
     la.st = st;
     la.bar = bar;
