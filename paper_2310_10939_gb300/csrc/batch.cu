@@ -297,34 +297,42 @@ extern "C" fsc_status fsc_batch_create(const fsc_batch_desc* d, void* stream, fs
         struct Launch {
             const void* kern;
             long long grid;
+            size_t smem;
             BatchArgs args;
         };
         std::vector<Launch> launches;
         for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess && rc == FSC_OK; ++gi) {
             const BatchGroup& grp = b->groups[gi];
-            Launch L{};
-            L.kern = d->store == FSC_F32 ? batch_kernel_f32(grp.LP, d->w != nullptr)
-                                         : batch_kernel_bf16(grp.LP, d->w != nullptr);
-            const int per_sm = kernel_occupancy(L.kern, KM_THREADS, smem);
-            if (per_sm < 1) { rc = FSC_ERR_INVALID_ARG; break; }
-            L.grid = (long long)per_sm * device_props().num_sms;
-            if (L.grid > grp.count) L.grid = grp.count;
-            L.args = a;
-            L.args.graphs = b->d_graphs + grp.first;
-            L.args.num_graphs = grp.count;
-            L.args.queue = b->d_queue + gi;
-            launches.push_back(L);
+            // the group's embedding kernel, then its k-means kernel, each with its own queue counter
+            for (int part = 0; part < 2; ++part) {
+                Launch L{};
+                if (part == 0)
+                    L.kern = d->store == FSC_F32 ? batch_kernel_f32(grp.LP, d->w != nullptr)
+                                                 : batch_kernel_bf16(grp.LP, d->w != nullptr);
+                else
+                    L.kern = batch_kmeans_kernel(grp.LP);
+                L.smem = part == 0 ? 0 : smem;
+                const int per_sm = kernel_occupancy(L.kern, KM_THREADS, L.smem);
+                if (per_sm < 1) { rc = FSC_ERR_INVALID_ARG; break; }
+                L.grid = (long long)per_sm * device_props().num_sms;
+                if (L.grid > grp.count) L.grid = grp.count;
+                L.args = a;
+                L.args.graphs = b->d_graphs + grp.first;
+                L.args.num_graphs = grp.count;
+                L.args.queue = b->d_queue + 2 * gi + part;
+                launches.push_back(L);
+            }
         }
         if (e != cudaSuccess || rc != FSC_OK) break;
         cudaStream_t cs = nullptr;
         if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaMemsetAsync(b->d_queue, 0, 4 * sizeof(int), cs);
+            cudaMemsetAsync(b->d_queue, 0, 8 * sizeof(int), cs);
             cudaMemsetAsync(b->stats, 0, sizeof(KmDevStats) * G, cs);
             for (Launch& L : launches) {
                 void* args[] = {&L.args};
-                cudaLaunchKernel(L.kern, dim3((unsigned)L.grid), dim3(KM_THREADS), args, smem, cs);
+                cudaLaunchKernel(L.kern, dim3((unsigned)L.grid), dim3(KM_THREADS), args, L.smem, cs);
             }
             e = cudaStreamEndCapture(cs, &b->graph);
         }

@@ -158,7 +158,9 @@ __device__ void power_block(const BatchGraph& g, const BatchArgs& a, TS* zA, TS*
                             int* s_E) {
     constexpr int U = G <= 8 ? 4 : 2;
     constexpr int RPW = 32 / G;
-    constexpr int R = 2;   // rows in flight per lane group
+    // rows in flight per lane group (the 64-register budget of two CTAs per SM holds two rows of
+    // up to 4 columns)
+    constexpr int R = LP <= 4 ? 2 : 1;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, sub = lane % G, grp = lane / G;
     const int64_t* rp = a.row_ptr + g.v0;
     const float* invdeg = a.invdeg + g.v0;
@@ -474,8 +476,10 @@ __device__ void lloyd_block(const float* X, int n, int l, int k, int max_iter, c
     __syncthreads();
 }
 
+// Steps 1-2 of Algorithm 2 for one graph: the start block and the t power steps; the last one
+// writes the float32 embedding.
 template <int LP, typename TS, bool W>
-__device__ void run_graph(const BatchArgs& a, const BatchGraph& g, unsigned char* smem) {
+__device__ void embed_graph(const BatchArgs& a, const BatchGraph& g) {
     __shared__ float s_cm[8];
     __shared__ int s_E[8];
     const int tid = threadIdx.x;
@@ -501,7 +505,13 @@ __device__ void run_graph(const BatchArgs& a, const BatchGraph& g, unsigned char
         }
     }
     __syncthreads();
-    // 3. k-means++ and Lloyd on the embedding rows
+}
+
+// Step 3 for one graph: k-means++ and Lloyd on the embedding rows.
+template <int LP>
+__device__ void kmeans_graph(const BatchArgs& a, const BatchGraph& g, unsigned char* smem) {
+    const int tid = threadIdx.x;
+    const float* emb = a.earena + g.eoff;
     const float A = block_absmax<LP>(emb, g.n, g.l);
     const Scales sc = scales_for(A, g.n, g.l);
     float* s_c = reinterpret_cast<float*>(smem);
@@ -519,8 +529,25 @@ __device__ void run_graph(const BatchArgs& a, const BatchGraph& g, unsigned char
     __syncthreads();
 }
 
+// The two persistent kernels of a row-width group, run one after the other: each CTA pops a
+// graph from the group's queue counter and runs that graph's part with block barriers only, so
+// no CTA ever waits on another.  The power steps are latency-bound gathers, so their kernel
+// runs two CTAs per SM (64 registers); k-means needs ~120 registers and runs one.
 template <int LP, typename TS, bool W>
-__global__ void __launch_bounds__(KM_THREADS, 1) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(KM_THREADS, 2) k_batch_embed(BatchArgs a) {
+    __shared__ int s_q;
+    for (;;) {
+        if (threadIdx.x == 0) s_q = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int q = s_q;
+        __syncthreads();
+        if (q >= a.num_graphs) break;
+        embed_graph<LP, TS, W>(a, a.graphs[q]);
+    }
+}
+
+template <int LP>
+__global__ void __launch_bounds__(KM_THREADS, 1) k_batch_kmeans(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char bsmem[];
     __shared__ int s_q;
     for (;;) {
@@ -529,13 +556,14 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_batch(BatchArgs a) {
         const int q = s_q;
         __syncthreads();
         if (q >= a.num_graphs) break;
-        const BatchGraph g = a.graphs[q];
-        run_graph<LP, TS, W>(a, g, bsmem);
+        kmeans_graph<LP>(a, a.graphs[q], bsmem);
     }
 }
 
-// Kernel entry points of one storage type (batch_k_f32.cu, batch_k_bf16.cu).
+// Kernel entry points: the embedding kernels of one storage type (batch_k_f32.cu,
+// batch_k_bf16.cu) and the k-means kernels (batch_k_f32.cu).
 const void* batch_kernel_f32(int LP, bool weighted);
 const void* batch_kernel_bf16(int LP, bool weighted);
+const void* batch_kmeans_kernel(int LP);
 
 }  // namespace fsc

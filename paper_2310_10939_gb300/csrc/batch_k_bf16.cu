@@ -5,10 +5,10 @@ namespace fsc {
 
 const void* batch_kernel_bf16(int LP, bool weighted) {
     switch (LP) {
-        case 1: return weighted ? (const void*)k_batch<1, __nv_bfloat16, true> : (const void*)k_batch<1, __nv_bfloat16, false>;
-        case 2: return weighted ? (const void*)k_batch<2, __nv_bfloat16, true> : (const void*)k_batch<2, __nv_bfloat16, false>;
-        case 4: return weighted ? (const void*)k_batch<4, __nv_bfloat16, true> : (const void*)k_batch<4, __nv_bfloat16, false>;
-        default: return weighted ? (const void*)k_batch<8, __nv_bfloat16, true> : (const void*)k_batch<8, __nv_bfloat16, false>;
+        case 1: return weighted ? (const void*)k_batch_embed<1, __nv_bfloat16, true> : (const void*)k_batch_embed<1, __nv_bfloat16, false>;
+        case 2: return weighted ? (const void*)k_batch_embed<2, __nv_bfloat16, true> : (const void*)k_batch_embed<2, __nv_bfloat16, false>;
+        case 4: return weighted ? (const void*)k_batch_embed<4, __nv_bfloat16, true> : (const void*)k_batch_embed<4, __nv_bfloat16, false>;
+        default: return weighted ? (const void*)k_batch_embed<8, __nv_bfloat16, true> : (const void*)k_batch_embed<8, __nv_bfloat16, false>;
     }
 }
 
