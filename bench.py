@@ -443,7 +443,9 @@ def batch_arm(args, w):
         "speedup_vs_per_graph": round(per_graph_s / (ms * 1e-3), 2),
         "mean_lloyd_iterations": round(float(np.mean([s_["iterations"] for s_ in stats])), 2),
         "generate_s": round(gen_s, 2), "plan_s": round(plan_s, 2),
-        "gpu_launches": args.steps,
+        # per step: an embedding and a k-means kernel for each row width l_pad present
+        "gpu_launches": args.steps * 2 * len({fsc.pad_l(fsc.default_params(int(voff[g + 1] - voff[g]), int(gb.k[g]))[0])
+                                              for g in range(gb.num_graphs)}),
         "clocks": clk,
     }
     return out

@@ -1,8 +1,10 @@
 // k-means++ seeding and Lloyd iterations on the embedding rows (Sec. 2.2, last step of Algorithm 2).
 //
-// Both phases run as one cooperative (co-resident) persistent launch each.  Blocks own
-// contiguous chunks of points; cross-block steps are separated by a bounded grid barrier
-// (grid_sync), after which every block reads the other blocks' partial results through L2.
+// Both phases run as one cooperative (co-resident) persistent launch each.  Tiles of KM_TILE
+// points are dealt round-robin over the blocks; cross-block steps are separated by a bounded
+// grid barrier (grid_sync), after which every block reads the other blocks' partial results
+// through L2.  Lloyd keeps the exact cluster sums as running totals that only points changing
+// cluster update, and skips points by Hamerly's bounds (see k_lloyd).
 //
 // Decisions follow fixed rules that a float64 CPU restatement reproduces:
 //  * squared distances: float32, columns in order, no fused multiply-add;
@@ -38,7 +40,6 @@ struct KppArgs {
     unsigned long long seed;
     float* d2[2];
     long long* ttot[3];  // per tile: exact D^2 total (warp atomics), three in rotation
-    int max_tiles;
     long long chunk;     // points per block, a multiple of KM_PPT
     unsigned* amax;      // max |x| (float bits), output for the Lloyd launch
     int* near;           // per point: index (selection order) of its nearest chosen centre
@@ -294,7 +295,6 @@ struct LloydArgs {
     unsigned long long* tot;    // 3 accumulators of k*(LP+1) exact sums (coordinates, count), zeroed
     unsigned long long* cnt3;   // 3 x (inertia sum, changed count, 2 unused), then the final inertia; zeroed
     const unsigned* amax;
-    long long chunk;            // points per block (a multiple of KM_PPT)
     int ntab;
     float* lbound;       // per point: lower bound on the distance to every other centroid (pruning)
     float* ubound;       // per point: upper bound on the distance to its own centroid (pruning)
@@ -705,7 +705,6 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         ka.d2[0] = reinterpret_cast<float*>(ws + o_d2);
         ka.d2[1] = reinterpret_cast<float*>(ws + o_d2 + up((size_t)n * 4));
         for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(ws + o_tt + q * up((size_t)ntiles * 8));
-        ka.max_tiles = (int)ntiles;
         if ((e = cudaMemsetAsync(ws + o_tt, 0, 3 * up((size_t)ntiles * 8), s)) != cudaSuccess) break;
         ka.chunk = chunk;
         ka.amax = amax;
@@ -730,7 +729,6 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.c64 = reinterpret_cast<double*>(ws + o_c64);
         la.tot = reinterpret_cast<unsigned long long*>(ws + o_acc);
         la.cnt3 = la.tot + (size_t)3 * k * (LP + 1);
-        la.chunk = chunk;
         la.amax = amax;
         la.ntab = ntab;
         la.lbound = ka.d2[0];          // the k-means++ D^2 buffers are free once seeding is done
@@ -966,7 +964,6 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     ka.d2[0] = reinterpret_cast<float*>(ws + o_d2);
     ka.d2[1] = reinterpret_cast<float*>(ws + o_d2 + up((size_t)n * 4));
     for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(ws + o_tt + q * up((size_t)ntiles * 8));
-    ka.max_tiles = (int)ntiles;
     FSC_CUDA(cudaMemsetAsync(ws + o_tt, 0, 3 * up((size_t)ntiles * 8), s));
     ka.chunk = chunk;
     ka.amax = amax;
@@ -991,7 +988,6 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     la.c64 = reinterpret_cast<double*>(ws + o_c64);
     la.tot = reinterpret_cast<unsigned long long*>(ws + o_acc);
     la.cnt3 = la.tot + (size_t)3 * k * (LP + 1);
-    la.chunk = chunk;
     la.amax = amax;
     la.ntab = ntab;
     la.lbound = ka.d2[0];
