@@ -296,7 +296,8 @@ fsc_status fsc_autotune(const fsc_graph* g, int l, fsc_dtype store, int* best_th
  * (or l[g] = 0, t[g] < 0) take fsc_default_params mode 0.  fsc_batch_create validates the
  * union, computes degrees, assigns lanes per row (autotuned with FSC_BATCH_AUTOTUNE), orders
  * the graphs largest first, allocates the per-graph workspace and captures the work (a queue
- * reset and one persistent kernel in which one CTA runs one whole graph) into a CUDA graph.
+ * reset and, per row width, two persistent kernels in which one CTA runs one graph's embedding,
+ * then one graph's k-means) into a CUDA graph.
  * fsc_batch_run replays that graph on `stream` (asynchronous); labels[v] receives the local
  * cluster id (0..k_g-1) of global vertex v.  Per graph the result equals fsc_cluster with the
  * same parameters and lanes per row.  The plan borrows row_ptr, col_idx, w and labels.

@@ -1,14 +1,16 @@
-// Batched Algorithm 2: thousands of graphs of uneven size in one persistent launch.
+// Batched Algorithm 2: thousands of graphs of uneven size in a few persistent launches.
 //
 // The batch is the disjoint union of its graphs, given as one CSR with global vertex ids.
-// A persistent kernel takes graphs from an atomic work queue, largest first (longest
-// processing time order), and one 512-thread CTA runs a whole graph: Gaussian start block,
-// t power iterations separated by block barriers, then block-local k-means++ and Lloyd.  CTAs
-// never wait on each other, so the launch has no inter-CTA spin wait at all.  Each graph uses
-// the same per-row power step (power_row) and the same exact fixed-point k-means rules as the
-// single-graph entry points, so its labels equal those of fsc_cluster with the same lanes per
-// row.  The launch sequence (queue reset, stats reset, kernel) is captured once into a CUDA
-// graph and replayed by fsc_batch_run.
+// Graphs are grouped by row width l_pad; per group two persistent kernels run one after the
+// other, each taking graphs from its own atomic work queue, largest first (longest processing
+// time order), with one 512-thread CTA per graph: k_batch_embed (Gaussian start block, t power
+// iterations separated by block barriers; two CTAs per SM) and k_batch_kmeans (block-local
+// k-means++ and Lloyd; one CTA per SM).  CTAs never wait on each other, so no launch has an
+// inter-CTA spin wait at all.  Each graph uses the same per-row power step arithmetic
+// (row_gather) and the same exact fixed-point k-means rules as the single-graph entry points,
+// so its labels equal those of fsc_cluster with the same lanes per row.  The launch sequence
+// (queue reset, stats reset, the kernels) is captured once into a CUDA graph and replayed by
+// fsc_batch_run.
 #include <algorithm>
 #include <mutex>
 #include <new>
@@ -67,7 +69,7 @@ struct fsc_batch {
     KmDevStats* stats = nullptr;
     int32_t* labels = nullptr;
     std::vector<BatchGraph> h_graphs;    // in queue order, grouped by row width
-    std::vector<BatchGroup> groups;      // one persistent launch each
+    std::vector<BatchGroup> groups;      // two persistent launches each (embedding, k-means)
     std::vector<long long> seed_off;     // by graph id
     std::vector<long long> cent_off;     // by graph id
     std::vector<int> k_of;
@@ -273,7 +275,7 @@ extern "C" fsc_status fsc_batch_create(const fsc_batch_desc* d, void* stream, fs
         b->cents_total = coff;
         if ((e = cudaMalloc(&b->stats, sizeof(KmDevStats) * G)) != cudaSuccess) break;
 
-        // capture queue reset + stats reset + the persistent launch into a CUDA graph
+        // capture queue reset + stats reset + the persistent launches into a CUDA graph
         BatchArgs a{};
         a.graphs = b->d_graphs;
         a.num_graphs = G;

@@ -1,6 +1,6 @@
-// Device side of the batched mode: per-graph pieces of Algorithm 2 run by one CTA, and the
-// persistent kernel, one instantiation per row width l_pad (graphs are grouped by it, so each
-// kernel's registers follow its own width instead of the widest one).
+// Device side of the batched mode: per-graph pieces of Algorithm 2 run by one CTA, and the two
+// persistent kernels (embedding, k-means), one instantiation per row width l_pad (graphs are
+// grouped by it, so each kernel's registers follow its own width instead of the widest one).
 #pragma once
 
 #include <math.h>
