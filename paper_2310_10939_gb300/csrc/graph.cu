@@ -178,70 +178,6 @@ __device__ __forceinline__ void degree_block_totals(int bad, unsigned iso, doubl
     }
 }
 
-// Weighted graphs: validation and degrees, kDegLanes lanes per row.  The lanes of a row read its
-// entries side by side (coalesced), each keeps a float64 partial sum, and the partials meet in a
-// shuffle tree.  D^-1/2 and 1/d are formed in float32 from the float64 degree (correctly rounded
-// sqrt and division, within 1-2 ulp of the exact values).
-constexpr int kDegLanes = 8;
-
-__global__ void __launch_bounds__(256) k_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
-                                                const int32_t* __restrict__ col, const float* __restrict__ w,
-                                                int check_sorted, double* __restrict__ deg,
-                                                float* __restrict__ dinv, float* __restrict__ invdeg,
-                                                unsigned long long* __restrict__ n_iso, double* __restrict__ vol,
-                                                int* __restrict__ status, double* __restrict__ sumsq,
-                                                unsigned long long* __restrict__ dmax_bits) {
-    constexpr int G = kDegLanes, RPW = 32 / G;
-    const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
-    int bad = 0;
-    unsigned iso = 0;
-    double vsum = 0.0, vsq = 0.0, vmax = 0.0;
-    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {   // warp-uniform trip count
-        const int64_t i = base + grp;
-        const bool active = i < n;
-        int64_t s = 0, e = 0;
-        if (active) {
-            s = rp[i];
-            e = rp[i + 1];
-            if (s < 0 || e < s || e > nnz) {
-                bad |= ST_BAD_ROWPTR;
-                s = e = 0;
-            }
-        }
-        double d = 0.0;
-        for (int64_t p = s + sub; p < e; p += G) {
-            const int j = col[p];
-            if (j < 0 || (int64_t)j >= n) { bad |= ST_INDEX_RANGE; continue; }
-            if ((int64_t)j == i) { bad |= ST_SELF_LOOP; continue; }
-            if (check_sorted && p > s && col[p - 1] >= j) bad |= ST_UNSORTED;
-            const float wv = w[p];
-            if (!(wv >= 0.0f) || isinf(wv)) { bad |= ST_BAD_WEIGHT; continue; }
-            d += (double)wv;
-        }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-        if (active && sub == 0) {
-            vsum += d;
-            deg[i] = d;
-            vsq += d * d;
-            vmax = fmax(vmax, d);
-            if (d > 0.0) {
-                const float df = (float)d;
-                dinv[i] = 1.0f / sqrtf(df);
-                invdeg[i] = 1.0f / df;
-            } else {
-                dinv[i] = 0.0f;
-                invdeg[i] = 0.0f;
-                ++iso;
-            }
-        }
-    }
-    degree_block_totals(bad, iso, vsum, vsq, vmax, n_iso, vol, status, sumsq, dmax_bits);
-}
-
 // Unit weights: d(v) is the row length, so the degrees come from row_ptr alone and col is read
 // only to validate it.  A block takes a tile of `rows` consecutive rows (dynamic shared memory
 // holds the tile's rows + 1 row_ptr values): one thread per row writes the degrees (coalesced),
@@ -369,6 +305,103 @@ __global__ void __launch_bounds__(256) k_degree_unit(int64_t n, int64_t nnz, con
                         sumsq, dmax_bits);
 }
 
+// Weighted graphs: the same tiles as k_degree_unit.  The flat scan over the tile's entries
+// validates col and w and stages the weights in shared memory (coalesced loads, kDegUnroll in
+// flight per thread); then one thread per row sums its row's weights in float64 in entry order
+// (deterministic; the same order as a sequential sum).  A tile with more than `cap` entries (a
+// few very long rows) sums from global memory instead.
+template <int U>
+__global__ void __launch_bounds__(256) k_degree_weighted(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col, const float* __restrict__ w,
+                                                         int rows, int cap, int check_sorted, double* __restrict__ deg,
+                                                         float* __restrict__ dinv, float* __restrict__ invdeg,
+                                                         unsigned long long* __restrict__ n_iso,
+                                                         double* __restrict__ vol, int* __restrict__ status,
+                                                         double* __restrict__ sumsq,
+                                                         unsigned long long* __restrict__ dmax_bits) {
+    extern __shared__ long long s_rpw[];   // rows + 1 row_ptr values, then cap weights
+    long long* s_rp = s_rpw;
+    float* s_w = reinterpret_cast<float*>(s_rpw + rows + 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
+    int bad = 0;
+    unsigned iso = 0;
+    double vsum = 0.0, vsq = 0.0, vmax = 0.0;
+    const int64_t ntiles = (n + rows - 1) / rows;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * rows;
+        const int nr = (int)(n - r0 < rows ? n - r0 : rows);
+        for (int q = threadIdx.x; q <= nr; q += blockDim.x) s_rp[q] = rp[r0 + q];
+        __syncthreads();
+        int tile_bad = 0;
+        for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+            const long long s = s_rp[q], e = s_rp[q + 1];
+            if (s < 0 || e < s || e > nnz) tile_bad = 1;
+        }
+        if (__syncthreads_or(tile_bad)) {
+            bad |= ST_BAD_ROWPTR;
+            continue;
+        }
+        const long long P0 = s_rp[0], P1 = s_rp[nr];   // 0 <= P0 <= P1 <= nnz, rows non-decreasing
+        const bool staged = P1 - P0 <= (long long)cap;
+        const int r0i = (int)r0;
+        for (long long p0 = P0 + threadIdx.x; p0 < P1; p0 += (long long)U * blockDim.x) {
+            int jv[U];
+            float wv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long p = p0 + (long long)u * blockDim.x;
+                jv[u] = p < P1 ? __ldg(col + p) : 0;
+                wv[u] = p < P1 ? __ldg(w + p) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long p = p0 + (long long)u * blockDim.x;
+                if (p >= P1) break;
+                const int j = jv[u];
+                const int jl = j - r0i;
+                if ((unsigned)j >= (unsigned)n) bad |= ST_INDEX_RANGE;
+                else if ((unsigned)jl < (unsigned)nr && s_rp[jl] <= p && p < s_rp[jl + 1]) bad |= ST_SELF_LOOP;
+                if (!(wv[u] >= 0.0f) || isinf(wv[u])) bad |= ST_BAD_WEIGHT;
+                if (staged) s_w[p - P0] = wv[u];
+                if (check_sorted && p > P0 && __ldg(col + p - 1) >= j) {
+                    int lo = 0, hi = nr - 1;   // last row whose start is <= p
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_rp[mid] <= p) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    if (p > s_rp[lo]) bad |= ST_UNSORTED;
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+            const long long s = s_rp[q], e = s_rp[q + 1];
+            double d = 0.0;
+            if (staged)
+                for (long long p = s; p < e; ++p) d += (double)s_w[p - P0];
+            else
+                for (long long p = s; p < e; ++p) d += (double)__ldg(w + p);
+            const int64_t i = r0 + q;
+            deg[i] = d;
+            vsum += d;
+            vsq += d * d;
+            vmax = fmax(vmax, d);
+            if (d > 0.0) {
+                const float df = (float)d;
+                dinv[i] = 1.0f / sqrtf(df);
+                invdeg[i] = 1.0f / df;
+            } else {
+                dinv[i] = 0.0f;
+                invdeg[i] = 0.0f;
+                ++iso;
+            }
+        }
+        __syncthreads();
+    }
+    degree_block_totals(bad, iso, vsum, vsq, vmax, n_iso, vol, status, sumsq, dmax_bits);
+}
+
 // One warp per row: each entry (i, j, w) must have its mirror (j, i, w) (binary search, sorted rows).
 __global__ void __launch_bounds__(256) k_symmetry(int64_t n, const int64_t* __restrict__ rp,
                                                   const int32_t* __restrict__ col, const float* __restrict__ w,
@@ -464,15 +497,25 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
                                                                g->deg, g->dinv, g->invdeg, &hdr->niso, &hdr->vol,
                                                                &hdr->status, &hdr->sumsq, &hdr->dmax_bits);
         } else {
-            constexpr int rows_per_block = threads / 32 * (32 / kDegLanes);
-            const int64_t want = (n + rows_per_block - 1) / rows_per_block;
-            // enough warps that each walks only a few rows: every row is a dependent row_ptr -> col
-            // load chain, so the kernel is latency-bound with fewer warps in flight
-            const int64_t cap = (int64_t)device_props().num_sms * 32;
-            const int blocks = (int)(want < cap ? want : cap);
-            k_degree<<<blocks, threads, 0, s>>>(n, nnz, row_ptr, col_idx, w, check_sorted, g->deg, g->dinv,
-                                                g->invdeg, &hdr->niso, &hdr->vol, &hdr->status, &hdr->sumsq,
-                                                &hdr->dmax_bits);
+            // tiles sized so that the staged weights of an average tile fill at most half of the
+            // 32 KB weight buffer, and the grid is about one wave of resident blocks
+            constexpr int kCap = 8192;
+            constexpr int64_t kMaxRows = 2048, kMinRows = 32;
+            const void* fn = (const void*)k_degree_weighted<4>;
+            int per_sm = kernel_occupancy(fn, threads, (size_t)(kMaxRows + 1) * 8 + (size_t)kCap * 4);
+            if (per_sm < 1) per_sm = 1;
+            const int64_t slots = (int64_t)device_props().num_sms * per_sm;
+            const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+            int64_t rows = ((n + slots - 1) / slots + 31) / 32 * 32;
+            const int64_t by_cap = avg > 0.0 ? (int64_t)((kCap / 2) / avg) / 32 * 32 : kMaxRows;
+            if (rows > by_cap) rows = by_cap;
+            rows = rows < kMinRows ? kMinRows : (rows > kMaxRows ? kMaxRows : rows);
+            const int64_t ntiles = (n + rows - 1) / rows;
+            const int blocks = (int)(ntiles < slots ? ntiles : slots);
+            const size_t smem = (size_t)(rows + 1) * 8 + (size_t)kCap * 4;
+            k_degree_weighted<4><<<blocks, threads, smem, s>>>(n, nnz, row_ptr, col_idx, w, (int)rows, kCap, check_sorted,
+                                                               g->deg, g->dinv, g->invdeg, &hdr->niso, &hdr->vol,
+                                                               &hdr->status, &hdr->sumsq, &hdr->dmax_bits);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         Header h{};
