@@ -98,6 +98,16 @@ def test_kmeans_matches_oracle_on_mixtures(torch, n, k, l, lp):
     _compare(torch, X, l, k, seed=31 + k)
 
 
+@pytest.mark.parametrize("seed", [3, 4])
+def test_kmeans_several_tiles_per_block(torch, seed):
+    """650,000 points: some blocks take three tiles of 2048 points, so Lloyd's per-warp queues fill
+    and are worked in the middle of a pass (in the first iteration every point is queued).  With
+    max_iter = 12 the run converges (seed 3) or stops with labels still changing (seed 4, where
+    the inertia is that of the last assignment, taken with the centroids it used)."""
+    X, _ = _mixture(650_000, 12, 4, seed=650_000 + seed, spread=0.3)
+    _compare(torch, X, 4, 12, seed=43 + seed, max_iter=12)
+
+
 @pytest.mark.parametrize("seed", range(1, 6))
 def test_kmeans_on_oracle_embedding_of_sbm(torch, seed):
     g = W.sbm([250] * 4, 0.1, 0.002, seed)
