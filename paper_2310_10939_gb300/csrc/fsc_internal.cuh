@@ -84,13 +84,6 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, float (&v)[LP]
     for (int c = 0; c < LP; ++c) v[c] = to_f32(e[c]);
 }
 
-// Same as load_row but through L2 only (data written by other blocks of the same launch).
-template <int LP>
-__device__ __forceinline__ void load_row_cg(const float* p, float (&v)[LP]) {
-#pragma unroll
-    for (int c = 0; c < LP; ++c) v[c] = __ldcg(p + c);
-}
-
 template <int LP, typename T>
 __device__ __forceinline__ void store_row(T* __restrict__ p, const float (&v)[LP]) {
     constexpr int BYTES = LP * (int)sizeof(T);
