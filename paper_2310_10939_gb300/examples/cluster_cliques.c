@@ -1,8 +1,11 @@
 /*
  * Algorithm 2 end to end through the C ABI alone: k disjoint cliques of s vertices, each of
- * which must come out as one cluster (the components of a disconnected graph are the top
- * eigenspace of M, Sec. 2, so the embedding rows of a clique coincide and k-means++ picks one
- * centre per clique).
+ * which must come out as one cluster.  The component indicators of a disconnected graph span
+ * the eigenvalue-1 eigenspace of M (Sec. 2); on K_s every other eigenvalue of M is
+ * (1 - 1/(s-1))/2, so after t = 30 power iterations the embedding rows of a clique coincide to
+ * float32 precision.  The points are then k distinct point masses, and k-means++ puts one centre
+ * on each (a mass that already holds a centre has D^2 = 0).  With the default t = ceil(log2 n)
+ * = 9 the rows still differ by about 2e-3 relative, and a few seeds land in a merged optimum.
  *
  * Build from the repository root after the library (python -m paper_2310_10939_gb300.build):
  *   gcc -O2 -Iinclude -I/usr/local/cuda/include paper_2310_10939_gb300/examples/cluster_cliques.c \
@@ -61,7 +64,8 @@ int main(void) {
     fsc_graph* g = NULL;
     FK(fsc_create_graph(n, nnz, d_row_ptr, d_col, NULL, FSC_VALIDATE_SYMMETRY, NULL, &g));
     int l = 0, t = 0;
-    FK(fsc_default_params(n, k, 0, &l, &t));
+    FK(fsc_default_params(n, k, 0, &l, &t));   /* l = ceil(log2 k) */
+    t = 30;
     fsc_kmeans_stats st;
     FK(fsc_cluster(g, k, l, t, 7, FSC_F32, 100, d_labels, &st, NULL, NULL));
     CK(cudaMemcpy(labels, d_labels, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost));
