@@ -159,6 +159,15 @@ def read_traffic(kernel_tag):
     return float(vals["traffic_per_launch_bytes"])
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of a list of floats over all ranks of the default process group
+    (the timing rule for N > 1: the slowest rank's time is the job's)."""
+    import torch
+    x = torch.tensor(list(values), dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in x.cpu()]
+
+
 def gpu_arm(args, w, rank, world, local_rank):
     import torch
     import paper_2310_10939_gb300 as fsc
@@ -216,9 +225,7 @@ def gpu_arm(args, w, rank, world, local_rank):
     ms = float(np.mean(step_ms))
     spmm_launch_ms = float(np.mean(spmm_ms)) / t
     if world > 1:
-        x = torch.tensor([ms, spmm_launch_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        ms, spmm_launch_ms = float(x[0]), float(x[1])
+        ms, spmm_launch_ms = max_over_ranks([ms, spmm_launch_ms], dev)
     ari = pm.ari(labels.cpu().numpy(), g.labels)
 
     # end to end through the public API with host buffers: H2D of the CSR, create, cluster, D2H of labels
@@ -247,9 +254,7 @@ def gpu_arm(args, w, rank, world, local_rank):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = float(np.mean(e2e_ms))
     if world > 1:
-        x = torch.tensor([e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        e2e = float(x[0])
+        e2e, = max_over_ranks([e2e], dev)
 
     variants = time_variants(args, g, rp, col, wt, k, l, t, seed, flush) if not args.no_variants else None
 
