@@ -189,7 +189,8 @@ fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int k, uint64_
  * device memory once they are running, e.g. code inside a runtime that hands out a fixed
  * memory budget up front, or a latency-critical loop where an allocation could block or
  * fail.  Same arguments, same kernels and same results as fsc_kmeans; the scratch space
- * (about 8 bytes per point plus per-block partial sums) lives in one fixed array of
+ * (12 bytes per point: two D^2 buffers, reused by Lloyd for its bounds, and each point's nearest
+ * chosen centre; plus per-tile sums and the centroids) lives in one fixed array of
  * FSC_KMEANS_STATIC_SCRATCH_BYTES compiled into the library, which every GPU that loads the
  * library keeps reserved until the process exits.
  *  - Problems whose scratch does not fit return FSC_ERR_TOO_LARGE (with 152 SMs this admits,
