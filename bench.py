@@ -1,23 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of fast spectral clustering (Algorithm 2) on one GB300 per rank.
 
-A step is one pass of the hot path over the resident CSR graph:
-fsc_create_graph (validation + degrees) followed by fsc_cluster (Gaussian start
-block, t fused power iterations, D^-1/2, k-means++ seeding, Lloyd to
-convergence).  Default workload: SBM with n = 2^20 vertices, 16 equal blocks,
-expected intra-/inter-block degree 20/2 (~11.5M undirected edges, unit
-weights), k = 16, l = 4, t = 20, float32 storage.
+A step is one pass of the hot path over the resident CSR graph: fsc_create_graph (validation +
+degrees) followed by the clustering call of the workload's path (start block, the sparse steps,
+k-means++ seeding, Lloyd to convergence).
 
-Prints one JSON line (rank 0).  `--impl reference` times the float64 CPU
-oracle on the same workload instead.  Under torchrun with N > 1 every rank
-runs its own replica (the method has no cross-GPU exchange for one graph in
-this library; see the design notes), value = max over ranks.
+Default workload: SBM with n = 2^22 vertices, 100 equal blocks, expected intra-/inter-block
+degree 36/4 (~84M undirected edges, unit weights), k = 100, l = 7.  The timed path is the learned
+degree-8 polynomial filter in place of M^t (basis stored in float16, float32 accumulation), the
+variants include the plain t = 22 power method in float32 it is compared against.
+
+Prints one JSON line (rank 0).  `--impl reference` times the float64 oracle (plain C + OpenMP on
+all host cores) on the same workload instead.  Under torchrun with N > 1 every rank runs its own
+replica (one graph does not shard in this library), value = max over ranks.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -30,18 +33,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "sbm_n2p20_k16": dict(kind="sbm", n=2 ** 20, k=16, deg_in=20.0, deg_out=2.0, l=4, t=20, store="f32", seed=7,
-                          desc="SBM n=2^20, 16 equal blocks, intra-degree 20, inter-degree 2, unit weights; "
-                               "k=16, l=4, t=20, float32"),
-    "knn_2e5_k10": dict(kind="knn", npts=200_000, dim=32, ncomp=10, knn=10, k=10, l=4, t=20, store="f32", seed=5,
-                        desc="10-NN graph of 200,000 points in R^32 from a 10-component Gaussian mixture; "
-                             "k=10, l=4, t=20, float32"),
-    "image_481x321_bf16": dict(kind="image", k=8, l=3, t=30, store="bf16", seed=3,
-                               desc="481x321 Voronoi image graph, radius 3; k=8, l=3, t=30, bfloat16 storage"),
-    "sbm_n2p22_k100": dict(kind="sbm_gpu", n=2 ** 22, k=100, deg_in=36.0, deg_out=4.0, l=7, t=22, store="f32", seed=19,
+    "sbm_n2p22_k100": dict(kind="sbm_gpu", n=2 ** 22, k=100, deg_in=36.0, deg_out=4.0, l=7, t=22, path="learned_f16",
+                           seed=19,
                            desc="SBM n=2^22, 100 equal blocks, intra-degree 36, inter-degree 4 (GPU generator), "
-                                "k=100, l=7; plain t=22 float32 (value) vs the learned degree-8 filter with bf16 "
-                                "iterates (variants)"),
+                                "k=100, l=7: learned degree-8 filter, float16 basis (value) vs plain t=22 power "
+                                "method in float32 and bfloat16 (variants)"),
+    "sbm_n2p20_k16": dict(kind="sbm", n=2 ** 20, k=16, deg_in=20.0, deg_out=2.0, l=4, t=20, path="plain_f32", seed=7,
+                          desc="SBM n=2^20, 16 equal blocks, intra-degree 20, inter-degree 2, unit weights; "
+                               "k=16, l=4, t=20, plain power method in float32"),
+    "knn_2e5_k10": dict(kind="knn", npts=200_000, dim=32, ncomp=10, knn=10, k=10, l=4, t=20, path="plain_f32",
+                        seed=5, desc="10-NN graph of 200,000 points in R^32 from a 10-component Gaussian mixture; "
+                                     "k=10, l=4, t=20, plain power method in float32"),
+    "image_481x321_bf16": dict(kind="image", k=8, l=3, t=30, path="plain_bf16", seed=3,
+                               desc="481x321 Voronoi image graph, radius 3; k=8, l=3, t=30, plain power method, "
+                                    "bfloat16 storage"),
     "sbm_batch_4096": dict(kind="batch", G=4096, n_range=(500, 50_000), k_range=(2, 20), deg_in=15.0, deg_out=1.5,
                            store="bf16", seed=13,
                            desc="4096 SBM graphs, n~U[500,50000], k~U[2,20], intra-degree 15, inter-degree 1.5, "
@@ -49,35 +54,48 @@ WORKLOADS = {
                                 "launch in a captured CUDA graph vs one fsc_cluster per graph"),
 }
 METRIC = "cluster ms & SpMM HBM GB/s (% peak) at matched ARI, learned/BF16 vs plain"
+UNIT = "ms per clustering (create_graph + cluster)"
+E2E_UNIT = "ms per clustering"
+DEFAULT_WORKLOAD = "sbm_n2p22_k100"
+PATH_DTYPE = {"learned_f16": "f16-store/f32-accumulate", "learned_f32": "f32", "learned_bf16": "bf16-store/f32-accumulate",
+              "plain_f32": "f32", "plain_bf16": "bf16-store/f32-accumulate"}
 
 
-def make_graph(w):
+def make_graph(w, device="cuda"):
+    """workloads.Graph (host CSR) of the workload; the 2^22-vertex SBM comes from the GPU generator."""
     import workloads as W
     if w["kind"] == "sbm":
         return W.sbm_by_degree(w["n"], w["k"], w["deg_in"], w["deg_out"], seed=w["seed"])
     if w["kind"] == "knn":
-        import torch
-        dev = "cuda" if torch.cuda.is_available() else "cpu"
-        return W.knn_mixture(w["npts"], w["dim"], w["ncomp"], w["knn"], seed=w["seed"], device=dev)
+        return W.knn_mixture(w["npts"], w["dim"], w["ncomp"], w["knn"], seed=w["seed"], device=device)
     if w["kind"] == "image":
         return W.image_grid(321, 481, 8, seed=w["seed"])
     if w["kind"] == "sbm_gpu":
         gb = W.sbm_batch_gpu(1, (w["n"], w["n"]), (w["k"], w["k"]), w["deg_in"], w["deg_out"], seed=w["seed"],
-                             with_weights=False)
+                             with_weights=False, device=device)
         return W.Graph(w["n"], gb.row_ptr.cpu().numpy(), gb.col.cpu().numpy(), None, gb.labels.cpu().numpy(),
                        "sbm_n2p22_k100")
     raise ValueError(w["kind"])
 
 
-def spmm_bytes_per_launch(g, l, store):
-    """Algorithmic bytes of one fused power step: CSR once, X once, Y once, 1/d once."""
-    import paper_2310_10939_gb300 as fsc
-    lp = fsc.pad_l(l)
-    s = 4 if store == "f32" else 2
-    b = 4 * g.nnz + 8 * (g.n + 1) + 4 * g.n + 2 * g.n * lp * s
-    if g.w is not None:
-        b += 4 * g.nnz
-    return b
+# ---- algorithmic bytes per launch of the sparse kernels -------------------------------------
+
+def csr_bytes(g):
+    """CSR once (col, weights when present, int64 row_ptr) and 1/d once."""
+    return 4 * g.nnz + (4 * g.nnz if g.w is not None else 0) + 8 * (g.n + 1) + 4 * g.n
+
+
+def power_step_bytes(g, lp, s):
+    """k_power_step: CSR + read the iterate once + write it once."""
+    return csr_bytes(g) + 2 * g.n * lp * s
+
+
+def cheb_step_bytes(g, lp, s):
+    """k_cheb_step, mean over the 8 launches of one filter: CSR each launch; iterate rows read once
+    (T_j) and written once (T_{j+1}); T_{j-1} read in launches 2..8; d(v) (float64) read in the four
+    launches that also form the moments."""
+    total = 8 * csr_bytes(g) + (2 + 7 * 3) * g.n * lp * s + 4 * 8 * g.n
+    return total / 8.0
 
 
 class ClockSampler:
@@ -137,23 +155,25 @@ def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    return 6800.0, "fallback 6.8 TB/s"
 
 
-def read_traffic(kernel_tag):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source has not changed since."""
-    import hashlib
-    src = os.path.join(ROOT, "paper_2310_10939_gb300", "csrc", "spmm.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    summ = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+def read_traffic(summary_name, sources):
+    """Per-launch DRAM bytes from a committed ncu summary, while the kernel sources it names still hash
+    to the value recorded in it; None otherwise."""
+    h = hashlib.sha256()
+    for src in sources:
+        h.update(open(os.path.join(ROOT, "paper_2310_10939_gb300", "csrc", src), "rb").read())
+    sha = h.hexdigest()[:16]
+    summ = os.path.join(ROOT, "profiles", f"{summary_name}.md")
     if not os.path.exists(summ):
         return None
     vals = {}
     for line in open(summ):
         if line.startswith("traffic_per_launch_bytes:") or line.startswith("kernel_source_sha:"):
-            k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
+            key, v = line.split(":", 1)
+            vals[key.strip()] = v.strip()
     if vals.get("kernel_source_sha") != sha or "traffic_per_launch_bytes" not in vals:
         return None
     return float(vals["traffic_per_launch_bytes"])
@@ -168,65 +188,104 @@ def max_over_ranks(values, device):
     return [float(v) for v in x.cpu()]
 
 
+# ---- the GPU arm -------------------------------------------------------------------------------
+
+class Runner:
+    """One clustering of the resident graph along a named path, through the C ABI."""
+
+    def __init__(self, fsc, rp, col, wt, k, l, t, params):
+        self.fsc, self.rp, self.col, self.wt = fsc, rp, col, wt
+        self.k, self.l, self.t, self.params = k, l, t, params
+
+    def run(self, path, seed, labels=None, events=None, mid=None, stream=None):
+        """Returns (labels, stats, sparse launches bracketed by `events`)."""
+        fsc = self.fsc
+        G = fsc.Graph(self.rp, self.col, self.wt)
+        if mid is not None:
+            mid.record(stream)
+        if path.startswith("learned"):
+            store = {"learned_f16": fsc.F16, "learned_f32": fsc.F32, "learned_bf16": fsc.BF16}[path]
+            lab, st = fsc.cluster_filtered(G, self.k, self.l, seed, self.params, store=store, labels=labels,
+                                           events=events)
+            launches = st["fallback_t"] if st["fallback"] else 8
+        else:
+            store = fsc.F32 if path == "plain_f32" else fsc.BF16
+            lab, st = fsc.cluster(G, self.k, self.l, self.t, seed, store=store, labels=labels, rescale=True,
+                                  events=events)
+            launches = self.t
+        G.close()
+        return lab, st, launches
+
+
+def timed_launch(fn, reps=10, warm=3):
+    """Mean device time (ms) of fn() on the current stream, CUDA events after warm-up."""
+    import torch
+    for _ in range(warm):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
 def gpu_arm(args, w, rank, world, local_rank):
     import torch
     import paper_2310_10939_gb300 as fsc
-    from paper_2310_10939_gb300 import metrics as pm
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    g = make_graph(w)
-    k, l, t, seed = w["k"], w["l"], w["t"], w["seed"]
-    store = fsc.BF16 if w["store"] == "bf16" else fsc.F32
+    g = make_graph(w, device=f"cuda:{local_rank}")
+    k, l, t, seed, path = w["k"], w["l"], w["t"], w["seed"], args.path or w["path"]
     rp = torch.as_tensor(g.row_ptr, device=dev)
     col = torch.as_tensor(g.col, device=dev)
     wt = None if g.w is None else torch.as_tensor(g.w, device=dev)
+    planted = torch.as_tensor(g.labels.astype(np.int32), device=dev)
+    kp = int(g.labels.max()) + 1
+    params = fsc.load_filter_params(device=dev) if os.path.exists(fsc.FILTER_WEIGHTS) else None
+    if path.startswith("learned") and params is None:
+        raise RuntimeError("the learned path needs the trained filter weights")
+    R = Runner(fsc, rp, col, wt, k, l, t, params)
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
     stream = torch.cuda.current_stream(dev)
 
-    def step(evs=None, mid=None):
-        G = fsc.Graph(rp, col, wt)
-        if mid is not None:
-            mid.record(stream)
-        _, st = fsc.cluster(G, k, l, t, seed, store=store, labels=labels, rescale=True, events=evs)
-        G.close()
-        return st
-
     for _ in range(args.warmup):
-        step()
+        R.run(path, seed, labels)
     torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+    starts, ends, mids = [ev() for _ in range(args.steps)], [ev() for _ in range(args.steps)], \
+        [ev() for _ in range(args.steps)]
+    brackets = [(ev(), ev()) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local_rank)
     clocks.start()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    stats = None
+    stats, nsparse = None, []
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
-        stats = step(sp[i], mids[i])
+        _, stats, nl = R.run(path, seed, labels, events=brackets[i], mid=mids[i], stream=stream)
         ends[i].record(stream)
+        nsparse.append(nl)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
     create_ms = float(np.mean([s.elapsed_time(m) for s, m in zip(starts, mids)]))
-    cluster_ms = float(np.mean([m.elapsed_time(e) for m, e in zip(mids, ends)]))
-    spmm_ms = [a.elapsed_time(b) for a, b in sp]
-    ms = float(np.mean(step_ms))
-    spmm_launch_ms = float(np.mean(spmm_ms)) / t
+    sparse_ms = float(np.mean([a.elapsed_time(b) for a, b in brackets]))
+    launch_ms = float(np.mean([a.elapsed_time(b) / n for (a, b), n in zip(brackets, nsparse)]))
     if world > 1:
-        ms, spmm_launch_ms = max_over_ranks([ms, spmm_launch_ms], dev)
-    ari = pm.ari(labels.cpu().numpy(), g.labels)
+        ms, launch_ms = max_over_ranks([ms, launch_ms], dev)
+    ari = fsc.partition_scores(labels, planted, k, kp)[0]
 
     # end to end through the public API with host buffers: H2D of the CSR, create, cluster, D2H of labels
     rp_h = torch.as_tensor(g.row_ptr).pin_memory()
@@ -235,6 +294,7 @@ def gpu_arm(args, w, rank, world, local_rank):
     lab_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
     rp_d, col_d = torch.empty_like(rp), torch.empty_like(col)
     w_d = None if wt is None else torch.empty_like(wt)
+    R_e2e = Runner(fsc, rp_d, col_d, w_d, k, l, t, params)
     h2d = rp_h.numel() * 8 + col_h.numel() * 4 + (0 if w_h is None else w_h.numel() * 4)
     e2e_ms = []
     for i in range(args.warmup + args.steps):
@@ -245,26 +305,56 @@ def gpu_arm(args, w, rank, world, local_rank):
         col_d.copy_(col_h, non_blocking=True)
         if w_d is not None:
             w_d.copy_(w_h, non_blocking=True)
-        G = fsc.Graph(rp_d, col_d, w_d)
-        lab_d, _ = fsc.cluster(G, k, l, t, seed, store=store, rescale=True)
+        lab_d, _, _ = R_e2e.run(path, seed)
         lab_h.copy_(lab_d, non_blocking=True)
         torch.cuda.synchronize()
-        G.close()
         if i >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = float(np.mean(e2e_ms))
     if world > 1:
         e2e, = max_over_ranks([e2e], dev)
+    del rp_d, col_d, w_d, R_e2e
 
-    variants = time_variants(args, g, rp, col, wt, k, l, t, seed, flush) if not args.no_variants else None
-
-    bytes_launch = spmm_bytes_per_launch(g, l, w["store"])
+    variants = None if args.no_variants else time_variants(R, g, planted, kp, seed, flush)
+    lp = fsc.pad_l(l)
     peak, peak_src = read_peaks()
-    achieved = bytes_launch / (spmm_launch_ms * 1e-3) / 1e9
+    floors = gather_floors(fsc, torch, rp, col, wt, l, dev)
+
+    def roofline(kernel, variant, bytes_launch, ms_launch, s_name):
+        achieved = bytes_launch / (ms_launch * 1e-3) / 1e9
+        fl = floors.get(s_name)
+        summary = f"{'cheb' if kernel == 'k_cheb_step' else 'spmm'}_{args.workload}_{s_name}"
+        srcs = ["spmm.cuh", "filter.cu"] if kernel == "k_cheb_step" else ["spmm.cuh"]
+        return {"kernel": kernel, "variant": variant, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": read_traffic(summary, srcs), "bytes_per_launch": int(bytes_launch),
+                "launch_ms": round(ms_launch, 5),
+                "gather_floor_ms": None if fl is None else round(fl, 5),
+                "frac_of_gather_floor": None if fl is None else round(fl / ms_launch, 4)}
+
+    value_store = {"learned_f16": "f16", "learned_f32": "f32", "learned_bf16": "bf16", "plain_f32": "f32",
+                   "plain_bf16": "bf16"}[path]
+    s_bytes = 4 if value_store == "f32" else 2
+    if path.startswith("learned") and not stats["fallback"]:
+        main_roof = roofline("k_cheb_step", path, cheb_step_bytes(g, lp, s_bytes), launch_ms, value_store)
+    else:
+        main_roof = roofline("k_power_step", path, power_step_bytes(g, lp, s_bytes), launch_ms, value_store)
+    others = []
+    for name, rec in (variants or {}).items():
+        if not isinstance(rec, dict) or "sparse_launch_ms" not in rec or name == path:
+            continue
+        st_name = name.split("_")[-1]
+        sb = 4 if st_name == "f32" else 2
+        if name.startswith("learned") and not rec.get("fallback"):
+            others.append(roofline("k_cheb_step", name, cheb_step_bytes(g, lp, sb), rec["sparse_launch_ms"], st_name))
+        elif name.startswith("plain") or (name.startswith("learned") and rec.get("fallback")):
+            others.append(roofline("k_power_step", name, power_step_bytes(g, lp, sb), rec["sparse_launch_ms"],
+                                   st_name))
+
     out = {
         "metric": METRIC,
         "value": round(ms, 4),
-        "unit": "ms per clustering (create_graph + cluster)",
+        "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -272,118 +362,241 @@ def gpu_arm(args, w, rank, world, local_rank):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if store == fsc.F32 else "bf16-store/f32-accumulate",
+        "dtype": PATH_DTYPE[path],
         "data": "synthetic (seeded generator)",
-        "config": {"workload": f"{args.workload}: {w['desc']}", "n": g.n, "nnz": g.nnz, "k": k, "l": l, "t": t,
+        "config": {"workload": f"{args.workload}: {w['desc']}", "path": path, "n": g.n, "nnz": g.nnz, "k": k, "l": l,
+                   "t": t if path.startswith("plain") else 8,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "512 MB buffer written between timed steps (flush)"},
-        "e2e": {"value": round(e2e, 4), "unit": "ms per clustering from pinned host CSR to host labels",
+        "e2e": {"value": round(e2e, 4), "unit": E2E_UNIT,
+                "region": "pinned host CSR -> device, create_graph, cluster, labels -> pinned host",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(g.n * 4)},
-        "roofline": {"kernel": "k_power_step (fused SpMM power iteration)", "bound": "hbm",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
-                     if peak_src == "measured" else "fallback 6.8 TB/s",
-                     "traffic": read_traffic("spmm_sbm_n2p20_l4_f32") if args.workload == "sbm_n2p20_k16" else None,
-                     "bytes_per_launch": int(bytes_launch), "launch_ms": round(spmm_launch_ms, 5)},
-        "breakdown_ms": {"create_graph": round(create_ms, 4), "cluster": round(cluster_ms, 4),
-                         "power_iterations": round(spmm_launch_ms * t, 4)},
+        "roofline": main_roof,
+        "rooflines_other": others,
+        "breakdown_ms": {"create_graph": round(create_ms, 4), "cluster": round(ms - create_ms, 4),
+                         "sparse_steps": round(sparse_ms, 4)},
         "ari_vs_planted": round(ari, 4),
         "lloyd_iterations": stats["iterations"] if stats else None,
-        "graphs_per_s": round(world * args.steps / (ms * args.steps * 1e-3), 3),
         "wall_s": round(wall, 3),
-        "gpu_launches": args.steps * (1 + 1 + t + 2),
+        "gpu_launches": args.steps * launches_per_step(path, stats, t),
         "clocks": clk,
         "variants": variants,
     }
+    if path.startswith("learned"):
+        out["filter"] = {"energy_ratio": round(stats["filter_energy_ratio"], 4),
+                         "threshold": round(stats["filter_threshold"], 4), "fallback": int(stats["fallback"])}
     return out, g
 
 
-def time_variants(args, g, rp, col, wt, k, l, t, seed, flush, steps=5):
-    """The same clustering with bf16 iterates, and with the learned degree-8 filter (float32 and
-    float16 basis): ms per clustering (create_graph + cluster), ARI against the planted labels,
-    and for the filter the energy guard's ratio and whether it fell back to the plain method."""
-    import torch
-    import paper_2310_10939_gb300 as fsc
-    from paper_2310_10939_gb300 import metrics as pm
+def launches_per_step(path, stats, t):
+    """Kernels of this library launched per step: degrees (1); plain: start block + t power steps;
+    learned: start block + 8 Chebyshev steps + coefficients + combine (+ start block and t power
+    steps on a fallback); k-means: k-means++ and Lloyd (2)."""
+    if path.startswith("learned"):
+        n = 1 + 1 + 8 + 1 + 1 + 2
+        if stats and stats.get("fallback"):
+            n += 1 + stats["fallback_t"]
+        return n
+    return 1 + 1 + t + 2
+
+
+def gather_floors(fsc, torch, rp, col, wt, l, dev):
+    """Mean duration (ms) of fsc_gather_floor on this graph for each storage type: the random-gather
+    floor of one sparse step at this row width."""
+    G = fsc.Graph(rp, col, wt)
+    lp = fsc.pad_l(l)
     out = {}
-    params = fsc.load_filter_params() if os.path.exists(fsc.FILTER_WEIGHTS) else None
+    for name, st, dt in (("f32", fsc.F32, torch.float32), ("bf16", fsc.BF16, torch.bfloat16),
+                         ("f16", fsc.F16, torch.float16)):
+        z = torch.randn((G.n, lp), device=dev).to(dt)
+        acc = torch.empty(1, dtype=torch.float32, device=dev)
+        out[name] = timed_launch(lambda: fsc.gather_floor(G, l, z, store=st, out=acc), reps=10, warm=3)
+        del z
+    G.close()
+    return out
 
-    # each run: (labels, filter info or None, Lloyd iterations) of one clustering with seed sd
-    def plain_f32(G, sd):
-        lab, st = fsc.cluster(G, k, l, t, sd)
-        return lab, None, st["iterations"]
 
-    def plain(G, sd):
-        lab, st = fsc.cluster(G, k, l, t, sd, store=fsc.BF16, rescale=True)
-        return lab, None, st["iterations"]
+def time_variants(R, g, planted, kp, seed, flush, steps=5):
+    """Every path on the same graph: ms per clustering (create_graph + cluster), ARI against the planted
+    labels, the mean sparse-step launch time, and for the filter the guard's energy ratio and whether it
+    fell back; the median over 8 seeds of the time of one clustering and of its Lloyd iteration count;
+    for every embedding, the ARI over 8 k-means seeds (median) and of the best of 8 by inertia."""
+    import torch
+    fsc = R.fsc
+    out = {}
+    paths = ["plain_f32", "plain_bf16"] + (["learned_f32", "learned_f16", "learned_bf16"] if R.params is not None else [])
+    paths.append("orthogonal_f32")
 
-    def orthogonal(G, sd):   # the same l columns kept D-orthonormal (every 4 steps)
-        lab, st, _, _ = fsc.kmeans(fsc.embed_orthogonal(G, l, t, sd, every=4), l, k, sd)
-        return lab, None, st["iterations"]
-
-    def filtered(store):
-        def run(G, sd):
-            lab, st = fsc.cluster_filtered(G, k, l, sd, params, store=store)
-            return lab, st, st["iterations"]
-        return run
-
-    runs = {"plain_f32": plain_f32, "plain_bf16": plain, "orthogonal_f32": orthogonal}
-    if params is not None:
-        runs["learned_filter_f32"] = filtered(fsc.F32)
-        runs["learned_filter_f16"] = filtered(fsc.F16)
-
-    def timed(fn, sd):
+    def one(path, sd, events=None):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        G = fsc.Graph(rp, col, wt)
-        res = fn(G, sd)
-        G.close()
+        if path == "orthogonal_f32":   # the same l columns kept D-orthonormal (every 4 steps)
+            G = fsc.Graph(R.rp, R.col, R.wt)
+            lab, st, _, _ = fsc.kmeans(fsc.embed_orthogonal(G, R.l, R.t, sd, every=4, events=events), R.l, R.k, sd)
+            G.close()
+            nl = R.t
+        else:
+            lab, st, nl = R.run(path, sd, events=events)
         b.record()
         torch.cuda.synchronize()
-        return a.elapsed_time(b), res
+        return a.elapsed_time(b), lab, st, nl
 
-    for name, fn in runs.items():
+    for path in paths:
         for _ in range(3):
-            timed(fn, seed)
-        times = []
+            one(path, seed)
+        times, launch = [], []
         for _ in range(steps):
-            ms, (lab, info, _) = timed(fn, seed)
+            evs = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ms, lab, st, nl = one(path, seed, evs)
             times.append(ms)
-        rec = {"ms": round(float(np.mean(times)), 4), "ari_vs_planted": round(pm.ari(lab.cpu().numpy(), g.labels), 4)}
-        if info is not None:
-            rec.update(energy_ratio=round(info["filter_energy_ratio"], 4), fallback=int(info["fallback"]))
-        # the seed draws both the start block and the k-means++ centres, and the Lloyd iteration
-        # count follows: the median over 8 seeds of one clustering each is the comparable time
-        per_seed = [timed(fn, seed + s) for s in range(8)]
+            launch.append(evs[0].elapsed_time(evs[1]) / nl)
+        rec = {"ms": round(float(np.mean(times)), 4),
+               "ari_vs_planted": round(fsc.partition_scores(lab, planted, R.k, kp)[0], 4),
+               "sparse_launch_ms": round(float(np.mean(launch)), 5)}
+        if "filter_energy_ratio" in st:
+            rec.update(energy_ratio=round(st["filter_energy_ratio"], 4), fallback=int(st["fallback"]))
+        per_seed = [one(path, seed + s) for s in range(8)]
         rec["ms_median_8_seeds"] = round(float(np.median([x[0] for x in per_seed])), 4)
-        rec["lloyd_iterations_median_8_seeds"] = float(np.median([x[1][2] for x in per_seed]))
-        out[name] = rec
-    if params is None:
-        out["learned_filter"] = "weights file missing"
+        rec["lloyd_iterations_median_8_seeds"] = float(np.median([x[2]["iterations"] for x in per_seed]))
+        rec["lloyd_iterations"] = st["iterations"]
+        out[path] = rec
     # k-means++ draws decide which local optimum Lloyd reaches, so one clustering per variant says
     # little about the embedding: ARI over 8 seeds (median) and of the best of 8 by inertia
-    G = fsc.Graph(rp, col, wt)
-    planted = torch.as_tensor(g.labels.astype(np.int32), device=rp.device)
-    kp = int(g.labels.max()) + 1
+    G = fsc.Graph(R.rp, R.col, R.wt)
+    l, t, k = R.l, R.t, R.k
     embs = {"plain_f32": lambda: fsc.embed(G, l, t, seed),
             "plain_bf16": lambda: fsc.embed(G, l, t, seed, store=fsc.BF16, rescale=True),
             "orthogonal_f32": lambda: fsc.embed_orthogonal(G, l, t, seed, every=4)}
-    if params is not None:
-        embs["learned_filter_f32"] = lambda: fsc.filter_embed(G, l, k, seed, params=params, store=fsc.F32)[0]
-        embs["learned_filter_f16"] = lambda: fsc.filter_embed(G, l, k, seed, params=params, store=fsc.F16)[0]
+    if R.params is not None:
+        for name, st in (("learned_f32", fsc.F32), ("learned_f16", fsc.F16), ("learned_bf16", fsc.BF16)):
+            embs[name] = (lambda st=st: fsc.filter_embed(G, l, k, seed, params=R.params, store=st)[0])
     for name, mk in embs.items():
         E = mk()
-        aris = []
-        for s in range(8):
-            lab, _, _, _ = fsc.kmeans(E, l, k, seed + s)
-            aris.append(fsc.partition_scores(lab, planted, k, kp)[0])
-        lab, _, _, _, _ = fsc.kmeans_best(E, l, k, seed, 8)
+        aris = [fsc.partition_scores(fsc.kmeans(E, l, k, seed + s)[0], planted, k, kp)[0] for s in range(8)]
+        lab = fsc.kmeans_best(E, l, k, seed, 8)[0]
         rec = out.setdefault(name, {})
         rec["ari_median_8_seeds"] = round(float(np.median(aris)), 4)
         rec["ari_best_of_8"] = round(fsc.partition_scores(lab, planted, k, kp)[0], 4)
+        del E
     G.close()
     return out
+
+
+# ---- the oracle on the host cores (CPU baseline and reference arm) -----------------------------
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def oracle_sample(g, w, lloyd_iters, csr=None, threads=None):
+    """Times a bounded sample of the float64 oracle's Algorithm 2 (plain power method) on the host
+    cores and scales it to one clustering: degrees, the start block and the float32 embedding once;
+    2 of the t power steps (x t/2); 3 of the k-1 k-means++ rounds (x (k-1)/3); one Lloyd iteration
+    with k centres (x the clustering's Lloyd iteration count).  Returns (ms, detail)."""
+    from oracle import omp
+    if threads is not None:
+        omp.set_threads(threads)
+    csr = csr or omp.Csr(g)
+    k, l, t, seed = w["k"], w["l"], w["t"], w["seed"]
+    tm = {}
+    t0 = time.perf_counter()
+    deg, dinv = omp.degrees(csr)
+    tm["degrees"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x = omp.gaussian_block(g.n, l, seed)
+    tm["start_block"] = time.perf_counter() - t0
+    S = min(2, t)
+    t0 = time.perf_counter()
+    omp.power_method(csr, deg, dinv, x, S)
+    tm["power_steps"] = (time.perf_counter() - t0) * (t / S if S else 0.0)
+    t0 = time.perf_counter()
+    B = omp.embedding_f32(dinv, x)
+    tm["embedding"] = time.perf_counter() - t0
+    rounds = min(4, k)
+    t0 = time.perf_counter()
+    omp.kmeanspp(B, k, seed, rounds=rounds)
+    tm["kmeanspp"] = (time.perf_counter() - t0) * ((k - 1) / (rounds - 1) if rounds > 1 else 0.0)
+    centres = np.linspace(0, g.n - 1, k).astype(np.int64)
+    t0 = time.perf_counter()
+    omp.lloyd(B, centres, max_iter=1)
+    tm["lloyd"] = (time.perf_counter() - t0) * lloyd_iters
+    ms = 1e3 * sum(tm.values())
+    return ms, {key: round(v * 1e3, 2) for key, v in tm.items()}
+
+
+def cpu_baseline(g, w, lloyd_iters):
+    """The all-core leg and a single-core leg of the same sample."""
+    from oracle import omp
+    cores = omp.threads()
+    csr = omp.Csr(g)
+    ms, parts = oracle_sample(g, w, lloyd_iters, csr=csr, threads=cores)
+    ms1, _ = oracle_sample(g, w, lloyd_iters, csr=csr, threads=1)
+    omp.set_threads(cores)
+    return {"value": round(ms, 1), "unit": E2E_UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"float64 oracle (plain C + OpenMP), plain power method t={w['t']}: degrees, start block and "
+                      f"embedding once, 2 power steps x t/2, 3 k-means++ rounds x (k-1)/3, 1 Lloyd iteration x "
+                      f"{lloyd_iters} (the clustering's count)",
+            "phases_ms": parts, "single_core_ms": round(ms1, 1), "cpu": cpu_model()}
+
+
+def reference_arm(args, w):
+    """The float64 oracle on the host cores (the comparison arm): a full oracle clustering once, then per
+    step the bounded sample of oracle_sample scaled to one clustering."""
+    from oracle import metrics, omp
+    dev = "cpu"
+    try:
+        import torch
+        if torch.cuda.is_available():
+            dev = "cuda"
+    except ImportError:
+        pass
+    g = make_graph(w, device=dev)
+    cores = omp.threads()
+    t0 = time.perf_counter()
+    full = omp.fast_spectral_cluster(g, w["k"], w["l"], w["t"], w["seed"])
+    full_ms = (time.perf_counter() - t0) * 1e3
+    iters = full["iters"]
+    csr = omp.Csr(g)
+    for _ in range(args.warmup):
+        oracle_sample(g, w, iters, csr=csr)
+    times = []
+    parts = None
+    for _ in range(args.steps):
+        ms, parts = oracle_sample(g, w, iters, csr=csr)
+        times.append(ms)
+    ms = float(np.mean(times))
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(ms, 2),
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 2),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 (k-means decisions in f32)",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"{args.workload}: {w['desc']}", "path": "plain power method (the paper's Algorithm 2)",
+                   "n": g.n, "nnz": g.nnz, "k": w["k"], "l": w["l"], "t": w["t"]},
+        "cpu_baseline": {"value": round(ms, 2), "unit": E2E_UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step: degrees, start block and embedding once, 2 power steps x t/2, 3 "
+                                   "k-means++ rounds x (k-1)/3, 1 Lloyd iteration x the Lloyd iteration count of "
+                                   "one full oracle clustering run before the steps",
+                         "phases_ms": parts, "cpu": cpu_model(), "full_clustering_ms": round(full_ms, 1)},
+        "e2e": {"value": round(ms, 2), "unit": E2E_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "ari_vs_planted": round(metrics.ari(full["labels"], g.labels), 4),
+        "lloyd_iterations": iters,
+    }
 
 
 def batch_arm(args, w):
@@ -391,7 +604,6 @@ def batch_arm(args, w):
     import torch
     import paper_2310_10939_gb300 as fsc
     import workloads as W
-    dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
     gb = W.sbm_batch_gpu(w["G"], w["n_range"], w["k_range"], w["deg_in"], w["deg_out"], seed=w["seed"])
@@ -416,21 +628,25 @@ def batch_arm(args, w):
     clk = clocks.stop()
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     stats, _, _ = plan.results()
-    # per-graph launches: one fsc_create_graph + fsc_cluster per graph on the same CSR slices
+    # per-graph launches: one fsc_create_graph + fsc_cluster per graph on the same CSR, its per-graph
+    # views (local row pointers and column ids) prepared before the timed loop
     voff = gb.vertex_offset
-    rp_h = gb.row_ptr
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    views = []
     for g in range(gb.num_graphs):
         lo, hi = int(voff[g]), int(voff[g + 1])
-        rp = rp_h[lo:hi + 1]
-        e0 = rp[0]
-        G = fsc.Graph(rp - e0, gb.col[int(e0):int(rp[-1])] - lo, gb.w[int(e0):int(rp[-1])] if gb.w is not None else None)
-        l, t = fsc.default_params(hi - lo, int(gb.k[g]))
+        rp = gb.row_ptr[lo:hi + 1]
+        e0, e1 = int(rp[0]), int(rp[-1])
+        views.append((rp - e0, gb.col[e0:e1] - lo, gb.w[e0:e1] if gb.w is not None else None,
+                      fsc.default_params(hi - lo, int(gb.k[g]))))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g, (rp, col, wv, (l, t)) in enumerate(views):
+        G = fsc.Graph(rp, col, wv)
         fsc.cluster(G, int(gb.k[g]), l, t, int(seeds[g]), store=store, rescale=True)
         G.close()
     torch.cuda.synchronize()
     per_graph_s = time.perf_counter() - t0
+    del views
     nnz = int(gb.col.numel())
     out = {
         "metric": "graphs/s (batched clustering of many graphs)",
@@ -456,71 +672,14 @@ def batch_arm(args, w):
     return out
 
 
-def cpu_oracle_step(g, w):
-    from oracle import kmeans as km
-    from oracle import metrics, spectral
-    B = spectral.embed(g, w["l"], w["t"], w["seed"])
-    out = km.kmeans(B.astype(np.float32), w["k"], w["seed"])
-    spectral.degrees(g)
-    return metrics.ari(out["labels"], g.labels), out
-
-
-def cpu_cores_used():
-    try:
-        from threadpoolctl import threadpool_info
-        n = max([1] + [int(i.get("num_threads", 1)) for i in threadpool_info()])
-        return n
-    except Exception:
-        return 1
-
-
-def reference_arm(args, w):
-    """The float64 CPU oracle, timed on the host cores (the comparison arm)."""
-    import workloads as W
-    tiny = W.sbm_by_degree(4096, 4, 20.0, 2.0, seed=1)
-    small_w = dict(w, k=4)
-    for _ in range(args.warmup):
-        cpu_oracle_step(tiny, small_w)
-    g = make_graph(w)
-    times = []
-    ari = None
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        ari, _ = cpu_oracle_step(g, w)
-        times.append((time.perf_counter() - t0) * 1e3)
-    ms = float(np.mean(times))
-    cores = cpu_cores_used()
-    return {
-        "impl": "reference",
-        "metric": METRIC,
-        "value": round(ms, 3),
-        "unit": "ms per clustering (create_graph + cluster)",
-        "n_gpus": args.gpus,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(ms, 3),
-        "higher_is_better": False,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64 (k-means decisions in f32)",
-        "data": "synthetic (seeded generator)",
-        "config": {"workload": f"{args.workload}: {w['desc']}", "n": g.n, "nnz": g.nnz},
-        "cpu_baseline": {"value": round(ms, 3), "unit": "ms per clustering", "cores": cores, "kind": "oracle",
-                         "sample": "the full workload per timed step (numpy/scipy float64 oracle); warm-up steps "
-                                   "on a 4096-vertex SBM"},
-        "e2e": {"value": round(ms, 3), "unit": "ms per clustering", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-        "ari_vs_planted": round(ari, 4) if ari is not None else None,
-    }
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["fsc", "reference"], default="fsc")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sbm_n2p20_k16")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--path", choices=sorted(PATH_DTYPE), default=None, help="override the workload's timed path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
@@ -547,14 +706,10 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     out, g = gpu_arm(args, w, rank, world, local_rank)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and g.n <= 2 ** 20:
-        t0 = time.perf_counter()
-        ari_cpu, _ = cpu_oracle_step(g, w)
-        cpu_ms = (time.perf_counter() - t0) * 1e3
-        out["cpu_baseline"] = {"value": round(cpu_ms, 3), "unit": "ms per clustering", "cores": cpu_cores_used(),
-                               "kind": "oracle",
-                               "sample": "one full clustering of the same graph (float64 numpy/scipy oracle)",
-                               "ari_vs_planted": round(ari_cpu, 4)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        plain = (out.get("variants") or {}).get("plain_f32", {})
+        iters = plain.get("lloyd_iterations") or out["lloyd_iterations"] or 1
+        out["cpu_baseline"] = cpu_baseline(g, w, iters)
     if world > 1:
         import torch
         torch.distributed.barrier()

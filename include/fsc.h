@@ -159,6 +159,18 @@ fsc_status fsc_power_step(const fsc_graph* g, int l, fsc_dtype store, const void
                           int threads_per_row, void* stream);
 
 /*
+ * fsc_gather_floor - a measurement aid, not a step of the method: the neighbour gathers of one
+ * power step (Algorithm 1 body: one iterate row per stored entry) with no row structure.  Reads
+ * every column index of g once, in order, loads the row of z it names and adds the rows up into
+ * *sum_out (device float, overwritten; the value itself means nothing).  z: n * fsc_pad_l(l)
+ * elements of `store` (FSC_F32, FSC_BF16 or FSC_F16), aligned like an embedding.  Its duration
+ * is the floor that random row gathers set for fsc_power_step (and the filter's sparse steps) on
+ * the same graph, row width and type: row_ptr, the per-row sums, 1/d and the output rows are
+ * left out.  Asynchronous.
+ */
+fsc_status fsc_gather_floor(const fsc_graph* g, int l, fsc_dtype store, const void* z, float* sum_out, void* stream);
+
+/*
  * fsc_kmeans - k-means++ seeding and Lloyd iterations on the rows of emb (Sec. 2.2).
  *
  * emb: float[n * ld], row i = point i, first l columns used (1 <= l <= ld, ld in {1,2,4,8}).
@@ -193,13 +205,20 @@ fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int k, uint64_
  * chosen centre; plus per-tile sums and the centroids) lives in one fixed array of
  * FSC_KMEANS_STATIC_SCRATCH_BYTES compiled into the library, which every GPU that loads the
  * library keeps reserved until the process exits.
- *  - Problems whose scratch does not fit return FSC_ERR_TOO_LARGE (with 152 SMs this admits,
- *    for example, n = 1,048,576 points with k = 64 and ld = 8).
- *  - All calls on a device share the one array: calls that may run at the same time on the
- *    GPU (different streams, threads or processes sharing the context) race; serialise them.
- *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
- *    with that device current); make that first call before any stream capture.
- *  - Always synchronous: it waits for `stream` and reports device-side errors; stats may be NULL.
+ *  - Size limit, independent of the GPU and of the launch shape: about
+ *      12 n + 24 ceil(n / 2048) + 24 k (ld + 1) + 12 k ld + 8 k + 1 KB  (each part rounded up
+ *    to 256 bytes) must not exceed FSC_KMEANS_STATIC_SCRATCH_BYTES; larger problems return
+ *    FSC_ERR_TOO_LARGE.  With k = 64 and ld = 8 that admits up to about 1.39 million points.
+ *  - All calls on a device share the one array, which keeps the last call's contents (the
+ *    call clears what must start at zero): calls that may run at the same time on the GPU
+ *    (different streams, threads or processes sharing the context) race; serialise them.
+ *  - Every call looks up the array's device address (cudaGetSymbolAddress) on the current
+ *    device; nothing is cached, so the call also works after cudaDeviceReset.
+ *  - Always synchronous: it waits for `stream` and copies results to the host, so it cannot be
+ *    used inside a stream capture (a call on a capturing stream returns FSC_ERR_INVALID_ARG
+ *    without touching the capture).  stats may be NULL.
+ *  - Device-side errors (e.g. FSC_ERR_TIMEOUT) are reported in the return value only; unlike
+ *    fsc_kmeans they are not added to the status word that fsc_sync_status() reads.
  */
 #define FSC_KMEANS_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 fsc_status fsc_kmeans_static(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int max_iter,

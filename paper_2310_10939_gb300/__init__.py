@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
         L.fsc_pad_l.restype = i32
         L.fsc_embed.argtypes = [vp, i32, i32, u64, i32, vp, C.POINTER(EmbedOpts), vp]
         L.fsc_power_step.argtypes = [vp, i32, i32, vp, vp, i32, vp]
+        L.fsc_gather_floor.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.fsc_gather_floor.restype = i32
         L.fsc_kmeans.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
         L.fsc_kmeans_static.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
         L.fsc_knn_graph.argtypes = [vp, i64, i32, i32, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(C.c_double), vp]
@@ -302,6 +304,16 @@ def power_step(g: Graph, l: int, z_in, z_out, store: int = F32, threads_per_row:
     _check(lib().fsc_power_step(g.handle, int(l), int(store), _ptr(z_in), _ptr(z_out), int(threads_per_row),
                                 _stream(stream)), "fsc_power_step")
     return z_out
+
+
+def gather_floor(g: Graph, l: int, z, store: int = F32, out=None, stream=None):
+    """fsc_gather_floor: the neighbour gathers of one power step with no row structure (a
+    measurement aid; the returned device float means nothing)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(1, dtype=torch.float32, device=z.device)
+    _check(lib().fsc_gather_floor(g.handle, l, store, _ptr(z), _ptr(out), _stream(stream)), "fsc_gather_floor")
+    return out
 
 
 def kmeans(emb, l: int, k: int, seed: int, max_iter: int = 100, labels=None, want_centroids: bool = False,

@@ -885,21 +885,13 @@ namespace fsc {
 static __device__ __align__(256) unsigned char g_kmeans_static_scratch[FSC_KMEANS_STATIC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kStaticMaxDevices = 64;
-void* g_static_base[kStaticMaxDevices];
-std::once_flag g_static_once[kStaticMaxDevices];
-cudaError_t g_static_err[kStaticMaxDevices];
-
-// Host code cannot use the array's name as a device address; look the address up once per device
-// (with that device current) and keep it.
-cudaError_t static_scratch(int dev, void** out) {
-    std::call_once(g_static_once[dev], [dev] {
-        void* p = nullptr;
-        g_static_err[dev] = cudaGetSymbolAddress(&p, g_kmeans_static_scratch);
-        g_static_base[dev] = (g_static_err[dev] == cudaSuccess) ? p : nullptr;
-    });
-    *out = g_static_base[dev];
-    return g_static_err[dev];
+// Host code cannot use the array's name as a device address.  The address is looked up on every
+// call, with the caller's device current: the lookup allocates nothing and costs little next to
+// the synchronous k-means, and an address kept from an earlier call could outlive its context
+// (cudaDeviceReset, or a caller that switches primary contexts) or keep a failed first lookup.
+cudaError_t static_scratch(void** out) {
+    *out = nullptr;
+    return cudaGetSymbolAddress(out, g_kmeans_static_scratch);
 }
 }  // namespace
 
@@ -907,11 +899,12 @@ template <int LP>
 static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64_t seed, int max_iter,
                                    int32_t* labels, double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats,
                                    cudaStream_t s) {
-    int dev = 0;
-    FSC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kStaticMaxDevices) return FSC_ERR_INVALID_ARG;
+    // the call ends with a host wait and host copies, which a stream capture cannot hold
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FSC_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return FSC_ERR_INVALID_ARG;
     void* basep = nullptr;
-    FSC_CUDA(static_scratch(dev, &basep));
+    FSC_CUDA(static_scratch(&basep));
     char* ws = static_cast<char*>(basep);
     if (!ws) return FSC_ERR_CUDA;
 

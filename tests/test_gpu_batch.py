@@ -56,7 +56,8 @@ def test_batch_equals_per_graph_cluster(torch, store_name, weighted):
 @pytest.mark.parametrize("store_name", ["f32", "bf16"])
 def test_batch_matches_oracle_on_sampled_members(torch, store_name):
     """Embedding error per member (1e-5 f32, 2e-2 bf16) and ARI within 0.01 of the oracle's
-    (every member in f32; in bf16 the members the oracle itself separates, ARI >= 0.9)."""
+    (every member in f32; in bf16 the members the oracle itself separates, ARI >= 0.9, and the
+    k-means stage of the others on the oracle's own float32 embedding)."""
     import paper_2310_10939_gb300 as fsc
     from _helpers import rel_fro
     from oracle import spectral
@@ -76,7 +77,26 @@ def test_batch_matches_oracle_on_sampled_members(torch, store_name):
         a_ref = metrics.ari(ref["labels"], m.labels)
         if store == fsc.F32 or a_ref >= 0.9:
             assert abs(a_gpu - a_ref) <= 0.01, (g, a_gpu, a_ref)
+        else:
+            # a member the oracle itself separates poorly: its k-means lands in a local optimum that
+            # a 2e-2 change of the points can move, so the ARI is not comparable; the k-means stage
+            # is then checked on the oracle's float32 embedding, labels equal up to near-ties
+            _kmeans_parity_on_oracle_embedding(torch, m, int(gb.k[g]), l, t, int(seeds[g]))
     b.close()
+
+
+def _kmeans_parity_on_oracle_embedding(torch, m, k, l, t, seed):
+    import paper_2310_10939_gb300 as fsc
+    from _helpers import near_boundary, oracle_embedding_f32
+    from oracle import kmeans as km
+    _, X = oracle_embedding_f32(m, l, t, seed, fsc.pad_l(l))
+    lab, _, _, sd = fsc.kmeans(torch.as_tensor(X, device="cuda"), l, k, seed, want_seeds=True)
+    ref = km.kmeans(X[:, :l], k, seed)
+    if not np.array_equal(sd.cpu().numpy(), ref["seeds"]):
+        assert near_boundary(X[:, :l], k, seed, ref["seeds"])
+        return
+    margin = km.relative_margin(ref["best"], ref["second"])
+    assert not ((lab.cpu().numpy() != ref["labels"]) & (margin >= 1e-6)).any()
 
 
 def test_batch_edge_cases(torch):
@@ -159,11 +179,14 @@ def test_full_scale_batch_4096_sampled(torch):
                       torch.as_tensor(m.w, device="cuda"))
         ref, _ = fsc.cluster(G, int(gb.k[g]), l, t, int(seeds[g]), store=fsc.BF16, rescale=True, threads_per_row=4)
         assert np.array_equal(labels[lo:hi], ref.cpu().numpy()), g
+        # every sampled member's embedding against the oracle, whatever its clustering quality
+        emb = b.embedding(int(g), m.n, l).cpu().numpy()
+        assert rel_fro(emb[:, :l], spectral.embed(m, l, t, int(seeds[g]))) <= 2e-2, g
         if i < 2:
-            emb = b.embedding(int(g), m.n, l).cpu().numpy()
-            assert rel_fro(emb[:, :l], spectral.embed(m, l, t, int(seeds[g]))) <= 2e-2
             oref = ocluster.fast_spectral_cluster(m, int(gb.k[g]), l, t, int(seeds[g]))
             a_ref = metrics.ari(oref["labels"], m.labels)
             if a_ref >= 0.9:
                 assert abs(metrics.ari(labels[lo:hi], m.labels) - a_ref) <= 0.01
+            else:
+                _kmeans_parity_on_oracle_embedding(torch, m, int(gb.k[g]), l, t, int(seeds[g]))
     b.close()

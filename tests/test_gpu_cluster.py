@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from _helpers import rel_fro, require_cuda
+from _helpers import near_boundary, rel_fro, require_cuda
 from oracle import cluster as ocluster
 from oracle import kmeans as km
 from oracle import metrics, spectral
@@ -53,6 +53,9 @@ def _full_scale_check(torch, g, k, l, t, seed, store, emb_tol):
     if np.array_equal(sd.cpu().numpy(), ref["seeds"]):
         margin = km.relative_margin(ref["best"], ref["second"])
         assert not ((lab_gpu != ref["labels"]) & (margin >= 1e-6)).any()
+    else:
+        # picks may part only where a draw lies within the documented error window of a boundary
+        assert near_boundary(X[:, :l], k, seed, ref["seeds"]), (sd.cpu().numpy(), ref["seeds"])
     # the whole GPU pipeline against the oracle pipeline: ARI within 0.01
     labels, st = fsc.cluster(G, k, l, t, seed, store=store, rescale=True)
     a_gpu = metrics.ari(labels.cpu().numpy(), g.labels)

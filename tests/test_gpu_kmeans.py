@@ -12,6 +12,8 @@ import numpy as np
 import pytest
 
 import workloads as W
+from _helpers import fixed_point_scales as _fixed_point_scales
+from _helpers import near_boundary as _near_boundary
 from _helpers import oracle_embedding_f32, require_cuda
 from oracle import kmeans as km
 from oracle import metrics
@@ -34,35 +36,6 @@ def _mixture(n, k, l, seed, spread=0.4, lp=None):
     out = np.zeros((n, lp), dtype=np.float32)
     out[:, :l] = X
     return out, lab
-
-
-def _fixed_point_scales(X, n, l):
-    """The library's fixed-point scales (documented in the k-means kernel header)."""
-    A = float(np.abs(X).max()) if X.size else 0.0
-    N = max(1, int(np.ceil(np.log2(max(n, 2)))))
-    Ex = (int(np.floor(np.log2(A))) + 1) if A > 0 else 0
-    Ed = 2 * Ex + int(np.ceil(np.log2(l))) + 3
-    return 62 - Ex - N, 62 - Ed - N
-
-
-def _near_boundary(X, k, seed, seeds):
-    """True if some k-means++ draw lies within the documented error window of a prefix boundary:
-    the GPU prefix is exact over D^2 truncated to 2^-Sd (error < n 2^-Sd), the oracle's float64
-    sequential prefix has rounding error < n 2^-53 P_total."""
-    n = X.shape[0]
-    _, Sd = _fixed_point_scales(X, n, X.shape[1])
-    D2 = km.dist32(X, X[seeds[0]])
-    for r in range(1, k):
-        if r > 1:
-            D2 = np.minimum(D2, km.dist32(X, X[seeds[r - 1]]))
-        P = np.cumsum(D2.astype(np.float64))
-        if P[-1] == 0:
-            continue
-        T = kmeanspp_uniform(seed, r) * P[-1]
-        window = n * 2.0 ** -Sd + n * 2.0 ** -53 * P[-1]
-        if np.min(np.abs(P - T)) <= window:
-            return True
-    return False
 
 
 def _compare(torch, X, l, k, seed, max_iter=100):

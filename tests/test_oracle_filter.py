@@ -99,3 +99,23 @@ def test_gelu_definition():
     c, cache = fl.mlp_forward(np.zeros(fl.NPARAM), np.zeros((1, 16)))
     assert np.allclose(c, 0)
     assert np.allclose(x * fl._phi(x), 0.5 * x * (1 + erf(x / np.sqrt(2))))
+
+
+def test_scalar_features_on_a_star_with_isolated_vertices():
+    """Hand-computed features f[0..7] of a star K_{1,4} plus two isolated vertices (n = 7, degrees
+    4, 1, 1, 1, 1, 0, 0; mean 8/7; population variance 20/7 - 64/49 = 76/49), k = 2, l = 3."""
+    g = W.with_isolated(W.from_edges(5, [0, 0, 0, 0], [1, 2, 3, 4]), 2)
+    X = gaussian_block(g.n, 3, 1)
+    f = fl.features(g, 2, 3, X)
+    expect = [np.log(7.0), np.log(8.0 / 7.0), np.sqrt(76.0) / 8.0, np.log(3.5), np.log(2.0), np.log(3.5),
+              3.0 / 8.0, 2.0 / 7.0]
+    assert np.allclose(f[:8], expect, rtol=1e-14, atol=1e-15), (f[:8], expect)
+
+
+def test_scalar_features_on_a_cycle():
+    """C_10 (every degree 2), k = 4, l = 8: f = log 10, log 2, 0, 0, log 4, log 2.5, 1, 0."""
+    g = W.cycle(10)
+    X = gaussian_block(g.n, 8, 2)
+    f = fl.features(g, 4, 8, X)
+    assert np.allclose(f[:8], [np.log(10.0), np.log(2.0), 0.0, 0.0, np.log(4.0), np.log(2.5), 1.0, 0.0],
+                       rtol=1e-14, atol=1e-15)

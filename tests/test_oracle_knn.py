@@ -46,3 +46,39 @@ def test_graph_is_the_symmetric_union_with_median_sigma():
                                                               col[row_ptr[i]:row_ptr[i + 1]])}
     assert all(abs(W[(i, j)] - W[(j, i)]) <= 1e-12 for (i, j) in edges)
     assert all(0.0 < v <= 1.0 for v in w)
+
+
+def test_weights_on_a_hand_worked_line():
+    """Points 0, 1, 3, 7 on a line, one neighbour each: directed distances 1, 1, 2, 4, so
+    sigma = (1 + 2) / 2 = 1.5 (median of an even count); edges {0,1}, {1,2}, {2,3} at distances
+    1, 2, 4 weigh exp(-1/2.25), exp(-4/2.25), exp(-16/2.25).  A slip such as exp(-d^2/sigma),
+    exp(-d^2/(2 sigma^2)) or exp(-d/sigma^2) fails here."""
+    X = np.array([[0.0], [1.0], [3.0], [7.0]], dtype=np.float32)
+    row_ptr, col, w, sigma, idx, _ = ok.knn_graph(X, 1)
+    assert list(idx[:, 0]) == [1, 0, 1, 2]
+    assert sigma == 1.5
+    assert list(row_ptr) == [0, 1, 3, 5, 6]
+    assert list(col) == [1, 0, 2, 1, 3, 2]
+    e1, e2, e3 = np.exp(-1 / 2.25), np.exp(-4 / 2.25), np.exp(-16 / 2.25)
+    assert np.allclose(w, [e1, e1, e2, e2, e3, e3], rtol=1e-15, atol=0)
+
+
+def test_weights_follow_library_distances():
+    """Every stored weight equals exp(-d^2 / sigma^2) with d the library's float64 distance of the
+    pair and sigma the median of its directed neighbour distances; the weights are unchanged when
+    all points are scaled by 2.5 (d and sigma scale alike)."""
+    nb = pytest.importorskip("sklearn.neighbors")
+    pw = pytest.importorskip("sklearn.metrics")
+    X = _points(300, 5, 2)
+    row_ptr, col, w, sigma, _, _ = ok.knn_graph(X, 7)
+    X64 = X.astype(np.float64)
+    d_dir = nb.NearestNeighbors(n_neighbors=7, algorithm="brute").fit(X64).kneighbors()[0]
+    s_ref = float(np.median(d_dir))
+    rows = np.repeat(np.arange(X.shape[0]), np.diff(row_ptr))
+    d = pw.pairwise_distances(X64)[rows, col]
+    # float32 squared distances of 5 columns: relative error a few 2^-24, carried into the exponent
+    a = d * d / s_ref ** 2
+    assert np.all(np.abs(w - np.exp(-a)) <= np.exp(-a) * (1e-5 + 1e-5 * a))
+    _, _, w2, sigma2, _, _ = ok.knn_graph((X * np.float32(2.5)).astype(np.float32), 7)
+    assert abs(sigma2 - 2.5 * sigma) <= 1e-6 * sigma2
+    assert np.allclose(w2, w, rtol=1e-5, atol=0)

@@ -82,3 +82,37 @@ def test_static_kmeans_allocates_nothing_and_rejects_oversized_problems(torch):
     big = torch.zeros((2 ** 21, 8), dtype=torch.float32, device="cuda")   # 2 x 8 MiB of D^2 alone
     rc, *_ = _call(L.fsc_kmeans_static, torch, big, 8, 64, 1)
     assert rc == 10 and fsc.status_string(rc).startswith("problem exceeds")
+
+
+def test_static_kmeans_size_limit_edge(torch):
+    """The limit depends on n, k and ld only: with k = 64 and ld = 8 about 12 bytes per point plus
+    the per-cluster tables fit in the 16 MiB array up to about 1.39 million points."""
+    import paper_2310_10939_gb300 as fsc
+    L = fsc.lib()
+    fits = torch.zeros((1_380_000, 8), dtype=torch.float32, device="cuda")
+    rc, lab, *_ = _call(L.fsc_kmeans_static, torch, fits, 8, 64, 2)
+    assert rc == 0 and (lab == 0).all()          # identical points: every label is the first centre's
+    del fits
+    over = torch.zeros((1_400_000, 8), dtype=torch.float32, device="cuda")
+    rc, *_ = _call(L.fsc_kmeans_static, torch, over, 8, 64, 2)
+    assert rc == 10
+
+
+def test_static_kmeans_refuses_a_capturing_stream(torch):
+    """The call waits for its stream and copies results to the host, which a capture cannot hold:
+    on a capturing stream it returns FSC_ERR_INVALID_ARG and leaves the capture intact."""
+    import paper_2310_10939_gb300 as fsc
+    L = fsc.lib()
+    Xt = torch.as_tensor(_mixture(10_000, 3, 2, 1, 2), device="cuda")
+    labels = torch.empty(10_000, dtype=torch.int32, device="cuda")
+    y = torch.zeros(16, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        y.add_(1.0)
+        stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        rc = L.fsc_kmeans_static(C.c_void_p(Xt.data_ptr()), 10_000, 2, 2, 3, 1, 100, C.c_void_p(labels.data_ptr()),
+                                 None, None, None, stream)
+    assert rc == 1
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(y[0]) == 1.0
