@@ -38,9 +38,12 @@ struct KppArgs {
     const float* X;
     int n, l, k;
     unsigned long long seed;
-    float* d2[2];
+    float* d2[2];        // D^2 per point, two buffers; tfl names the one holding a tile's current values
     long long* ttot[3];  // per tile: exact D^2 total (warp atomics), three in rotation
-    long long chunk;     // points per block, a multiple of KM_PPT
+    unsigned* tdmax[3];  // per tile: largest D^2 (float bits, warp atomics), three in rotation
+    int* tfl[2];         // per tile: the d2 buffer holding its D^2 after round r is tfl[r & 1][tile]
+    float* tcen;         // per tile: centre of its points (LP floats)
+    float* trad;         // per tile: largest distance of its points from that centre, widened
     unsigned* amax;      // max |x| (float bits), output for the Lloyd launch
     int* near;           // per point: index (selection order) of its nearest chosen centre
     int64_t* seeds;
@@ -56,6 +59,12 @@ struct KppArgs {
 // |x - c| >= |c - c_a| - |x - c_a| > sqrt(D^2)), so its D^2 is carried over without loading
 // the point.  Both sides of the test are widened by KPP_EPS relative, far above float32
 // rounding of the distances, so a skipped point is one whose min(D^2, d) is D^2 exactly.
+// The same argument for a whole tile of points with centre m and radius rho (every point within
+// rho of m) whose largest D^2 is Dmax: if |c - m| - rho > sqrt(Dmax), then for every point x of
+// the tile |x - c| >= |c - m| - |x - m| > sqrt(Dmax) >= sqrt(D^2(x)), so no D^2 of the tile changes
+// and the tile is carried over (its D^2, nearest centres and exact total) without reading any of
+// its per-point state.  rho is widened when it is stored, |c - m| shrunk and sqrt(Dmax) grown by
+// KPP_EPS relative, so a carried tile is one the per-point rule would leave unchanged.
 constexpr float KPP_EPS = 1e-5f;
 
 template <int LP>
@@ -67,21 +76,64 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     __shared__ long long s_T, s_base, s_tile;
     __shared__ unsigned s_amax;
     __shared__ int s_bstar, s_idx;
+    __shared__ float s_tsum[KM_WARPS][LP], s_tm[LP], s_tr[KM_WARPS];
+    __shared__ int s_live[KM_THREADS], s_nlive;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
-    const long long chunk = a.chunk;                 // multiple of KM_PPT
-    const long long lo = min(n, (long long)b * chunk), hi = min(n, lo + chunk);
+    const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
 
-    // ---- phase 0: A = max |x| over the used columns (sets the fixed-point scales)
+    // ---- phase 0: A = max |x| over the used columns (sets the fixed-point scales), and for each
+    // of the block's tiles the mean of its points and their largest distance from it
     if (tid == 0) s_amax = 0u;
     __syncthreads();
     {
         float m = 0.f;
-        for (long long i = lo + tid; i < hi; i += KM_THREADS) {
-            float x[LP];
-            load_point<LP>(a.X, i, a.l, x);
+        for (long long tile = b; tile < ntiles; tile += G) {
+            const long long i0 = tile * KM_TILE + (long long)KM_PPT * tid;
+            float x[KM_PPT][LP];
+            float sum[LP];
 #pragma unroll
-            for (int c = 0; c < LP; ++c) m = fmaxf(m, fabsf(x[c]));
+            for (int c = 0; c < LP; ++c) sum[c] = 0.f;
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u) {
+                if (i0 + u < n) {
+                    load_point<LP>(a.X, i0 + u, a.l, x[u]);
+#pragma unroll
+                    for (int c = 0; c < LP; ++c) {
+                        m = fmaxf(m, fabsf(x[u][c]));
+                        sum[c] += x[u][c];
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < LP; ++c) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], off);
+                if (lane == 0) s_tsum[wid][c] = sum[c];
+            }
+            __syncthreads();
+            if (tid < LP) {
+                float t = 0.f;
+                for (int w = 0; w < KM_WARPS; ++w) t += s_tsum[w][tid];
+                const long long cnt = min((long long)KM_TILE, n - tile * KM_TILE);
+                s_tm[tid] = t / (float)cnt;
+            }
+            __syncthreads();
+            float r2 = 0.f;
+#pragma unroll
+            for (int u = 0; u < KM_PPT; ++u)
+                if (i0 + u < n) r2 = fmaxf(r2, sqdist<LP>(x[u], s_tm));
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, off));
+            if (lane == 0) s_tr[wid] = r2;
+            __syncthreads();
+            if (tid == 0) {
+                float r = 0.f;
+                for (int w = 0; w < KM_WARPS; ++w) r = fmaxf(r, s_tr[w]);
+                a.trad[tile] = sqrtf(r) * (1.0f + KPP_EPS);
+            }
+            if (tid < LP) a.tcen[tile * LP + tid] = s_tm[tid];
+            __syncthreads();
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -106,7 +158,6 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     if (tid < LP) s_cent[tid] = tid < a.l ? a.X[(size_t)s_chosen[0] * LP + tid] : 0.f;
     __syncthreads();
 
-    const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
     for (int r = 1; r < a.k; ++r) {
         const float* s_c = s_cent + (size_t)(r - 1) * LP;   // the centre chosen last round
         // squared half-distances from the new centre to the earlier ones, shrunk by the margin
@@ -118,81 +169,140 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             s_half2[j] = h * h;
         }
         __syncthreads();
-        float* d2n = a.d2[r & 1];
-        const float* d2o = a.d2[(r - 1) & 1];
         long long* tt = a.ttot[r % 3];              // exact D^2 total per tile (atomics)
         long long* tz = a.ttot[(r + 1) % 3];        // cleared here for round r + 1
+        const long long* tp = a.ttot[(r + 2) % 3];  // round r - 1's totals
+        unsigned* dm = a.tdmax[r % 3];              // largest D^2 per tile (atomics)
+        unsigned* dz = a.tdmax[(r + 1) % 3];
+        const unsigned* dp = a.tdmax[(r + 2) % 3];
+        int* fl = a.tfl[r & 1];
+        const int* fp = a.tfl[(r + 1) & 1];         // after round r - 1
+        // A tile the new centre cannot reach (the rule above KPP_EPS) keeps its state.
+        auto far_tile = [&](long long t) -> bool {
+            if (r == 1) return false;
+            float mc[LP];
+#pragma unroll
+            for (int c = 0; c < LP; ++c) mc[c] = __ldcg(a.tcen + t * LP + c);
+            const float dc = sqrtf(sqdist<LP>(mc, s_c));
+            const float dmax = __uint_as_float(__ldcg(dp + t));
+            return dc * (1.0f - KPP_EPS) - __ldcg(a.trad + t) > sqrtf(dmax) * (1.0f + KPP_EPS);
+        };
         // ---- phase A: D^2 update.  Tiles of KM_TILE points are dealt round-robin (block b takes
         // b, b + G, ...): the points that cannot skip the new centre are that centre's
         // neighbourhood, a contiguous run of vertices in a clustered graph, and dealing tiles
         // spreads them over the blocks instead of loading one block while the others wait at the
-        // barrier.  The next tile's D^2 and nearest-centre indices load while this tile computes,
-        // and for l_pad <= 4 its points too (all of them: the skip then saves no latency, only L2
-        // reads, and the registers of the l_pad = 8 kernel are spent).
+        // barrier.  A tile's D^2 is read from the buffer holding it and written to the other one
+        // (the selection of the previous round may still read the first).  The next tile's D^2 and
+        // nearest-centre indices load while this tile computes, and for l_pad <= 4 its points too
+        // (all of them: the skip then saves no latency, only L2 reads, and the registers of the
+        // l_pad = 8 kernel are spent).
         constexpr bool kPre = LP <= 4;
-        float old_n[KM_PPT];
-        int na_n[KM_PPT];
-        float x_n[KM_PPT][LP];
-#pragma unroll
-        for (int u = 0; u < KM_PPT; ++u) {
-            const long long i = (long long)b * KM_TILE + (long long)KM_PPT * tid + u;
-            old_n[u] = (r > 1 && i < n) ? d2o[i] : 0.f;
-            na_n[u] = (r > 1 && i < n) ? a.near[i] : 0;
-            if constexpr (kPre) {
-                if (i < n) load_point<LP>(a.X, i, a.l, x_n[u]);
+        // The far-tile tests of the block's tiles (b, b + G, ...) run in parallel, one tile per
+        // thread, which also carries a far tile's state; the live tiles are then worked in order
+        // from a list in shared memory.
+        const long long mytiles = (ntiles - b + G - 1) / G;
+        for (long long q0 = 0; q0 < mytiles; q0 += KM_THREADS) {
+            const long long q = q0 + tid;
+            bool live = false;
+            if (q < mytiles) {
+                const long long t = b + q * G;
+                if (!far_tile(t)) {
+                    live = true;
+                } else {
+                    tt[t] = __ldcg(tp + t);
+                    tz[t] = 0;
+                    dm[t] = __ldcg(dp + t);
+                    dz[t] = 0;
+                    fl[t] = __ldcg(fp + t);
+                }
             }
-        }
-        for (long long tile = b; tile < ntiles; tile += G) {
-            const long long t0 = tile * KM_TILE;
-            const long long i0 = t0 + (long long)KM_PPT * tid;
-            float old[KM_PPT];
-            int na[KM_PPT];
-            bool need[KM_PPT];
-            float x[KM_PPT][LP];
+            const int incl = (int)block_scan_ll(live ? 1 : 0, s_red);
+            if (live) s_live[incl - 1] = (int)(q - q0);
+            if (tid == KM_THREADS - 1) s_nlive = incl;
+            __syncthreads();
+            const int nlive = s_nlive;
+            auto live_tile = [&](int j) -> long long { return j < nlive ? b + (q0 + s_live[j]) * G : ntiles; };
+            float old_n[KM_PPT];
+            int na_n[KM_PPT];
+            float x_n[KM_PPT][LP];
+            long long tile = live_tile(0);
+            int src_n = (r > 1 && tile < ntiles) ? __ldcg(fp + tile) : 0;
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
-                old[u] = old_n[u];
-                na[u] = na_n[u];
-                const long long inext = i0 + (long long)G * KM_TILE + u;
-                old_n[u] = (r > 1 && inext < n) ? d2o[inext] : 0.f;
-                na_n[u] = (r > 1 && inext < n) ? a.near[inext] : 0;
+                const long long i = tile * KM_TILE + (long long)KM_PPT * tid + u;
+                old_n[u] = (r > 1 && i < n) ? a.d2[src_n][i] : 0.f;
+                na_n[u] = (r > 1 && i < n) ? a.near[i] : 0;
                 if constexpr (kPre) {
-#pragma unroll
-                    for (int c = 0; c < LP; ++c) x[u][c] = x_n[u][c];
-                    if (inext < n) load_point<LP>(a.X, inext, a.l, x_n[u]);
+                    if (i < n) load_point<LP>(a.X, i, a.l, x_n[u]);
                 }
             }
+            for (int jl = 0; jl < nlive; ++jl) {
+                const long long nxt = live_tile(jl + 1);
+                const int src = src_n;
+                src_n = (r > 1 && nxt < ntiles) ? __ldcg(fp + nxt) : 0;
+                float* d2n = a.d2[src ^ 1];
+                const long long t0 = tile * KM_TILE;
+                const long long i0 = t0 + (long long)KM_PPT * tid;
+                float old[KM_PPT];
+                int na[KM_PPT];
+                bool need[KM_PPT];
+                float x[KM_PPT][LP];
 #pragma unroll
-            for (int u = 0; u < KM_PPT; ++u) {
-                const bool in = i0 + u < n;
-                need[u] = in && (r == 1 || old[u] * (1.0f + KPP_EPS) * (1.0f + KPP_EPS) >= s_half2[na[u]]);
-            }
-            if constexpr (!kPre) {
+                for (int u = 0; u < KM_PPT; ++u) {
+                    old[u] = old_n[u];
+                    na[u] = na_n[u];
+                    const long long inext = nxt * KM_TILE + (long long)KM_PPT * tid + u;
+                    old_n[u] = (r > 1 && inext < n) ? a.d2[src_n][inext] : 0.f;
+                    na_n[u] = (r > 1 && inext < n) ? a.near[inext] : 0;
+                    if constexpr (kPre) {
 #pragma unroll
-                for (int u = 0; u < KM_PPT; ++u)
-                    if (need[u]) load_point<LP>(a.X, i0 + u, a.l, x[u]);
-            }
-            long long v = 0;
-#pragma unroll
-            for (int u = 0; u < KM_PPT; ++u) {
-                if (i0 + u < n) {
-                    float dd = old[u];
-                    if (need[u]) {
-                        const float dn = sqdist<LP>(x[u], s_c);
-                        if (r == 1 || dn < old[u]) {
-                            dd = dn;
-                            a.near[i0 + u] = r - 1;
-                        }
+                        for (int c = 0; c < LP; ++c) x[u][c] = x_n[u][c];
+                        if (inext < n) load_point<LP>(a.X, inext, a.l, x_n[u]);
                     }
-                    d2n[i0 + u] = dd;
-                    v += fixq(dd, sc.Sd);
                 }
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    const bool in = i0 + u < n;
+                    need[u] = in && (r == 1 || old[u] * (1.0f + KPP_EPS) * (1.0f + KPP_EPS) >= s_half2[na[u]]);
+                }
+                if constexpr (!kPre) {
+#pragma unroll
+                    for (int u = 0; u < KM_PPT; ++u)
+                        if (need[u]) load_point<LP>(a.X, i0 + u, a.l, x[u]);
+                }
+                long long v = 0;
+                float dmx = 0.f;
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    if (i0 + u < n) {
+                        float dd = old[u];
+                        if (need[u]) {
+                            const float dn = sqdist<LP>(x[u], s_c);
+                            if (r == 1 || dn < old[u]) {
+                                dd = dn;
+                                a.near[i0 + u] = r - 1;
+                            }
+                        }
+                        d2n[i0 + u] = dd;
+                        v += fixq(dd, sc.Sd);
+                        dmx = fmaxf(dmx, dd);
+                    }
+                }
+                v = warp_sum_ll(v);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, off));
+                if (lane == 0) {
+                    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(tt + tile), (unsigned long long)v);
+                    if (dmx > 0.f) atomicMax(dm + tile, __float_as_uint(dmx));
+                    if (wid == 0) {
+                        tz[tile] = 0;
+                        dz[tile] = 0;
+                        fl[tile] = src ^ 1;
+                    }
+                }
+                tile = nxt;
             }
-            v = warp_sum_ll(v);
-            if (lane == 0) {
-                if (v) atomicAdd(reinterpret_cast<unsigned long long*>(tt + tile), (unsigned long long)v);
-                if (wid == 0) tz[tile] = 0;
-            }
+            __syncthreads();   // s_live is rewritten by the next chunk
         }
         if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
 
@@ -239,6 +349,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             __syncthreads();
             const long long tq = s_tile;
             if (tq >= 0) {   // always (exact sums cross the target); block-uniform
+                const float* d2n = a.d2[__ldcg(fl + tq)];
                 const long long i0 = tq * KM_TILE + (long long)KM_PPT * tid;
                 long long qv[KM_PPT];
                 long long v = 0;
@@ -641,6 +752,54 @@ static size_t lloyd_smem_bytes(int k, int LP, int ntab) {
     return lloyd_queue_offset(k, LP, ntab) + (size_t)KM_WARPS * KM_QUEUE * 12;
 }
 
+// Workspace of one k-means call: header (stats, grid barrier, status, max |x|) and the Lloyd
+// accumulators (zeroed together), the two D^2 buffers, the per-tile k-means++ state (zeroed:
+// exact totals x 3, largest D^2 x 3, buffer flags x 2; not zeroed: tile centres and radii), the
+// centroids (float64, float32), the k-means++ picks and each point's nearest chosen centre.
+struct KmLayout {
+    size_t hdr, acc, o_d2, o_tt, tt_bytes, o_tg, o_c64, o_c32, o_seed, o_near, total;
+    size_t d2_stride, tt8, tt4;
+};
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static KmLayout km_layout(long long n, int k, int LP) {
+    KmLayout L{};
+    const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
+    L.hdr = up256(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
+    L.acc = up256((size_t)3 * k * (LP + 1) * 8 + 16 * 8);
+    L.d2_stride = up256((size_t)n * 4);
+    L.tt8 = up256((size_t)ntiles * 8);
+    L.tt4 = up256((size_t)ntiles * 4);
+    size_t off = L.hdr + L.acc;
+    L.o_d2 = off; off += 2 * L.d2_stride;
+    L.o_tt = off; L.tt_bytes = 3 * L.tt8 + 5 * L.tt4; off += L.tt_bytes;
+    L.o_tg = off; off += up256((size_t)ntiles * LP * 4) + L.tt4;
+    L.o_c64 = off; off += up256((size_t)k * LP * 8);
+    L.o_c32 = off; off += up256((size_t)k * LP * 4);
+    L.o_seed = off; off += up256((size_t)k * 8);
+    L.o_near = off; off += up256((size_t)n * 4);
+    L.total = off;
+    return L;
+}
+
+// Points the k-means++ arguments at the buffers of a workspace laid out by km_layout.
+static void kpp_buffers(KppArgs& ka, char* ws, const KmLayout& L, long long ntiles, int LP) {
+    ka.d2[0] = reinterpret_cast<float*>(ws + L.o_d2);
+    ka.d2[1] = reinterpret_cast<float*>(ws + L.o_d2 + L.d2_stride);
+    char* t = ws + L.o_tt;
+    for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(t + q * L.tt8);
+    t += 3 * L.tt8;
+    for (int q = 0; q < 3; ++q) ka.tdmax[q] = reinterpret_cast<unsigned*>(t + q * L.tt4);
+    t += 3 * L.tt4;
+    for (int q = 0; q < 2; ++q) ka.tfl[q] = reinterpret_cast<int*>(t + q * L.tt4);
+    ka.tcen = reinterpret_cast<float*>(ws + L.o_tg);
+    ka.trad = reinterpret_cast<float*>(ws + L.o_tg + up256((size_t)ntiles * LP * 4));
+    ka.seeds = reinterpret_cast<int64_t*>(ws + L.o_seed);
+    ka.near = reinterpret_cast<int*>(ws + L.o_near);
+    ka.c32 = reinterpret_cast<float*>(ws + L.o_c32);
+}
+
 template <typename K>
 static int coop_blocks(K kern, size_t smem) {
     int per_sm = kernel_occupancy((const void*)kern, KM_THREADS, smem);
@@ -665,36 +824,21 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     if (G2 < G) G = G2;
     if (G < 1) return FSC_ERR_CUDA;
     if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
-    // both kernels deal tiles of KM_TILE points round-robin: no more blocks than tiles; the
-    // k-means++ maximum pass takes contiguous chunks (multiples of KM_PPT points)
+    // both kernels deal tiles of KM_TILE points round-robin: no more blocks than tiles
     const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;
     if (G > ntiles) G = (int)ntiles;
-    long long chunk = ((long long)n + G - 1) / G;
-    chunk = (chunk + KM_PPT - 1) / KM_PPT * KM_PPT;
-    G = (int)(((long long)n + chunk - 1) / chunk);
 
-    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
-    size_t off = 0;
-    const size_t acc = up((size_t)3 * k * (LP + 1) * 8 + 16 * 8);   // Lloyd accumulators, zeroed with the header
-    const size_t o_hdr = off; off += hdr;
-    const size_t o_acc = off; off += acc;
-    const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
-    const size_t o_tt = off; off += 3 * up((size_t)ntiles * 8);
-    const size_t o_c64 = off; off += up((size_t)k * LP * 8);
-    const size_t o_c32 = off; off += up((size_t)k * LP * 4);
-    const size_t o_seed = off; off += up((size_t)k * 8);
-    const size_t o_near = off; off += up((size_t)n * 4);
+    const KmLayout Lw = km_layout(n, k, LP);
     char* ws = nullptr;
-    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&ws), off, s);
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&ws), Lw.total, s);
     if (e != cudaSuccess) return cuda_status(e);
     fsc_status rc = FSC_OK;
-    KmDevStats* st = reinterpret_cast<KmDevStats*>(ws + o_hdr);
-    GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + o_hdr + sizeof(KmDevStats));
-    int* call_status = reinterpret_cast<int*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier));
-    unsigned* amax = reinterpret_cast<unsigned*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier) + 8);
+    KmDevStats* st = reinterpret_cast<KmDevStats*>(ws);
+    GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + sizeof(KmDevStats));
+    int* call_status = reinterpret_cast<int*>(ws + sizeof(KmDevStats) + sizeof(GridBarrier));
+    unsigned* amax = reinterpret_cast<unsigned*>(ws + sizeof(KmDevStats) + sizeof(GridBarrier) + 8);
     do {
-        if ((e = cudaMemsetAsync(ws + o_hdr, 0, hdr + acc, s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(ws, 0, Lw.hdr + Lw.acc, s)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(labels, 0xff, (size_t)n * 4, s)) != cudaSuccess) break;
         KppArgs ka{};
         ka.X = emb;
@@ -702,15 +846,9 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         ka.l = l;
         ka.k = k;
         ka.seed = seed;
-        ka.d2[0] = reinterpret_cast<float*>(ws + o_d2);
-        ka.d2[1] = reinterpret_cast<float*>(ws + o_d2 + up((size_t)n * 4));
-        for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(ws + o_tt + q * up((size_t)ntiles * 8));
-        if ((e = cudaMemsetAsync(ws + o_tt, 0, 3 * up((size_t)ntiles * 8), s)) != cudaSuccess) break;
-        ka.chunk = chunk;
+        kpp_buffers(ka, ws, Lw, ntiles, LP);
+        if ((e = cudaMemsetAsync(ws + Lw.o_tt, 0, Lw.tt_bytes, s)) != cudaSuccess) break;
         ka.amax = amax;
-        ka.seeds = reinterpret_cast<int64_t*>(ws + o_seed);
-        ka.near = reinterpret_cast<int*>(ws + o_near);
-        ka.c32 = reinterpret_cast<float*>(ws + o_c32);
         ka.bar = bar;
         ka.status = call_status;
         ka.limit = wait_limit_ns();
@@ -726,8 +864,8 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.max_iter = max_iter;
         la.labels = labels;
         la.c32 = ka.c32;
-        la.c64 = reinterpret_cast<double*>(ws + o_c64);
-        la.tot = reinterpret_cast<unsigned long long*>(ws + o_acc);
+        la.c64 = reinterpret_cast<double*>(ws + Lw.o_c64);
+        la.tot = reinterpret_cast<unsigned long long*>(ws + Lw.hdr);
         la.cnt3 = la.tot + (size_t)3 * k * (LP + 1);
         la.amax = amax;
         la.ntab = ntab;
@@ -923,30 +1061,16 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
     const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;   // both kernels deal these round-robin
     if (G > ntiles) G = (int)ntiles;
-    long long chunk = ((long long)n + G - 1) / G;
-    chunk = (chunk + KM_PPT - 1) / KM_PPT * KM_PPT;
-    G = (int)(((long long)n + chunk - 1) / chunk);
 
-    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t hdr = up(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
-    size_t off = 0;
-    const size_t acc = up((size_t)3 * k * (LP + 1) * 8 + 16 * 8);   // Lloyd accumulators, zeroed with the header
-    const size_t o_hdr = off; off += hdr;
-    const size_t o_acc = off; off += acc;
-    const size_t o_d2 = off; off += 2 * up((size_t)n * 4);
-    const size_t o_tt = off; off += 3 * up((size_t)ntiles * 8);
-    const size_t o_c64 = off; off += up((size_t)k * LP * 8);
-    const size_t o_c32 = off; off += up((size_t)k * LP * 4);
-    const size_t o_seed = off; off += up((size_t)k * 8);
-    const size_t o_near = off; off += up((size_t)n * 4);
-    if (off > (size_t)FSC_KMEANS_STATIC_SCRATCH_BYTES) return FSC_ERR_TOO_LARGE;
+    const KmLayout Lw = km_layout(n, k, LP);
+    if (Lw.total > (size_t)FSC_KMEANS_STATIC_SCRATCH_BYTES) return FSC_ERR_TOO_LARGE;
 
-    KmDevStats* st = reinterpret_cast<KmDevStats*>(ws + o_hdr);
-    GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + o_hdr + sizeof(KmDevStats));
-    int* call_status = reinterpret_cast<int*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier));
-    unsigned* amax = reinterpret_cast<unsigned*>(ws + o_hdr + sizeof(KmDevStats) + sizeof(GridBarrier) + 8);
+    KmDevStats* st = reinterpret_cast<KmDevStats*>(ws);
+    GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + sizeof(KmDevStats));
+    int* call_status = reinterpret_cast<int*>(ws + sizeof(KmDevStats) + sizeof(GridBarrier));
+    unsigned* amax = reinterpret_cast<unsigned*>(ws + sizeof(KmDevStats) + sizeof(GridBarrier) + 8);
     // the array keeps the previous call's contents: clear what the kernels expect to start at zero
-    FSC_CUDA(cudaMemsetAsync(ws + o_hdr, 0, hdr + acc, s));
+    FSC_CUDA(cudaMemsetAsync(ws, 0, Lw.hdr + Lw.acc, s));
     FSC_CUDA(cudaMemsetAsync(labels, 0xff, (size_t)n * 4, s));
     KppArgs ka{};
     ka.X = emb;
@@ -954,15 +1078,9 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     ka.l = l;
     ka.k = k;
     ka.seed = seed;
-    ka.d2[0] = reinterpret_cast<float*>(ws + o_d2);
-    ka.d2[1] = reinterpret_cast<float*>(ws + o_d2 + up((size_t)n * 4));
-    for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(ws + o_tt + q * up((size_t)ntiles * 8));
-    FSC_CUDA(cudaMemsetAsync(ws + o_tt, 0, 3 * up((size_t)ntiles * 8), s));
-    ka.chunk = chunk;
+    kpp_buffers(ka, ws, Lw, ntiles, LP);
+    FSC_CUDA(cudaMemsetAsync(ws + Lw.o_tt, 0, Lw.tt_bytes, s));
     ka.amax = amax;
-    ka.seeds = reinterpret_cast<int64_t*>(ws + o_seed);
-    ka.near = reinterpret_cast<int*>(ws + o_near);
-    ka.c32 = reinterpret_cast<float*>(ws + o_c32);
     ka.bar = bar;
     ka.status = call_status;
     ka.limit = wait_limit_ns();
@@ -978,8 +1096,8 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     la.max_iter = max_iter;
     la.labels = labels;
     la.c32 = ka.c32;
-    la.c64 = reinterpret_cast<double*>(ws + o_c64);
-    la.tot = reinterpret_cast<unsigned long long*>(ws + o_acc);
+    la.c64 = reinterpret_cast<double*>(ws + Lw.o_c64);
+    la.tot = reinterpret_cast<unsigned long long*>(ws + Lw.hdr);
     la.cnt3 = la.tot + (size_t)3 * k * (LP + 1);
     la.amax = amax;
     la.ntab = ntab;
