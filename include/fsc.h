@@ -13,8 +13,10 @@
  *    comment says "host".  `stream` is a cudaStream_t passed as void*
  *    (NULL = the legacy default stream).
  *  - Matrices are row-major.  An embedding of l columns is stored with
- *    ld = fsc_pad_l(l) floats per row (1, 2, 4 or 8); columns l..ld-1 are
- *    written as zero by fsc_embed and ignored by fsc_kmeans.
+ *    ld = fsc_pad_l(l) floats per row (1, 2, 4 or 8 for l <= 8; 16, 32, 64 or
+ *    128 for l = 9 .. 128, accepted by fsc_embed_orthogonal, fsc_top_eigenvectors,
+ *    fsc_kmeans and fsc_kmeans_best); columns l..ld-1 are written as zero by
+ *    the embeddings and ignored by fsc_kmeans.
  *  - No C++ exception crosses the ABI.  Every call returns an fsc_status;
  *    outputs are defined only when it returns FSC_OK.  Calls marked
  *    "asynchronous" only enqueue work on `stream`; errors detected on the
@@ -173,7 +175,9 @@ fsc_status fsc_gather_floor(const fsc_graph* g, int l, fsc_dtype store, const vo
 /*
  * fsc_kmeans - k-means++ seeding and Lloyd iterations on the rows of emb (Sec. 2.2).
  *
- * emb: float[n * ld], row i = point i, first l columns used (1 <= l <= ld, ld in {1,2,4,8}).
+ * emb: float[n * ld], row i = point i, first l columns used (1 <= l <= ld, ld in {1, 2, 4, 8,
+ * 16, 32, 64, 128}; the rows of 16 .. 128 floats are the wide embeddings of
+ * fsc_embed_orthogonal / fsc_top_eigenvectors with l = k, and need 16-byte alignment).
  * Seeding: first centre floor(u_0 * n); round r picks the smallest i whose
  * float64 prefix sum of D^2 (float32 squared distance to the nearest chosen
  * centre) exceeds u_r * sum(D^2); u_r from Philox4x64-10 key (seed, 2),
@@ -187,8 +191,10 @@ fsc_status fsc_gather_floor(const fsc_graph* g, int l, fsc_dtype store, const vo
  * stats: host struct or NULL.  With stats != NULL the call synchronises
  * `stream` and reports device-side errors (e.g. FSC_ERR_TIMEOUT) in its
  * return value; with NULL it is asynchronous.
- * Limits: 1 <= k <= n, k <= 1024, k * ld <= 4096, 1 <= max_iter.
- * Workspace is allocated stream-ordered (cudaMallocAsync) and freed on return.
+ * Limits: 1 <= k <= n, k <= 1024, k * ld <= 4096 (ld <= 8) or 32768 (ld >= 16), 1 <= max_iter.
+ * Workspace is allocated stream-ordered (cudaMallocAsync) and freed on return.  With ld >= 16
+ * the same rules and results come from per-round / per-iteration launches (no pruning), and
+ * the call synchronises `stream` once per Lloyd iteration whether or not stats is given.
  */
 fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int max_iter,
                       int32_t* labels, double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats,
@@ -232,7 +238,10 @@ fsc_status fsc_kmeans_static(const float* emb, int64_t n, int l, int ld, int k, 
  * paper compares against (Sec. 4); the span after t steps is that of M^t X0, so only the basis,
  * not the subspace, differs from fsc_embed.  emb: n x fsc_pad_l(l) floats = D^-1/2 Q (columns
  * orthonormal in x-space).  Float32 only; opts->flags must be 0.  A column linearly dependent on
- * the earlier ones comes out zero.  Same start block as fsc_embed(seed).  Asynchronous.
+ * the earlier ones comes out zero.  Same start block as fsc_embed(seed).  1 <= l <= 128: blocks of
+ * 16 .. 128 columns (l > 8, "PM k Vectors" for k up to 128) use their own kernels for the power
+ * step (a lane group per row, 16 bytes per lane), the Gram, the Cholesky factor and Z R^-1.
+ * Asynchronous.
  */
 fsc_status fsc_embed_orthogonal(const fsc_graph* g, int l, int t, int every, uint64_t seed, float* emb,
                                 const fsc_embed_opts* opts, void* stream);
@@ -256,9 +265,10 @@ fsc_status fsc_knn_graph(const float* points, int64_t n, int dim, int knn, int64
 /*
  * fsc_top_eigenvectors - Rayleigh-Ritz on the fsc_embed_orthogonal basis: with Q that basis
  * (x-space, orthonormal), H = Q^T M Q (one more power step and a D-weighted Gram), H = V diag(theta)
- * V^T by cyclic Jacobi (float64, l <= 8), and emb <- D^-1/2 Q V, columns in decreasing theta, each
+ * V^T by cyclic Jacobi (float64; one thread for l <= 8, the block's threads rotating l/2 disjoint
+ * pairs at a time for l = 9 .. 128), and emb <- D^-1/2 Q V, columns in decreasing theta, each
  * column's largest entry of V positive.  For t large enough the pairs converge to the top l
- * eigenpairs of M: the "k Eigs" embedding of the paper's comparison (Sec. 4) when l = k <= 8.
+ * eigenpairs of M: the "k Eigs" embedding of the paper's comparison (Sec. 4) when l = k <= 128.
  * values: host double[l] <- theta.  Synchronous.
  */
 fsc_status fsc_top_eigenvectors(const fsc_graph* g, int l, int t, int every, uint64_t seed, float* emb,

@@ -46,7 +46,7 @@ def load() -> C.CDLL:
         L.orc_power_method.argtypes = [i64, vp, vp, vp, vp, vp, i32, i32, vp, vp]
         L.orc_embedding_f32.argtypes = [i64, i32, vp, vp, vp]
         L.orc_kmeanspp.argtypes = [i64, i32, vp, i32, i32, u64, vp, vp, vp]
-        L.orc_lloyd.argtypes = [i64, i32, vp, i32, vp, i32, vp, vp, vp, vp, vp]
+        L.orc_lloyd.argtypes = [i64, i32, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp]
         L.orc_lloyd.restype = i32
         _lib = L
     return _lib
@@ -132,10 +132,11 @@ def lloyd(X: np.ndarray, seeds: np.ndarray, max_iter: int = 100):
     inertia = C.c_double(0.0)
     changed = C.c_int64(0)
     best = np.empty(n, dtype=np.float32)
+    second = np.empty(n, dtype=np.float32)
     it = load().orc_lloyd(n, l, _p(X), k, _p(seeds), max_iter, _p(labels), _p(c64), C.byref(inertia),
-                          C.byref(changed), _p(best))
+                          C.byref(changed), _p(best), _p(second))
     return {"labels": labels, "centroids": c64, "iters": int(it), "inertia": float(inertia.value),
-            "changed": int(changed.value)}
+            "changed": int(changed.value), "best": best, "second": second}
 
 
 def kmeans(X: np.ndarray, k: int, seed: int, max_iter: int = 100):

@@ -196,9 +196,10 @@ void orc_kmeanspp(int64_t n, int l, const float* X, int k, int rounds, uint64_t 
 }
 
 /* Lloyd from the centres X[seeds]; returns the iteration count, writes labels, float64
- * centroids (k x l), the last assignment's inertia and the number of labels it changed. */
+ * centroids (k x l), the last assignment's inertia and the number of labels it changed, and each
+ * point's nearest and second-nearest float32 distances in that assignment. */
 int orc_lloyd(int64_t n, int l, const float* X, int k, const int64_t* seeds, int max_iter, int32_t* labels,
-              double* c64, double* inertia, int64_t* changed, float* best) {
+              double* c64, double* inertia, int64_t* changed, float* best, float* second) {
     float* c32 = (float*)malloc(sizeof(float) * (size_t)k * (size_t)l);
     double* sum = (double*)malloc(sizeof(double) * (size_t)k * (size_t)l);
     int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
@@ -215,17 +216,21 @@ int orc_lloyd(int64_t n, int l, const float* X, int k, const int64_t* seeds, int
 #pragma omp parallel for schedule(static) reduction(+ : ch)
         for (int64_t i = 0; i < n; ++i) {
             int bj = 0;
-            float bd = dist32(X + i * l, c32, l);
+            float bd = dist32(X + i * l, c32, l), sd = INFINITY;
             for (int j = 1; j < k; ++j) {
                 const float d = dist32(X + i * l, c32 + j * l, l);
                 if (d < bd) {
+                    sd = bd;
                     bd = d;
                     bj = j;
+                } else if (d < sd) {
+                    sd = d;
                 }
             }
             ch += labels[i] != bj;
             labels[i] = bj;
             best[i] = bd;
+            second[i] = sd;
         }
         double in = 0.0;
         for (int64_t i = 0; i < n; ++i) in += (double)best[i];

@@ -75,6 +75,10 @@ cudaError_t launch_init(int LP, int n, int l, unsigned long long seed, const flo
         case 2: k_gauss_init<2, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
         case 4: k_gauss_init<4, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
         case 8: k_gauss_init<8, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+        case 16: k_gauss_init<16, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+        case 32: k_gauss_init<32, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+        case 64: k_gauss_init<64, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+        case 128: k_gauss_init<128, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

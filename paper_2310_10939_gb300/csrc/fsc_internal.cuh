@@ -195,7 +195,12 @@ __device__ __forceinline__ float sqdist(const float (&x)[LP], const float* __res
     return acc;
 }
 
-inline int pad_l(int l) { return l == 1 ? 1 : l == 2 ? 2 : l <= 4 ? 4 : l <= 8 ? 8 : 0; }
+// Row width of an l-column block: 1, 2, 4, 8 for l <= 8 (every entry point); 16, 32, 64, 128 for
+// l = 9 .. 128 (orthogonal iteration, Ritz vectors, k-means); 0 beyond.
+inline int pad_l(int l) {
+    return l < 1 ? 0 : l == 1 ? 1 : l == 2 ? 2 : l <= 4 ? 4 : l <= 8 ? 8 : l <= 16 ? 16 : l <= 32 ? 32 : l <= 64 ? 64
+                                                                                         : l <= 128 ? 128 : 0;
+}
 
 }  // namespace fsc
 

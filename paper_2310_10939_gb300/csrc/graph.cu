@@ -592,7 +592,7 @@ extern "C" fsc_status fsc_graph_info(const fsc_graph* g, fsc_graph_info_t* info)
     return FSC_OK;
 }
 
-extern "C" int fsc_pad_l(int l) { return (l >= 1 && l <= 8) ? pad_l(l) : 0; }
+extern "C" int fsc_pad_l(int l) { return pad_l(l); }
 
 extern "C" fsc_status fsc_default_params(int64_t n, int k, int mode, int* l, int* t) {
     if (!l || !t || n < 1 || k < 1 || k > n || (mode != 0 && mode != 1)) return FSC_ERR_INVALID_ARG;

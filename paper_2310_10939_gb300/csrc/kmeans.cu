@@ -911,6 +911,10 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     return rc;
 }
 
+// rows of 16 .. 128 floats (kmeans_wide.cu)
+fsc_status kmeans_wide(const float* emb, int n, int l, int ld, int k, uint64_t seed, int max_iter, int32_t* labels,
+                       double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats, cudaStream_t s);
+
 }  // namespace fsc
 
 using namespace fsc;
@@ -921,11 +925,13 @@ extern "C" fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int
     if (!emb || !labels || n < 1 || n > 2147483647LL || l < 1 || l > ld || k < 1 || (int64_t)k > n || k > 1024 ||
         max_iter < 1)
         return FSC_ERR_INVALID_ARG;
-    if (ld != 1 && ld != 2 && ld != 4 && ld != 8) return FSC_ERR_INVALID_ARG;
-    if ((int64_t)k * ld > 4096) return FSC_ERR_INVALID_ARG;
+    if (ld != 1 && ld != 2 && ld != 4 && ld != 8 && ld != 16 && ld != 32 && ld != 64 && ld != 128)
+        return FSC_ERR_INVALID_ARG;
+    if ((int64_t)k * ld > (ld <= 8 ? 4096 : 32768)) return FSC_ERR_INVALID_ARG;
     const size_t al = (size_t)ld * 4 < 16 ? (size_t)ld * 4 : 16;
     if (reinterpret_cast<uintptr_t>(emb) % al) return FSC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
+    if (ld > 8) return kmeans_wide(emb, (int)n, l, ld, k, seed, max_iter, labels, centroids, seed_idx, stats, s);
     switch (ld) {
         case 1: return kmeans_lp<1>(emb, (int)n, l, k, seed, max_iter, labels, centroids, seed_idx, stats, s);
         case 2: return kmeans_lp<2>(emb, (int)n, l, k, seed, max_iter, labels, centroids, seed_idx, stats, s);
@@ -940,7 +946,7 @@ extern "C" fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int
 extern "C" fsc_status fsc_kmeans_best(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int n_init,
                                       int max_iter, int32_t* labels, double* centroids, int64_t* seed_idx,
                                       fsc_kmeans_stats* stats, int32_t* best_run, void* stream) {
-    if (n_init < 1 || n_init > 1000000 || !labels || n < 1 || n > 2147483647LL || k < 1 || l < 1 || l > 8)
+    if (n_init < 1 || n_init > 1000000 || !labels || n < 1 || n > 2147483647LL || k < 1 || l < 1 || l > 128)
         return FSC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     char* spare = nullptr;

@@ -22,6 +22,11 @@ int choose_threads_per_row(const fsc_graph* g, int requested, int LP, int store)
 
 constexpr int kOrthoThreads = 256;
 
+// l = 9 .. 128 (wide.cu)
+fsc_status embed_orthogonal_wide(fsc_graph* g, int l, int t, int every, uint64_t seed, float* emb,
+                                 const fsc_embed_opts* opts, cudaStream_t s);
+fsc_status ritz_wide(fsc_graph* g, int l, float* emb, double* values, cudaStream_t s);
+
 // Per-block partial Gram sums (upper triangle, row-major index a * LP + b, a <= b).
 template <int LP>
 __global__ void __launch_bounds__(kOrthoThreads) k_gram(int n, const float* __restrict__ z,
@@ -311,9 +316,10 @@ extern "C" fsc_status fsc_embed_orthogonal(const fsc_graph* gc, int l, int t, in
 extern "C" fsc_status fsc_top_eigenvectors(const fsc_graph* gc, int l, int t, int every, uint64_t seed, float* emb,
                                            double* values, const fsc_embed_opts* opts, void* stream) {
     fsc_graph* g = const_cast<fsc_graph*>(gc);
-    if (!g || !emb || !values || l < 1 || l > 8 || t < 0 || every < 1) return FSC_ERR_INVALID_ARG;
+    if (!g || !emb || !values || l < 1 || l > 128 || t < 0 || every < 1) return FSC_ERR_INVALID_ARG;
     fsc_status rc = fsc_embed_orthogonal(gc, l, t, every, seed, emb, opts, stream);
     if (rc != FSC_OK) return rc;
+    if (l > 8) return ritz_wide(g, l, emb, values, as_stream(stream));
     const int LP = pad_l(l);
     const int n = (int)g->n;
     cudaStream_t s = as_stream(stream);
@@ -359,11 +365,12 @@ extern "C" fsc_status fsc_top_eigenvectors(const fsc_graph* gc, int l, int t, in
 extern "C" fsc_status fsc_embed_orthogonal(const fsc_graph* gc, int l, int t, int every, uint64_t seed, float* emb,
                                            const fsc_embed_opts* opts, void* stream) {
     fsc_graph* g = const_cast<fsc_graph*>(gc);
-    if (!g || !emb || l < 1 || l > 8 || t < 0 || every < 1) return FSC_ERR_INVALID_ARG;
+    if (!g || !emb || l < 1 || l > 128 || t < 0 || every < 1) return FSC_ERR_INVALID_ARG;
     if (opts && opts->flags) return FSC_ERR_INVALID_ARG;
     const int LP = pad_l(l);
     if (reinterpret_cast<uintptr_t>(emb) % (size_t)(LP * 4 < 16 ? LP * 4 : 16)) return FSC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
+    if (l > 8) return embed_orthogonal_wide(g, l, t, every, seed, emb, opts, s);
     const int n = (int)g->n;
     fsc_status rc = ensure_workspace(g, (size_t)n * LP * 4 + 256, s);
     if (rc != FSC_OK) return rc;

@@ -49,7 +49,8 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_host_only_calls(L):
     assert L.fsc_version().decode().count(".") == 2
-    assert [fsc.pad_l(l) for l in range(0, 10)] == [0, 1, 2, 4, 4, 8, 8, 8, 8, 0]
+    assert [fsc.pad_l(l) for l in range(0, 10)] == [0, 1, 2, 4, 4, 8, 8, 8, 8, 16]
+    assert [fsc.pad_l(l) for l in (16, 17, 32, 33, 64, 65, 100, 128, 129)] == [16, 32, 32, 64, 64, 128, 128, 128, 0]
     for n, k in [(1000, 4), (2 ** 20, 16), (154401, 8), (2 ** 22, 100), (500, 2), (50000, 20), (7, 1)]:
         assert fsc.default_params(n, k, 0) == ocluster.default_params(n, k)
         assert fsc.default_params(n, k, 1) == ocluster.paper_remark_params(n, k)

@@ -87,3 +87,12 @@ def test_cluster_end_to_end_matches_on_an_sbm():
     a = omp.fast_spectral_cluster(g, 4, 2, 20, 6)
     b = oc.fast_spectral_cluster(g, 4, 2, 20, 6)
     assert abs(metrics.ari(a["labels"], g.labels) - metrics.ari(b["labels"], g.labels)) <= 0.01
+
+
+def test_lloyd_distances_match_the_numpy_oracle():
+    """The last assignment's nearest and second-nearest distances (the margin rule's inputs)."""
+    X = _mixture(3000, 6, 4, 9)
+    a = omp.kmeans(X, 6, 2)
+    b = km.kmeans(X, 6, 2)
+    if np.array_equal(a["labels"], b["labels"]):
+        assert np.array_equal(a["best"], b["best"]) and np.array_equal(a["second"], b["second"])
