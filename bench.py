@@ -425,15 +425,22 @@ def time_variants(R, g, planted, kp, seed, flush, steps=5):
     fsc = R.fsc
     out = {}
     paths = ["plain_f32", "plain_bf16"] + (["learned_f32", "learned_f16", "learned_bf16"] if R.params is not None else [])
-    paths.append("orthogonal_f32")
+    paths += ["orthogonal_f32", "pm_k_vectors_f32", "k_eigs_f32"]
 
     def one(path, sd, events=None):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        if path == "orthogonal_f32":   # the same l columns kept D-orthonormal (every 4 steps)
+        if path in ("orthogonal_f32", "pm_k_vectors_f32", "k_eigs_f32"):
+            # orthogonal iteration (D-orthonormal every 4 steps) on the method's l columns, or on
+            # l = k columns ("PM k Vectors"), or Rayleigh-Ritz on that basis ("k Eigenvectors")
             G = fsc.Graph(R.rp, R.col, R.wt)
-            lab, st, _, _ = fsc.kmeans(fsc.embed_orthogonal(G, R.l, R.t, sd, every=4, events=events), R.l, R.k, sd)
+            lw = R.l if path == "orthogonal_f32" else R.k
+            if path == "k_eigs_f32":
+                E = fsc.top_eigenvectors(G, lw, R.t, sd, every=4, events=events)[1]
+            else:
+                E = fsc.embed_orthogonal(G, lw, R.t, sd, every=4, events=events)
+            lab, st, _, _ = fsc.kmeans(E, lw, R.k, sd)
             G.close()
             nl = R.t
         else:
@@ -443,10 +450,12 @@ def time_variants(R, g, planted, kp, seed, flush, steps=5):
         return a.elapsed_time(b), lab, st, nl
 
     for path in paths:
-        for _ in range(3):
+        first = one(path, seed)[0]
+        slow = first > 100.0          # the l = k variants at k = 100: fewer repetitions
+        for _ in range(0 if slow else 2):
             one(path, seed)
         times, launch = [], []
-        for _ in range(steps):
+        for _ in range(2 if slow else steps):
             evs = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             ms, lab, st, nl = one(path, seed, evs)
             times.append(ms)
@@ -456,9 +465,10 @@ def time_variants(R, g, planted, kp, seed, flush, steps=5):
                "sparse_launch_ms": round(float(np.mean(launch)), 5)}
         if "filter_energy_ratio" in st:
             rec.update(energy_ratio=round(st["filter_energy_ratio"], 4), fallback=int(st["fallback"]))
-        per_seed = [one(path, seed + s) for s in range(8)]
-        rec["ms_median_8_seeds"] = round(float(np.median([x[0] for x in per_seed])), 4)
-        rec["lloyd_iterations_median_8_seeds"] = float(np.median([x[2]["iterations"] for x in per_seed]))
+        per_seed = [one(path, seed + s) for s in range(3 if slow else 8)]
+        rec["ms_median_8_seeds" if not slow else "ms_median_3_seeds"] = round(float(np.median([x[0] for x in per_seed])), 4)
+        rec["lloyd_iterations_median_8_seeds" if not slow else "lloyd_iterations_median_3_seeds"] = \
+            float(np.median([x[2]["iterations"] for x in per_seed]))
         rec["lloyd_iterations"] = st["iterations"]
         out[path] = rec
     # k-means++ draws decide which local optimum Lloyd reaches, so one clustering per variant says
@@ -467,14 +477,16 @@ def time_variants(R, g, planted, kp, seed, flush, steps=5):
     l, t, k = R.l, R.t, R.k
     embs = {"plain_f32": lambda: fsc.embed(G, l, t, seed),
             "plain_bf16": lambda: fsc.embed(G, l, t, seed, store=fsc.BF16, rescale=True),
-            "orthogonal_f32": lambda: fsc.embed_orthogonal(G, l, t, seed, every=4)}
+            "orthogonal_f32": lambda: fsc.embed_orthogonal(G, l, t, seed, every=4),
+            "pm_k_vectors_f32": lambda: fsc.embed_orthogonal(G, k, t, seed, every=4)}
     if R.params is not None:
         for name, st in (("learned_f32", fsc.F32), ("learned_f16", fsc.F16), ("learned_bf16", fsc.BF16)):
             embs[name] = (lambda st=st: fsc.filter_embed(G, l, k, seed, params=R.params, store=st)[0])
     for name, mk in embs.items():
         E = mk()
-        aris = [fsc.partition_scores(fsc.kmeans(E, l, k, seed + s)[0], planted, k, kp)[0] for s in range(8)]
-        lab = fsc.kmeans_best(E, l, k, seed, 8)[0]
+        le = k if name == "pm_k_vectors_f32" else l   # (k Eigs: a rotation of the same rows, same clusterings)
+        aris = [fsc.partition_scores(fsc.kmeans(E, le, k, seed + s)[0], planted, k, kp)[0] for s in range(8)]
+        lab = fsc.kmeans_best(E, le, k, seed, 8)[0]
         rec = out.setdefault(name, {})
         rec["ari_median_8_seeds"] = round(float(np.median(aris)), 4)
         rec["ari_best_of_8"] = round(fsc.partition_scores(lab, planted, k, kp)[0], 4)

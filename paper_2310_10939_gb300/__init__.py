@@ -366,7 +366,7 @@ def embed_orthogonal(g: Graph, l: int, t: int, seed: int, every: int = 1, out=No
 
 
 def top_eigenvectors(g: Graph, l: int, t: int, seed: int, every: int = 4, out=None, threads_per_row: int = 0,
-                     stream=None):
+                     events=None, stream=None):
     """fsc_top_eigenvectors: Ritz pairs of M from orthogonal iteration.  Returns (values (l,) numpy,
     embedding n x pad_l(l) = D^-1/2 [Ritz vectors])."""
     torch = _torch()
@@ -374,7 +374,7 @@ def top_eigenvectors(g: Graph, l: int, t: int, seed: int, every: int = 4, out=No
         out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=g.row_ptr.device)
     _require_cuda(out, torch.float32, "out")
     vals = (C.c_double * int(l))()
-    o = _opts(False, threads_per_row, None)
+    o = _opts(False, threads_per_row, events)
     _check(lib().fsc_top_eigenvectors(g.handle, int(l), int(t), int(every), int(seed) & (2**64 - 1), _ptr(out), vals,
                                       C.byref(o), _stream(stream)), "fsc_top_eigenvectors")
     import numpy as _np
