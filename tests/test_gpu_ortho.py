@@ -27,6 +27,7 @@ def test_orthogonal_iteration_matches_oracle(torch, name, every):
     l, t, seed = (4, 12, 3) if name == "sbm" else (5, 10, 4)
     emb = fsc.embed_orthogonal(G, l, t, seed, every=every).cpu().numpy()[:, :l].astype(np.float64)
     ref = spectral.orthogonal_iteration(g, l, t, every, seed)
+    print(f"orthogonal iteration {name} l={l} every={every}: relative error {rel_fro(emb, ref):.2e}")
     assert rel_fro(emb, ref) <= 1e-4
     # the same basis as one QR of M^t X0 at the end (the span never changes)
     Y = spectral.power_method(spectral.signless_laplacian(g), gaussian_block(g.n, l, seed), t)
