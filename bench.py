@@ -38,6 +38,10 @@ WORKLOADS = {
                            desc="SBM n=2^22, 100 equal blocks, intra-degree 36, inter-degree 4 (GPU generator), "
                                 "k=100, l=7: learned degree-8 filter, float16 basis (value) vs plain t=22 power "
                                 "method in float32 and bfloat16 (variants)"),
+    "sbm_n2p20_k100": dict(kind="sbm_gpu", n=2 ** 20, k=100, deg_in=36.0, deg_out=4.0, l=7, t=22, path="learned_f16",
+                           seed=19,
+                           desc="SBM n=2^20, 100 equal blocks, intra-degree 36, inter-degree 4 (GPU generator), "
+                                "k=100, l=7: the 2^22-vertex configuration at a quarter of its size (ncu captures)"),
     "sbm_n2p20_k16": dict(kind="sbm", n=2 ** 20, k=16, deg_in=20.0, deg_out=2.0, l=4, t=20, path="plain_f32", seed=7,
                           desc="SBM n=2^20, 16 equal blocks, intra-degree 20, inter-degree 2, unit weights; "
                                "k=16, l=4, t=20, plain power method in float32"),
@@ -74,7 +78,7 @@ def make_graph(w, device="cuda"):
         gb = W.sbm_batch_gpu(1, (w["n"], w["n"]), (w["k"], w["k"]), w["deg_in"], w["deg_out"], seed=w["seed"],
                              with_weights=False, device=device)
         return W.Graph(w["n"], gb.row_ptr.cpu().numpy(), gb.col.cpu().numpy(), None, gb.labels.cpu().numpy(),
-                       "sbm_n2p22_k100")
+                       f"sbm_n{w['n']}_k{w['k']}")
     raise ValueError(w["kind"])
 
 

@@ -441,6 +441,20 @@ void fsc_set_wait_limit_ns(int64_t ns);
  * the call reports FSC_ERR_TIMEOUT.  Host call; 0 restores normal operation. */
 void fsc_inject_barrier_stall(int enable);
 
+/*
+ * fsc_bounds_report - the first out-of-range index found by a library built with the compile flag
+ * FSC_BOUNDS_CHECK (python -m paper_2310_10939_gb300.build --bounds-check: libfsc_checked.so).  Such
+ * a build tests every index a kernel derives from its inputs before the access it addresses (a
+ * neighbour's column index against the rows of the iterate, a point's label or nearest-centre
+ * index against the centres, a chosen point against n), records the first one outside its range
+ * and skips the access; nothing traps.  Host call, synchronising the device.  *site: 0 = nothing
+ * recorded, -1 = this library has no checks, else the kernel site (1 sparse-step gather, 2 wide
+ * power-step gather, 3 k-means++ nearest centre, 4 Lloyd label, 5 wide k-means++ nearest centre,
+ * 6 wide Lloyd label, 7 k-means++ pick); *index, *lo, *hi (optional) the value and its range
+ * [lo, hi).  clear != 0 resets the records.
+ */
+fsc_status fsc_bounds_report(int32_t* site, int64_t* index, int64_t* lo, int64_t* hi, int clear);
+
 /* Static, human-readable name of a status code. */
 const char* fsc_status_string(fsc_status s);
 

@@ -25,7 +25,9 @@ __all__ = [
     "knn_graph", "embed_orthogonal", "top_eigenvectors", "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
 ]
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfsc.so")
+# FSC_LIBRARY=checked selects the build with index checks (build.py --bounds-check)
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "libfsc_checked.so" if os.environ.get("FSC_LIBRARY") == "checked" else "libfsc.so")
 
 F32, BF16, F16 = 0, 1, 2
 FILTER_NO_FALLBACK = 0x100
@@ -98,6 +100,8 @@ def lib() -> C.CDLL:
         L.fsc_power_step.argtypes = [vp, i32, i32, vp, vp, i32, vp]
         L.fsc_gather_floor.argtypes = [vp, i32, i32, vp, vp, vp]
         L.fsc_gather_floor.restype = i32
+        L.fsc_bounds_report.argtypes = [C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), i32]
+        L.fsc_bounds_report.restype = i32
         L.fsc_kmeans.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
         L.fsc_kmeans_static.argtypes = [vp, i64, i32, i32, i32, u64, i32, vp, vp, vp, C.POINTER(KmeansStats), vp]
         L.fsc_knn_graph.argtypes = [vp, i64, i32, i32, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(C.c_double), vp]
@@ -304,6 +308,19 @@ def power_step(g: Graph, l: int, z_in, z_out, store: int = F32, threads_per_row:
     _check(lib().fsc_power_step(g.handle, int(l), int(store), _ptr(z_in), _ptr(z_out), int(threads_per_row),
                                 _stream(stream)), "fsc_power_step")
     return z_out
+
+
+def bounds_report(clear: bool = False):
+    """fsc_bounds_report: None if nothing was recorded, -1 if the library has no index checks, else
+    (site, index, lo, hi) of the first out-of-range index."""
+    site, idx, lo, hi = C.c_int(0), C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _check(lib().fsc_bounds_report(C.byref(site), C.byref(idx), C.byref(lo), C.byref(hi), 1 if clear else 0),
+           "fsc_bounds_report")
+    if site.value == 0:
+        return None
+    if site.value < 0:
+        return -1
+    return site.value, idx.value, lo.value, hi.value
 
 
 def gather_floor(g: Graph, l: int, z, store: int = F32, out=None, stream=None):

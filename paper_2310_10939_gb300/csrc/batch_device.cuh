@@ -93,7 +93,7 @@ template <int LP, typename TI, int G, int U, bool W, int R>
 __device__ __forceinline__ void rows_gather(const bool (&active)[R], const long long (&row)[R], int sub,
                                             const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                             const float* __restrict__ w, const TI* zin, long long col_off,
-                                            float (&acc)[R][LP]) {
+                                            long long nz, float (&acc)[R][LP]) {
     int64_t p[R], e[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -119,6 +119,7 @@ __device__ __forceinline__ void rows_gather(const bool (&active)[R], const long 
                 const int64_t q = p[r] + (int64_t)u * G;
                 const bool ok = live[r] && q < e[r];
                 j[r][u] = ok ? (long long)__ldg(col + q) - col_off : -1;
+                if (ok && !in_range(j[r][u], 0, nz, BS_GATHER)) j[r][u] = -1;
                 if (W) wv[r][u] = ok ? __ldg(w + q) : 0.f;
             }
         float v[R][U][LP];
@@ -190,7 +191,7 @@ __device__ void power_block(const BatchGraph& g, const BatchArgs& a, TS* zA, TS*
                 act[r] = row[r] < g.n;
             }
             float acc[R][LP];
-            rows_gather<LP, TS, G, U, W, R>(act, row, sub, rp, a.col, a.w, zin, g.v0, acc);
+            rows_gather<LP, TS, G, U, W, R>(act, row, sub, rp, a.col, a.w, zin, g.v0, g.n, acc);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (act[r] && sub == 0) {   // the same epilogue as power_row

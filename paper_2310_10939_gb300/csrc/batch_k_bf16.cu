@@ -12,4 +12,5 @@ const void* batch_kernel_bf16(int LP, bool weighted) {
     }
 }
 
+FSC_BOUNDS_READER(batch_bf16)
 }  // namespace fsc

@@ -21,4 +21,5 @@ const void* batch_kmeans_kernel(int LP) {
     }
 }
 
+FSC_BOUNDS_READER(batch_f32)
 }  // namespace fsc

@@ -50,7 +50,7 @@ k_cheb_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ c
         const long long row = base + grp;
         const bool active = row < n;
         float acc[LP];
-        row_gather<LP, TS, G, U, W, true>(active, row, sub, rp, col, w, cur, col_off, acc);
+        row_gather<LP, TS, G, U, W, true>(active, row, sub, rp, col, w, cur, col_off, n, acc);
         if (active && sub == 0) {
             const float id = invdeg[row];
             float y[LP];
@@ -351,6 +351,8 @@ __global__ void __launch_bounds__(64) k_mlp_forward(const float* __restrict__ P,
 }
 
 static bool is_aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+FSC_BOUNDS_READER(filter)
 
 }  // namespace fsc
 

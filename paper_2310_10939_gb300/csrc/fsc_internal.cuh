@@ -26,6 +26,52 @@ enum : int {
 
 fsc_status status_from_bits(int bits);
 
+// ---- optional bounds checking (compile flag FSC_BOUNDS_CHECK) ----------------------------------
+// With the flag, an index that a kernel derives from its inputs (a column index, a label, the index
+// of a chosen centre) is tested against its range before the access it addresses; the first index
+// found outside is recorded (site, value, range) in the translation unit's record, the access is
+// skipped, and fsc_bounds_report() returns the record.  Nothing traps.  Without the flag the test
+// is the constant true and compiles away.
+enum BoundsSite : int {
+    BS_GATHER = 1,        // neighbour row of a sparse step (column index, minus the graph's first vertex)
+    BS_GATHER_WIDE = 2,   // neighbour row of the wide power step
+    BS_KPP_NEAR = 3,      // k-means++: a point's nearest-centre index
+    BS_LLOYD_LABEL = 4,   // Lloyd: a point's label
+    BS_WIDE_NEAR = 5,     // wide k-means++: a point's nearest-centre index
+    BS_WIDE_LABEL = 6,    // wide Lloyd: a point's previous label
+    BS_KPP_PICK = 7,      // k-means++: the chosen point
+};
+struct BoundsRecord {
+    int site;
+    int unused;
+    long long index, lo, hi;
+};
+#ifdef FSC_BOUNDS_CHECK
+static __device__ BoundsRecord g_bounds;   // one per translation unit
+__device__ __forceinline__ bool in_range(long long i, long long lo, long long hi, int site) {
+    if (i >= lo && i < hi) return true;
+    if (atomicCAS(&g_bounds.site, 0, site) == 0) {
+        g_bounds.index = i;
+        g_bounds.lo = lo;
+        g_bounds.hi = hi;
+    }
+    return false;
+}
+// Host reader of one translation unit's record (defined by FSC_BOUNDS_READER in that unit).
+#define FSC_BOUNDS_READER(name)                                                              \
+    cudaError_t bounds_read_##name(BoundsRecord* r, bool clear) {                           \
+        cudaError_t e = cudaMemcpyFromSymbol(r, g_bounds, sizeof(BoundsRecord));            \
+        if (e == cudaSuccess && clear) {                                                     \
+            const BoundsRecord z{};                                                          \
+            e = cudaMemcpyToSymbol(g_bounds, &z, sizeof(BoundsRecord));                      \
+        }                                                                                    \
+        return e;                                                                            \
+    }
+#else
+__device__ __forceinline__ constexpr bool in_range(long long, long long, long long, int) { return true; }
+#define FSC_BOUNDS_READER(name)
+#endif
+
 // ---- host helpers ---------------------------------------------------------------------
 struct DeviceProps {
     int device;

@@ -594,6 +594,48 @@ extern "C" fsc_status fsc_graph_info(const fsc_graph* g, fsc_graph_info_t* info)
 
 extern "C" int fsc_pad_l(int l) { return pad_l(l); }
 
+#ifdef FSC_BOUNDS_CHECK
+namespace fsc {
+cudaError_t bounds_read_spmm_f32(BoundsRecord*, bool);
+cudaError_t bounds_read_spmm_bf16(BoundsRecord*, bool);
+cudaError_t bounds_read_filter(BoundsRecord*, bool);
+cudaError_t bounds_read_batch_f32(BoundsRecord*, bool);
+cudaError_t bounds_read_batch_bf16(BoundsRecord*, bool);
+cudaError_t bounds_read_kmeans(BoundsRecord*, bool);
+cudaError_t bounds_read_kmeans_wide(BoundsRecord*, bool);
+cudaError_t bounds_read_wide(BoundsRecord*, bool);
+}  // namespace fsc
+#endif
+
+extern "C" fsc_status fsc_bounds_report(int32_t* site, int64_t* index, int64_t* lo, int64_t* hi, int clear) {
+    if (!site) return FSC_ERR_INVALID_ARG;
+#ifdef FSC_BOUNDS_CHECK
+    cudaError_t (*readers[])(BoundsRecord*, bool) = {bounds_read_spmm_f32, bounds_read_spmm_bf16, bounds_read_filter,
+                                                     bounds_read_batch_f32, bounds_read_batch_bf16, bounds_read_kmeans,
+                                                     bounds_read_kmeans_wide, bounds_read_wide};
+    *site = 0;
+    for (auto rd : readers) {
+        BoundsRecord r{};
+        const cudaError_t e = rd(&r, clear != 0);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (r.site && *site == 0) {
+            *site = r.site;
+            if (index) *index = r.index;
+            if (lo) *lo = r.lo;
+            if (hi) *hi = r.hi;
+        }
+    }
+    return FSC_OK;
+#else
+    (void)index;
+    (void)lo;
+    (void)hi;
+    (void)clear;
+    *site = -1;   // built without bounds checks
+    return FSC_OK;
+#endif
+}
+
 extern "C" fsc_status fsc_default_params(int64_t n, int k, int mode, int* l, int* t) {
     if (!l || !t || n < 1 || k < 1 || k > n || (mode != 0 && mode != 1)) return FSC_ERR_INVALID_ARG;
     if (mode == 0) {

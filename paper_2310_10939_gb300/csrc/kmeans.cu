@@ -263,7 +263,8 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
 #pragma unroll
                 for (int u = 0; u < KM_PPT; ++u) {
                     const bool in = i0 + u < n;
-                    need[u] = in && (r == 1 || old[u] * (1.0f + KPP_EPS) * (1.0f + KPP_EPS) >= s_half2[na[u]]);
+                    const bool nok = r == 1 || !in || in_range(na[u], 0, r - 1, BS_KPP_NEAR);
+                need[u] = in && (r == 1 || !nok || old[u] * (1.0f + KPP_EPS) * (1.0f + KPP_EPS) >= s_half2[na[u]]);
                 }
                 if constexpr (!kPre) {
 #pragma unroll
@@ -377,7 +378,8 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             s_chosen[r] = s_idx;
             if (b == 0) a.seeds[r] = s_idx;
         }
-        if (tid < LP) s_cent[(size_t)r * LP + tid] = tid < a.l ? a.X[(size_t)s_idx * LP + tid] : 0.f;
+        const bool pick_ok = in_range(s_idx, 0, n, BS_KPP_PICK);
+        if (tid < LP) s_cent[(size_t)r * LP + tid] = tid < a.l && pick_ok ? a.X[(size_t)s_idx * LP + tid] : 0.f;
         __syncthreads();
     }
     if (b == 0) {
@@ -563,7 +565,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                 // the tight test: the exact distance to the own centroid
                 bool settled = false;
                 float da = 0.f;
-                if (pr && act) {
+                if (pr && act && in_range(oldl, 0, k, BS_LLOYD_LABEL)) {
                     da = sqdist<LP>(xv, s_c + oldl * LP);
                     const float bnd = fmaxf(s_sep[oldl], lw);
                     settled = da * PRUNE_GROW2 < bnd * bnd;
@@ -627,7 +629,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             for (int u = 0; u < KM_PPT; ++u) {
                 bool need = i0 + u < hi;
                 float lw = 0.f;
-                if (pr && need) {
+                if (pr && need && in_range(old[u], 0, k, BS_LLOYD_LABEL)) {
                     const int ca = old[u];
                     lw = fmaxf(0.f, lbv[u] - pmax);
                     const float bnd = fmaxf(s_sep[ca], lw);
@@ -731,7 +733,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                 float x[LP];
                 load_point<LP>(a.X, i0 + u, a.l, x);
                 const int lab = a.labels[i0 + u];
-                inert += fixq(sqdist<LP>(x, s_c + lab * LP), sc.Sd);
+                if (in_range(lab, 0, k, BS_LLOYD_LABEL)) inert += fixq(sqdist<LP>(x, s_c + lab * LP), sc.Sd);
             }
         }
     }
@@ -910,6 +912,8 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     if (ef != cudaSuccess) return cuda_status(ef);
     return rc;
 }
+
+FSC_BOUNDS_READER(kmeans)
 
 // rows of 16 .. 128 floats (kmeans_wide.cu)
 fsc_status kmeans_wide(const float* emb, int n, int l, int ld, int k, uint64_t seed, int max_iter, int32_t* labels,

@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(KW_PASS) k_wkm_pass(WideKm a, int r) {
         bool need = true;
         if (r > 1) {
             dd = a.d2[i];
-            need = dd * (1.0f + KW_EPS) * (1.0f + KW_EPS) >= s_half2[a.near[i]];
+            const int na = a.near[i];
+            need = !in_range(na, 0, r - 1, BS_WIDE_NEAR) || dd * (1.0f + KW_EPS) * (1.0f + KW_EPS) >= s_half2[na];
         }
         if (need) {
             float x[LP];
@@ -309,7 +310,8 @@ __global__ void __launch_bounds__(KW_ASSIGN) k_wkm_assign(WideKm a) {
             a.labels[i] = bj;
             ++changed;
             unsigned long long* to = a.tot + (size_t)bj * (LP + 1);
-            unsigned long long* from = old >= 0 ? a.tot + (size_t)old * (LP + 1) : nullptr;
+            unsigned long long* from =
+                old >= 0 && in_range(old, 0, k, BS_WIDE_LABEL) ? a.tot + (size_t)old * (LP + 1) : nullptr;
 #pragma unroll
             for (int q = 0; q < LP; ++q) {
                 const long long v = q < a.l ? fixq(x[q], sc.Sx) : 0;
@@ -487,5 +489,7 @@ fsc_status kmeans_wide(const float* emb, int n, int l, int ld, int k, uint64_t s
     }
     return FSC_ERR_INVALID_ARG;
 }
+
+FSC_BOUNDS_READER(kmeans_wide)
 
 }  // namespace fsc

@@ -49,11 +49,12 @@ __device__ __forceinline__ void load_z(const T* p, float (&v)[LP]) {
 
 // sum_j w_ij z_j of one row, computed by the G lanes `sub` = 0..G-1 of a group and reduced with
 // full-warp shuffles (every lane of the warp must call it).  `row` indexes rp; column ids are
-// shifted by col_off to index zin.  After the call every lane of the group holds the sum.
+// shifted by col_off to index zin, which has nz rows.  After the call every lane of the group holds
+// the sum.
 template <int LP, typename TI, int G, int U, bool W, bool NC>
 __device__ __forceinline__ void row_gather(bool active, long long row, int sub, const int64_t* __restrict__ rp,
                                            const int32_t* __restrict__ col, const float* __restrict__ w,
-                                           const TI* zin, long long col_off, float (&acc)[LP]) {
+                                           const TI* zin, long long col_off, long long nz, float (&acc)[LP]) {
 #pragma unroll
     for (int c = 0; c < LP; ++c) acc[c] = 0.f;
     if (active) {
@@ -66,6 +67,7 @@ __device__ __forceinline__ void row_gather(bool active, long long row, int sub, 
                 const int64_t q = p + (int64_t)u * G;
                 const bool ok = q < e;
                 j[u] = ok ? (long long)__ldg(col + q) - col_off : -1;
+                if (ok && !in_range(j[u], 0, nz, BS_GATHER)) j[u] = -1;
                 if (W) wv[u] = ok ? __ldg(w + q) : 0.f;
             }
             float v[U][LP];
@@ -96,9 +98,9 @@ template <int LP, typename TI, typename TO, int G, int U, bool W, bool NC>
 __device__ __forceinline__ bool power_row(bool active, long long row, int sub, const int64_t* __restrict__ rp,
                                           const int32_t* __restrict__ col, const float* __restrict__ w,
                                           const float* __restrict__ invdeg, const TI* zin, TO* zout,
-                                          long long col_off, const float (&scale)[LP], float (&y)[LP]) {
+                                          long long col_off, long long nz, const float (&scale)[LP], float (&y)[LP]) {
     float acc[LP];
-    row_gather<LP, TI, G, U, W, NC>(active, row, sub, rp, col, w, zin, col_off, acc);
+    row_gather<LP, TI, G, U, W, NC>(active, row, sub, rp, col, w, zin, col_off, nz, acc);
     if (active && sub == 0) {
         float self[LP];
         load_z<LP, TI, NC>(zin + (size_t)row * LP, self);
@@ -145,7 +147,8 @@ k_power_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ 
     for (long long base = warp * RPW; base < n; base += nwarps * RPW) {
         const long long row = base + grp;
         float y[LP];
-        if (power_row<LP, TI, TO, G, U, W, true>(row < n, row, sub, rp, col, w, invdeg, zin, zout, col_off, scale, y)) {
+        if (power_row<LP, TI, TO, G, U, W, true>(row < n, row, sub, rp, col, w, invdeg, zin, zout, col_off, n, scale,
+                                                  y)) {
 #pragma unroll
             for (int c = 0; c < LP; ++c) cmx[c] = fmaxf(cmx[c], fabsf(y[c]));
         }

@@ -9,4 +9,5 @@ cudaError_t launch_step_bf16(int LP, int G, bool weighted, const StepArgs& a, cu
 cudaError_t launch_step_bf16_to_f32(int LP, int G, bool weighted, const StepArgs& a, cudaStream_t s) {
     return launch_step_any<__nv_bfloat16, float>(LP, G, weighted, a, s);
 }
+FSC_BOUNDS_READER(spmm_bf16)
 }  // namespace fsc

@@ -54,8 +54,12 @@ k_power_step_wide(int n, const int64_t* __restrict__ rp, const int32_t* __restri
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int src = q + u < cnt ? q + u : q;
-                    const int j = __shfl_sync(gmask, jl, src, L);
+                    int j = __shfl_sync(gmask, jl, src, L);
                     wq[u] = q + u < cnt ? (W ? __shfl_sync(gmask, wl, src, L) : 1.f) : 0.f;
+                    if (!in_range(j, 0, n, BS_GATHER_WIDE)) {
+                        j = 0;
+                        wq[u] = 0.f;
+                    }
                     v[u] = __ldg(reinterpret_cast<const float4*>(zin + (size_t)j * LP) + sub);
                 }
 #pragma unroll
@@ -554,5 +558,7 @@ fsc_status ritz_wide(fsc_graph* g, int l, float* emb, double* values, cudaStream
     if (ef != cudaSuccess) return cuda_status(ef);
     return FSC_OK;
 }
+
+FSC_BOUNDS_READER(wide)
 
 }  // namespace fsc
