@@ -44,6 +44,8 @@ struct KppArgs {
     int* tfl[2];         // per tile: the d2 buffer holding its D^2 after round r is tfl[r & 1][tile]
     float* tcen;         // per tile: centre of its points (LP floats)
     float* trad;         // per tile: largest distance of its points from that centre, widened
+    float* tlb;          // per tile: lower bound on its points' distances to the centres it was carried past
+    float* lb2;          // per point: lower bound on its distance to every chosen centre but its nearest
     unsigned* amax;      // max |x| (float bits), output for the Lloyd launch
     int* near;           // per point: index (selection order) of its nearest chosen centre
     int64_t* seeds;
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                 a.trad[tile] = sqrtf(r) * (1.0f + KPP_EPS);
             }
             if (tid < LP) a.tcen[tile * LP + tid] = s_tm[tid];
+            if (tid == 0) a.tlb[tile] = __int_as_float(0x7f800000);   // +inf
             __syncthreads();
         }
 #pragma unroll
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     if (tid < LP) s_cent[tid] = tid < a.l ? a.X[(size_t)s_chosen[0] * LP + tid] : 0.f;
     __syncthreads();
 
-    for (int r = 1; r < a.k; ++r) {
+    for (int r = 1; r <= a.k; ++r) {
         const float* s_c = s_cent + (size_t)(r - 1) * LP;   // the centre chosen last round
         // squared half-distances from the new centre to the earlier ones, shrunk by the margin
         for (int j = tid; j < r - 1; j += KM_THREADS) {
@@ -178,14 +181,17 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         int* fl = a.tfl[r & 1];
         const int* fp = a.tfl[(r + 1) & 1];         // after round r - 1
         // A tile the new centre cannot reach (the rule above KPP_EPS) keeps its state.
-        auto far_tile = [&](long long t) -> bool {
+        // dcr receives |c - m|, shrunk, minus the tile's radius: a lower bound on the distance from
+        // any point of the tile to the new centre.
+        auto far_tile = [&](long long t, float& dcr) -> bool {
             if (r == 1) return false;
             float mc[LP];
 #pragma unroll
             for (int c = 0; c < LP; ++c) mc[c] = __ldcg(a.tcen + t * LP + c);
             const float dc = sqrtf(sqdist<LP>(mc, s_c));
             const float dmax = __uint_as_float(__ldcg(dp + t));
-            return dc * (1.0f - KPP_EPS) - __ldcg(a.trad + t) > sqrtf(dmax) * (1.0f + KPP_EPS);
+            dcr = dc * (1.0f - KPP_EPS) - __ldcg(a.trad + t);
+            return dcr > sqrtf(dmax) * (1.0f + KPP_EPS);
         };
         // ---- phase A: D^2 update.  Tiles of KM_TILE points are dealt round-robin (block b takes
         // b, b + G, ...): the points that cannot skip the new centre are that centre's
@@ -206,9 +212,12 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             bool live = false;
             if (q < mytiles) {
                 const long long t = b + q * G;
-                if (!far_tile(t)) {
+                float dcr = 0.f;
+                if (!far_tile(t, dcr)) {
                     live = true;
                 } else {
+                    // every point of the tile is at least dcr from the new centre
+                    a.tlb[t] = fminf(a.tlb[t], fmaxf(0.f, dcr) * (1.0f - KPP_EPS));
                     tt[t] = __ldcg(tp + t);
                     tz[t] = 0;
                     dm[t] = __ldcg(dp + t);
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             __syncthreads();
             const int nlive = s_nlive;
             auto live_tile = [&](int j) -> long long { return j < nlive ? b + (q0 + s_live[j]) * G : ntiles; };
-            float old_n[KM_PPT];
+            float old_n[KM_PPT], lb_n[KM_PPT];
             int na_n[KM_PPT];
             float x_n[KM_PPT][LP];
             long long tile = live_tile(0);
@@ -232,6 +241,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                 const long long i = tile * KM_TILE + (long long)KM_PPT * tid + u;
                 old_n[u] = (r > 1 && i < n) ? a.d2[src_n][i] : 0.f;
                 na_n[u] = (r > 1 && i < n) ? a.near[i] : 0;
+                lb_n[u] = (r > 1 && i < n) ? a.lb2[i] : 0.f;
                 if constexpr (kPre) {
                     if (i < n) load_point<LP>(a.X, i, a.l, x_n[u]);
                 }
@@ -243,7 +253,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                 float* d2n = a.d2[src ^ 1];
                 const long long t0 = tile * KM_TILE;
                 const long long i0 = t0 + (long long)KM_PPT * tid;
-                float old[KM_PPT];
+                float old[KM_PPT], lb[KM_PPT];
                 int na[KM_PPT];
                 bool need[KM_PPT];
                 float x[KM_PPT][LP];
@@ -251,9 +261,11 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                 for (int u = 0; u < KM_PPT; ++u) {
                     old[u] = old_n[u];
                     na[u] = na_n[u];
+                    lb[u] = lb_n[u];
                     const long long inext = nxt * KM_TILE + (long long)KM_PPT * tid + u;
                     old_n[u] = (r > 1 && inext < n) ? a.d2[src_n][inext] : 0.f;
                     na_n[u] = (r > 1 && inext < n) ? a.near[inext] : 0;
+                    lb_n[u] = (r > 1 && inext < n) ? a.lb2[inext] : 0.f;
                     if constexpr (kPre) {
 #pragma unroll
                         for (int c = 0; c < LP; ++c) x[u][c] = x_n[u][c];
@@ -277,13 +289,23 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                 for (int u = 0; u < KM_PPT; ++u) {
                     if (i0 + u < n) {
                         float dd = old[u];
+                        // lower bound on the distance to the centre that is not (or no longer) the nearest
+                        float lbc = __int_as_float(0x7f800000);
                         if (need[u]) {
                             const float dn = sqdist<LP>(x[u], s_c);
                             if (r == 1 || dn < old[u]) {
                                 dd = dn;
                                 a.near[i0 + u] = r - 1;
+                                if (r > 1) lbc = sqrtf(old[u]);
+                            } else {
+                                lbc = sqrtf(dn);
                             }
+                        } else {   // |x - c| >= |c - c_a| - |x - c_a| (the skip's own margins kept)
+                            lbc = 2.0f * sqrtf(s_half2[na[u]]) - sqrtf(old[u]) * (1.0f + KPP_EPS);
                         }
+                        const float lbn = fminf(r == 1 ? __int_as_float(0x7f800000) : lb[u],
+                                                fmaxf(0.f, lbc) * (1.0f - KPP_EPS));
+                        if (r == 1 || lbn < lb[u]) a.lb2[i0 + u] = lbn;
                         d2n[i0 + u] = dd;
                         v += fixq(dd, sc.Sd);
                         dmx = fmaxf(dmx, dd);
@@ -305,6 +327,9 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             }
             __syncthreads();   // s_live is rewritten by the next chunk
         }
+        // after the last pick one more pass (r = k) folds it into D^2 and the nearest centres, which
+        // Lloyd's first assignment then reads; no selection follows it
+        if (r == a.k) break;
         if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
 
         // ---- selection (identical in every block, exact integer arithmetic).  The tile: every
@@ -412,6 +437,17 @@ struct LloydArgs {
     float* lbound;       // per point: lower bound on the distance to every other centroid (pruning)
     float* ubound;       // per point: upper bound on the distance to its own centroid (pruning)
     int prune;           // 1: skip the k-way scan of points whose bounds prove the label unchanged
+    // The first assignment from the seeding (seeded = 1): each point's nearest of the k chosen
+    // centres (near),
+    // its D^2 (in the buffer dfl[tile] names) and a lower bound on the distance to every other centre
+    // (min of lb2 and the tile's tlb), instead of a k-way scan.  (d2s0 / d2s1: the two D^2 buffers.)
+    int seeded;
+    const int* near;
+    const float* d2s0;
+    const float* d2s1;
+    const int* dfl;
+    const float* lb2;
+    const float* tlb;
     KmDevStats* st;
     GridBarrier* bar;
     int* status;
@@ -481,6 +517,9 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
 
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
+    // a seeding that stopped on an error (a barrier timeout) left its per-point results
+    // unwritten: report its status and leave
+    if (*reinterpret_cast<volatile int*>(a.status) != 0) return;
     // tiles of KM_TILE points dealt round-robin (block b takes b, b + G, ...): the points that
     // need the k-way scan or change cluster sit where planted clusters meet, a contiguous vertex
     // range, and dealing spreads them over the blocks
@@ -572,7 +611,20 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                 }
                 float best = __int_as_float(0x7f800000), sec = __int_as_float(0x7f800000);
                 int bj = 0;
-                if (__any_sync(0xffffffffu, act && !settled)) {
+                float lbs = 0.f;
+                const bool seeded1 = it == 1 && a.seeded;
+                if (seeded1) {
+                    // k-means++ already found each point's nearest centre (strict '<' in index
+                    // order over the same float32 distances): the scan's answer, without the scan
+                    if (act) {
+                        const long long tl = i / KM_TILE;
+                        best = ((__ldcg(a.dfl + tl) & 1) ? a.d2s1 : a.d2s0)[i];
+                        bj = a.near[i];
+                        if (!in_range(bj, 0, k, BS_LLOYD_LABEL)) bj = 0;
+                        bj = min(max(bj, 0), k - 1);   // memory safety whatever the seeding left
+                        lbs = fminf(a.lb2[i], __ldcg(a.tlb + tl));
+                    }
+                } else if (__any_sync(0xffffffffu, act && !settled)) {
 #pragma unroll 4
                     for (int j = 0; j < k; ++j) {
                         const float d = sqdist<LP>(xv, s_c + j * LP);
@@ -590,8 +642,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                         a.lbound[i] = lw;
                         a.ubound[i] = sqrtf(da) * (1.0f + PRUNE_EPS);
                     } else {
-                        lloyd_commit<LP>(a, i, xv, oldl, bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), it == 1, sc, sl,
-                                         my_tab, inert, changed);
+                        lloyd_commit<LP>(a, i, xv, oldl, bj, best, seeded1 ? lbs : sqrtf(sec) * (1.0f - PRUNE_EPS),
+                                         it == 1, sc, sl, my_tab, inert, changed);
                         if (a.prune) a.ubound[i] = sqrtf(best) * (1.0f + PRUNE_EPS);
                     }
                 }
@@ -759,7 +811,7 @@ static size_t lloyd_smem_bytes(int k, int LP, int ntab) {
 // exact totals x 3, largest D^2 x 3, buffer flags x 2; not zeroed: tile centres and radii), the
 // centroids (float64, float32), the k-means++ picks and each point's nearest chosen centre.
 struct KmLayout {
-    size_t hdr, acc, o_d2, o_tt, tt_bytes, o_tg, o_c64, o_c32, o_seed, o_near, total;
+    size_t hdr, acc, o_d2, o_tt, tt_bytes, o_tg, o_c64, o_c32, o_seed, o_near, o_lb2, total;
     size_t d2_stride, tt8, tt4;
 };
 
@@ -776,11 +828,12 @@ static KmLayout km_layout(long long n, int k, int LP) {
     size_t off = L.hdr + L.acc;
     L.o_d2 = off; off += 2 * L.d2_stride;
     L.o_tt = off; L.tt_bytes = 3 * L.tt8 + 5 * L.tt4; off += L.tt_bytes;
-    L.o_tg = off; off += up256((size_t)ntiles * LP * 4) + L.tt4;
+    L.o_tg = off; off += up256((size_t)ntiles * LP * 4) + 2 * L.tt4;
     L.o_c64 = off; off += up256((size_t)k * LP * 8);
     L.o_c32 = off; off += up256((size_t)k * LP * 4);
     L.o_seed = off; off += up256((size_t)k * 8);
     L.o_near = off; off += up256((size_t)n * 4);
+    L.o_lb2 = off; off += up256((size_t)n * 4);
     L.total = off;
     return L;
 }
@@ -797,6 +850,8 @@ static void kpp_buffers(KppArgs& ka, char* ws, const KmLayout& L, long long ntil
     for (int q = 0; q < 2; ++q) ka.tfl[q] = reinterpret_cast<int*>(t + q * L.tt4);
     ka.tcen = reinterpret_cast<float*>(ws + L.o_tg);
     ka.trad = reinterpret_cast<float*>(ws + L.o_tg + up256((size_t)ntiles * LP * 4));
+    ka.tlb = reinterpret_cast<float*>(ws + L.o_tg + up256((size_t)ntiles * LP * 4) + L.tt4);
+    ka.lb2 = reinterpret_cast<float*>(ws + L.o_lb2);
     ka.seeds = reinterpret_cast<int64_t*>(ws + L.o_seed);
     ka.near = reinterpret_cast<int*>(ws + L.o_near);
     ka.c32 = reinterpret_cast<float*>(ws + L.o_c32);
@@ -874,6 +929,13 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.lbound = ka.d2[0];          // the k-means++ D^2 buffers are free once seeding is done
         la.ubound = ka.d2[1];
         la.prune = k <= 256 ? 1 : 0;
+        la.seeded = 1;
+        la.near = ka.near;
+        la.d2s0 = ka.d2[0];
+        la.d2s1 = ka.d2[1];
+        la.dfl = ka.tfl[k & 1];   // the flags after the final pass (r = k)
+        la.lb2 = ka.lb2;
+        la.tlb = ka.tlb;
         la.st = st;
         la.bar = bar;
         la.status = call_status;
@@ -1114,6 +1176,13 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     la.lbound = ka.d2[0];
     la.ubound = ka.d2[1];
     la.prune = k <= 256 ? 1 : 0;
+    la.seeded = 1;
+    la.near = ka.near;
+    la.d2s0 = ka.d2[0];
+    la.d2s1 = ka.d2[1];
+    la.dfl = ka.tfl[k & 1];   // the flags after the final pass (r = k)
+    la.lb2 = ka.lb2;
+    la.tlb = ka.tlb;
     la.st = st;
     la.bar = bar;
     la.status = call_status;

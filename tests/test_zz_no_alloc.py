@@ -85,15 +85,15 @@ def test_static_kmeans_allocates_nothing_and_rejects_oversized_problems(torch):
 
 
 def test_static_kmeans_size_limit_edge(torch):
-    """The limit depends on n, k and ld only: with k = 64 and ld = 8 about 12 bytes per point plus
-    the per-cluster tables fit in the 16 MiB array up to about 1.39 million points."""
+    """The limit depends on n, k and ld only: with k = 64 and ld = 8 about 16 bytes per point plus
+    the per-cluster tables fit in the 16 MiB array up to about 1.04 million points."""
     import paper_2310_10939_gb300 as fsc
     L = fsc.lib()
-    fits = torch.zeros((1_380_000, 8), dtype=torch.float32, device="cuda")
+    fits = torch.zeros((1_000_000, 8), dtype=torch.float32, device="cuda")
     rc, lab, *_ = _call(L.fsc_kmeans_static, torch, fits, 8, 64, 2)
     assert rc == 0 and (lab == 0).all()          # identical points: every label is the first centre's
     del fits
-    over = torch.zeros((1_400_000, 8), dtype=torch.float32, device="cuda")
+    over = torch.zeros((1_100_000, 8), dtype=torch.float32, device="cuda")
     rc, *_ = _call(L.fsc_kmeans_static, torch, over, 8, 64, 2)
     assert rc == 10
 
