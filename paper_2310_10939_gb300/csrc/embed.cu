@@ -94,14 +94,27 @@ cudaError_t launch_init_any(int LP, int n, int l, unsigned long long seed, const
 // ---- lanes per row: explicit request > autotuned table > degree heuristic ------------------
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tune;   // (LP, store, weighted, degree bucket) -> lanes
+// (LP, store, weighted, degree bucket) -> lanes per row | unroll << 8
+std::map<std::tuple<int, int, int, int>, int> g_tune;
 int degree_bucket(double avg) { return (int)floor(2.0 * log2(avg < 1.0 ? 1.0 : avg)); }   // half octaves
 }  // namespace
 
-int tuned_threads_per_row(double avg_degree, int LP, int store, bool weighted) {
+static int tuned_code(double avg_degree, int LP, int store, bool weighted) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(std::make_tuple(LP, store, weighted ? 1 : 0, degree_bucket(avg_degree)));
     return it == g_tune.end() ? 0 : it->second;
+}
+
+int tuned_threads_per_row(double avg_degree, int LP, int store, bool weighted) {
+    return tuned_code(avg_degree, LP, store, weighted) & 0xff;
+}
+
+// The autotuned number of neighbour rows each lane keeps in flight (0: the kernel's default), for
+// calls that let the library choose the lane count.
+int tuned_unroll(const fsc_graph* g, int requested_threads, int LP, int store) {
+    if (requested_threads) return 0;
+    const double avg = g->n > 0 ? (double)g->nnz / (double)g->n : 0.0;
+    return tuned_code(avg, LP, store, g->w != nullptr) >> 8;
 }
 
 int choose_threads_per_row(const fsc_graph* g, int requested, int LP, int store) {
@@ -117,8 +130,9 @@ int choose_threads_per_row(const fsc_graph* g, int requested, int LP, int store)
 
 int choose_threads_per_row(const fsc_graph* g, int requested) { return choose_threads_per_row(g, requested, 4, 0); }
 
-// Times one power step for each lane count on scratch iterates and records the fastest for the
-// graph's (row width, storage type, weighting, degree bucket).
+// Times one power step for each (lane count, rows in flight per lane) candidate on scratch
+// iterates and records the fastest for the graph's (row width, storage type, weighting, degree
+// bucket).
 fsc_status autotune_graph(fsc_graph* g, int l, fsc_dtype store, int* best, float* best_us, cudaStream_t s) {
     const int LP = pad_l(l);
     const size_t es = store == FSC_F32 ? 4 : 2;
@@ -131,11 +145,13 @@ fsc_status autotune_graph(fsc_graph* g, int l, fsc_dtype store, int* best, float
     cudaError_t e = cudaMemsetAsync(zin, 0, bytes, s);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int bestG = 0;
+    int bestG = 0, bestU = 0;
     float bestT = 1e30f;
-    const int cands[4] = {4, 8, 16, 32};
-    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
+    const int cands[5] = {4, 4, 8, 16, 32}, unrolls[5] = {0, 3, 0, 0, 0};
+    for (int ci = 0; ci < 5 && e == cudaSuccess; ++ci) {
         StepArgs a{};
+        a.unroll = unrolls[ci];
+        a.max_row = g->max_row;
         a.n = (int)g->n;
         a.rp = g->row_ptr;
         a.col = g->col;
@@ -156,7 +172,7 @@ fsc_status autotune_graph(fsc_graph* g, int l, fsc_dtype store, int* best, float
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
         float ms = 0.f;
         if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
-        if (ms < bestT) { bestT = ms; bestG = cands[ci]; }
+        if (ms < bestT) { bestT = ms; bestG = cands[ci]; bestU = unrolls[ci]; }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -166,7 +182,7 @@ fsc_status autotune_graph(fsc_graph* g, int l, fsc_dtype store, int* best, float
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         const double avg = g->n > 0 ? (double)g->nnz / (double)g->n : 0.0;
-        g_tune[std::make_tuple(LP, (int)store, g->w ? 1 : 0, degree_bucket(avg))] = bestG;
+        g_tune[std::make_tuple(LP, (int)store, g->w ? 1 : 0, degree_bucket(avg))] = bestG | (bestU << 8);
     }
     if (best) *best = bestG;
     if (best_us) *best_us = bestT * 1000.f / 5.f;
@@ -227,6 +243,8 @@ extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed
     a.invdeg = g->invdeg;
     a.expo = expo;
     a.col_off = g->col_off;
+    a.max_row = g->max_row;
+    a.unroll = tuned_unroll(g, opts ? opts->threads_per_row : 0, LP, (int)store);
     const bool weighted = g->w != nullptr;
 
     if (store == FSC_F32) {
@@ -244,6 +262,7 @@ extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed
             a.cm_zero = (rescale && !last) ? cm + 8 * ((it + 2) % 3) : nullptr;
             a.last = last ? 1 : 0;
             FSC_CUDA(launch_step_f32(LP, G, weighted, a, s));
+            FSC_CUDA(long_rows_power(g, LP, 0, 0, a, s));
         }
     } else {
         __nv_bfloat16* wb[2];
@@ -261,6 +280,7 @@ extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed
             a.last = last ? 1 : 0;
             if (last) FSC_CUDA(launch_step_bf16_to_f32(LP, G, weighted, a, s));
             else FSC_CUDA(launch_step_bf16(LP, G, weighted, a, s));
+            FSC_CUDA(long_rows_power(g, LP, 1, last ? 0 : 1, a, s));
         }
     }
     if (opts && opts->ev_spmm_end) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_end, s));
@@ -284,10 +304,13 @@ extern "C" fsc_status fsc_power_step(const fsc_graph* g, int l, fsc_dtype store,
     a.zin = z_in;
     a.zout = z_out;
     a.col_off = g->col_off;
+    a.max_row = g->max_row;
+    a.unroll = tuned_unroll(g, threads_per_row, LP, (int)store);
     const int G = choose_threads_per_row(g, threads_per_row, LP, (int)store);
     cudaStream_t s = as_stream(stream);
     if (store == FSC_F32) FSC_CUDA(launch_step_f32(LP, G, g->w != nullptr, a, s));
     else FSC_CUDA(launch_step_bf16(LP, G, g->w != nullptr, a, s));
+    FSC_CUDA(long_rows_power(g, LP, store == FSC_F32 ? 0 : 1, store == FSC_F32 ? 0 : 1, a, s));
     return FSC_OK;
 }
 

@@ -21,7 +21,7 @@
 // c^T Gn c - 2 bn^T c + 1 (= ||sum_j c_j K_j - PX||^2 / ||PX||^2) with Adam.
 #include <math.h>
 
-#include "spmm.cuh"
+#include "longrows.cuh"
 
 namespace fsc {
 
@@ -40,7 +40,8 @@ template <int LP, typename TS, int G, int U, bool W>
 __global__ void __launch_bounds__(256)
 k_cheb_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ w,
             const float* __restrict__ invdeg, const double* __restrict__ deg, const TS* __restrict__ cur,
-            const TS* __restrict__ prev, TS* __restrict__ out, float* __restrict__ mom, long long col_off, int first) {
+            const TS* __restrict__ prev, TS* __restrict__ out, float* __restrict__ mom, long long col_off, int first,
+            long long max_row) {
     constexpr int RPW = 32 / G;
     const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G, wid = threadIdx.x >> 5;
     float s_oc = 0.f, s_oo = 0.f, s_cc = 0.f;
@@ -50,8 +51,8 @@ k_cheb_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ c
         const long long row = base + grp;
         const bool active = row < n;
         float acc[LP];
-        row_gather<LP, TS, G, U, W, true>(active, row, sub, rp, col, w, cur, col_off, n, acc);
-        if (active && sub == 0) {
+        const bool own = row_gather<LP, TS, G, U, W, true>(active, row, sub, rp, col, w, cur, col_off, n, max_row, acc);
+        if (own && sub == 0) {
             const float id = invdeg[row];
             float y[LP];
             if (first) {
@@ -113,13 +114,15 @@ struct ChebArgs {
     float* mom;
     long long col_off;
     int first;
+    long long max_row;
 };
 
 template <int LP, typename TS, int G, int U, bool W>
 static cudaError_t launch_cheb(const ChebArgs& a, int blocks, cudaStream_t s) {
     k_cheb_step<LP, TS, G, U, W><<<blocks, 256, 0, s>>>(a.n, a.rp, a.col, a.w, a.invdeg, a.deg,
                                                         static_cast<const TS*>(a.cur), static_cast<const TS*>(a.prev),
-                                                        static_cast<TS*>(a.out), a.mom, a.col_off, a.first);
+                                                        static_cast<TS*>(a.out), a.mom, a.col_off, a.first,
+                                                        a.max_row);
     return cudaGetLastError();
 }
 
@@ -142,6 +145,88 @@ static cudaError_t launch_cheb_any(int LP, int G, bool weighted, const ChebArgs&
         default: return weighted ? launch_cheb_g<8, TS, true>(G, a, blocks, s) : launch_cheb_g<8, TS, false>(G, a, blocks, s);
     }
 }
+
+// The Chebyshev step of the long rows (longrows.cu's decomposition): their segments' partial sums
+// added in order, the step's epilogue, and their moment terms summed in a fixed order by one block
+// into the launch's extra moment slot.
+template <int LP, typename TS>
+__global__ void __launch_bounds__(256)
+k_long_cheb(int64_t nl, const int64_t* __restrict__ rows, const int32_t* __restrict__ seg0,
+            const int32_t* __restrict__ nseg, const float* __restrict__ part, const float* __restrict__ invdeg,
+            const double* __restrict__ deg, const TS* __restrict__ cur, const TS* __restrict__ prev,
+            TS* __restrict__ out, float* __restrict__ mom_slot, int first) {
+    float s_oc = 0.f, s_oo = 0.f, s_cc = 0.f;
+    for (int64_t h = threadIdx.x; h < nl; h += blockDim.x) {
+        const int64_t row = rows[h];
+        float acc[LP], y[LP];
+        long_row_sum(h, seg0, nseg, part, LP, acc);
+        const float id = invdeg[row];
+        if (first) {
+#pragma unroll
+            for (int c = 0; c < LP; ++c) y[c] = id * acc[c];
+        } else {
+            float pv[LP];
+            load_row<LP, TS>(prev + (size_t)row * LP, pv);
+#pragma unroll
+            for (int c = 0; c < LP; ++c) y[c] = fmaf(2.0f * id, acc[c], -pv[c]);
+        }
+        store_row<LP, TS>(out + (size_t)row * LP, y);
+        if (mom_slot) {
+            float cv[LP];
+            load_row<LP, TS>(cur + (size_t)row * LP, cv);
+            const float d = (float)deg[row];
+#pragma unroll
+            for (int c = 0; c < LP; ++c) {
+                const float yr = to_f32(from_f32<TS>(y[c]));
+                s_oc = fmaf(d * yr, cv[c], s_oc);
+                s_oo = fmaf(d * yr, yr, s_oo);
+                s_cc = fmaf(d * cv[c], cv[c], s_cc);
+            }
+        }
+    }
+    if (mom_slot) {
+        __shared__ float s_r[3][8];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s_oc += __shfl_xor_sync(0xffffffffu, s_oc, off);
+            s_oo += __shfl_xor_sync(0xffffffffu, s_oo, off);
+            s_cc += __shfl_xor_sync(0xffffffffu, s_cc, off);
+        }
+        if (lane == 0) {
+            s_r[0][wid] = s_oc;
+            s_r[1][wid] = s_oo;
+            s_r[2][wid] = s_cc;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            float v = 0.f;
+            for (int q = 0; q < 8; ++q) v += s_r[threadIdx.x][q];
+            mom_slot[threadIdx.x] = v;
+        }
+    }
+}
+
+template <int LP, typename TS>
+static cudaError_t long_cheb_lp(const fsc_graph* g, const ChebArgs& a, float* mom_slot, cudaStream_t s) {
+    seg_partial_launch<LP, TS>(g, static_cast<const TS*>(a.cur), s);
+    k_long_cheb<LP, TS><<<1, 256, 0, s>>>(g->n_long, g->long_rows, g->long_seg0, g->long_nseg, g->seg_part, g->invdeg,
+                                          g->deg, static_cast<const TS*>(a.cur), static_cast<const TS*>(a.prev),
+                                          static_cast<TS*>(a.out), mom_slot, a.first);
+    return cudaGetLastError();
+}
+
+template <typename TS>
+static cudaError_t long_cheb(const fsc_graph* g, int LP, const ChebArgs& a, float* mom_slot, cudaStream_t s) {
+    if (g->n_long == 0) return cudaSuccess;
+    switch (LP) {
+        case 1: return long_cheb_lp<1, TS>(g, a, mom_slot, s);
+        case 2: return long_cheb_lp<2, TS>(g, a, mom_slot, s);
+        case 4: return long_cheb_lp<4, TS>(g, a, mom_slot, s);
+        default: return long_cheb_lp<8, TS>(g, a, mom_slot, s);
+    }
+}
+
 
 // ---- the MLP --------------------------------------------------------------------------------------
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
@@ -405,16 +490,20 @@ extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64
     const long long cap = (long long)device_props().num_sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    // workspace: 9 basis blocks | 4 x 3 x blocks moment sums | coefficients (16) | features (16)
-    const size_t mom_bytes = (size_t)4 * 3 * blocks * 4;
+    // workspace: 9 basis blocks | 4 x 3 x (blocks + 1) moment sums (the last slot of each launch holds
+    // the long rows' terms) | coefficients (16) | features (16)
+    const long long mslots = blocks + 1;
+    const size_t mom_bytes = (size_t)4 * 3 * mslots * 4;
     fsc_status rc = ensure_workspace(g, NCOEF * blk + mom_bytes + 256, s);
     if (rc != FSC_OK) return rc;
     char* ws = static_cast<char*>(g->ws);
     float* mom = reinterpret_cast<float*>(ws + NCOEF * blk);
     float* coeffs = reinterpret_cast<float*>(ws + NCOEF * blk + mom_bytes);
     FSC_CUDA(launch_init_any(LP, n, l, seed, g->dinv, ws, (int)store, s));
+    FSC_CUDA(cudaMemsetAsync(mom, 0, mom_bytes, s));
     if (opts && opts->ev_spmm_begin) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_begin, s));
     ChebArgs a{};
+    a.max_row = g->max_row;
     a.n = n;
     a.rp = g->row_ptr;
     a.col = g->col;
@@ -426,14 +515,22 @@ extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64
         a.cur = ws + (size_t)j * blk;
         a.prev = j > 0 ? ws + (size_t)(j - 1) * blk : nullptr;
         a.out = ws + (size_t)(j + 1) * blk;
-        a.mom = j < 4 ? mom + (size_t)j * 3 * blocks : nullptr;
+        a.mom = j < 4 ? mom + (size_t)j * 3 * mslots : nullptr;
         a.first = j == 0;
-        if (store == FSC_F32) FSC_CUDA(launch_cheb_any<float>(LP, G, g->w != nullptr, a, (int)blocks, s));
-        else if (store == FSC_F16) FSC_CUDA(launch_cheb_any<__half>(LP, G, g->w != nullptr, a, (int)blocks, s));
-        else FSC_CUDA(launch_cheb_any<__nv_bfloat16>(LP, G, g->w != nullptr, a, (int)blocks, s));
+        float* mslot = j < 4 ? mom + (size_t)j * 3 * mslots + 3 * blocks : nullptr;
+        if (store == FSC_F32) {
+            FSC_CUDA(launch_cheb_any<float>(LP, G, g->w != nullptr, a, (int)blocks, s));
+            FSC_CUDA(long_cheb<float>(g, LP, a, mslot, s));
+        } else if (store == FSC_F16) {
+            FSC_CUDA(launch_cheb_any<__half>(LP, G, g->w != nullptr, a, (int)blocks, s));
+            FSC_CUDA(long_cheb<__half>(g, LP, a, mslot, s));
+        } else {
+            FSC_CUDA(launch_cheb_any<__nv_bfloat16>(LP, G, g->w != nullptr, a, (int)blocks, s));
+            FSC_CUDA(long_cheb<__nv_bfloat16>(g, LP, a, mslot, s));
+        }
     }
     if (opts && opts->ev_spmm_end) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_end, s));
-    k_filter_coeffs<<<1, 256, 0, s>>>(mom, (int)blocks, (double)n, g->volume, g->deg_sumsq, g->deg_max,
+    k_filter_coeffs<<<1, 256, 0, s>>>(mom, (int)mslots, (double)n, g->volume, g->deg_sumsq, g->deg_max,
                                       (double)g->n_isolated, k, l, params, coeffs_override, feats_out, coeffs);
     FSC_CUDA(cudaGetLastError());
     long long cb = ((long long)n + 255) / 256;

@@ -243,6 +243,11 @@ __device__ __forceinline__ float sqdist(const float (&x)[LP], const float* __res
 
 // Row width of an l-column block: 1, 2, 4, 8 for l <= 8 (every entry point); 16, 32, 64, 128 for
 // l = 9 .. 128 (orthogonal iteration, Ritz vectors, k-means); 0 beyond.
+// Rows with more stored entries than kLongRow are summed in segments of kSegLen entries by their
+// own kernels (longrows.cu); the row-split kernels skip them.
+constexpr int64_t kLongRow = 1024;
+constexpr int64_t kSegLen = 1024;
+
 inline int pad_l(int l) {
     return l < 1 ? 0 : l == 1 ? 1 : l == 2 ? 2 : l <= 4 ? 4 : l <= 8 ? 8 : l <= 16 ? 16 : l <= 32 ? 32 : l <= 64 ? 64
                                                                                          : l <= 128 ? 128 : 0;
@@ -270,4 +275,14 @@ struct fsc_graph {
     unsigned* colmax;   // 3 x 8 unsigned
     int* expo;          // 8 ints
     long long col_off;  // subtracted from column ids (0, or the first vertex of a graph inside a batch)
+    // long rows (longrows.cu): max_row = kLongRow when there are any, else no limit
+    long long max_row = 0x7fffffffffffffffLL;
+    int64_t n_long, n_seg;
+    void* long_base;             // one allocation holding the tables below
+    int64_t* long_rows;          // the long rows, increasing
+    int32_t* long_seg0;          // per long row: its first segment
+    int32_t* long_nseg;          // per long row: its number of segments
+    int64_t* seg_lo;             // per segment: first entry
+    int64_t* seg_hi;             // per segment: one past its last entry
+    float* seg_part;             // per segment: partial sums, 8 floats
 };

@@ -12,6 +12,11 @@
 
 namespace fsc {
 
+// long rows (longrows.cu)
+cudaError_t launch_long_rows(int64_t n, const int64_t* rp, int64_t cap, unsigned long long* count, int64_t* rows,
+                             cudaStream_t s);
+fsc_status build_long_rows(fsc_graph* g, int64_t count, const int64_t* d_rows, cudaStream_t s);
+
 namespace {
 constexpr int kMaxDevices = 64;
 DeviceProps g_props[kMaxDevices];
@@ -439,16 +444,19 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     fsc_graph* g = new (std::nothrow) fsc_graph();
     if (!g) return FSC_ERR_OOM;
     memset(g, 0, sizeof(*g));
+    g->max_row = 0x7fffffffffffffffLL;
     g->device = dev;
     g->n = n;
     g->nnz = nnz;
     g->row_ptr = row_ptr;
     g->col = col_idx;
     g->w = w;
-    // one allocation: deg (n doubles) | header (256 B: volume, n_iso, status, sumsq, max bits) |
-    //                 dinv (n floats) | invdeg (n floats) | colmax 24 u32 | expo 8 int
+    // one allocation: deg (n doubles) | header (256 B: volume, n_iso, status, sumsq, max bits,
+    //                 long-row count) | dinv (n floats) | invdeg (n floats) | colmax 24 u32 | expo 8 int |
+    //                 long-row triples (at most nnz / kLongRow rows can be longer than kLongRow)
     const size_t n8 = (size_t)n * 8, n4 = ((size_t)n * 4 + 255) & ~(size_t)255;
-    const size_t bytes = n8 + 256 + 2 * n4 + 256;
+    const int64_t lcap = nnz / kLongRow + 1;
+    const size_t bytes = n8 + 256 + 2 * n4 + 256 + (size_t)lcap * 24;
     char* base = nullptr;
     cudaError_t e = pool_malloc(reinterpret_cast<void**>(&base), bytes, s);
     if (e != cudaSuccess) {
@@ -462,6 +470,7 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
         double pad2;
         double sumsq;
         unsigned long long dmax_bits;
+        unsigned long long nlong;
     };
     Header* hdr = reinterpret_cast<Header*>(base + n8);
     g->deg = reinterpret_cast<double*>(base);
@@ -469,6 +478,7 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     g->invdeg = reinterpret_cast<float*>(base + n8 + 256 + n4);
     g->colmax = reinterpret_cast<unsigned*>(base + n8 + 256 + 2 * n4);
     g->expo = reinterpret_cast<int*>(base + n8 + 256 + 2 * n4 + 128);
+    int64_t* long_list = reinterpret_cast<int64_t*>(base + n8 + 256 + 2 * n4 + 256);
     fsc_status rc = FSC_OK;
     do {
         if ((e = cudaMemsetAsync(base + n8, 0, 256, s)) != cudaSuccess) break;
@@ -518,6 +528,7 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
                                                                &hdr->status, &hdr->sumsq, &hdr->dmax_bits);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = launch_long_rows(n, row_ptr, lcap, &hdr->nlong, long_list, s)) != cudaSuccess) break;
         Header h{};
         if ((e = cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
@@ -530,6 +541,8 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
         }
         if (bits) { rc = status_from_bits(bits); break; }
+        const int64_t nlong = (int64_t)h.nlong < lcap ? (int64_t)h.nlong : lcap;
+        if (nlong > 0 && (rc = build_long_rows(g, nlong, long_list, s)) != FSC_OK) break;
         g->n_isolated = (int64_t)h.niso;
         g->volume = h.vol;
         g->deg_sumsq = h.sumsq;
@@ -538,6 +551,7 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     if (e != cudaSuccess) rc = cuda_status(e);
     if (rc != FSC_OK) {
         pool_free(base, s);
+        if (g->long_base) pool_free(g->long_base, s);
         cudaStreamSynchronize(s);
         delete g;
         return rc;
@@ -556,6 +570,7 @@ extern "C" fsc_status fsc_destroy_graph(fsc_graph* g) {
     cudaError_t e = cudaDeviceSynchronize();
     pool_free(g->ws, 0);
     pool_free(g->deg, 0);
+    if (g->long_base) pool_free(g->long_base, 0);
     cudaSetDevice(prev);
     delete g;
     return e == cudaSuccess ? FSC_OK : cuda_status(e);

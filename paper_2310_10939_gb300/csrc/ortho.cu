@@ -343,10 +343,12 @@ extern "C" fsc_status fsc_top_eigenvectors(const fsc_graph* gc, int l, int t, in
         a.w = g->w;
         a.invdeg = g->invdeg;
         a.col_off = g->col_off;
+        a.max_row = g->max_row;
         a.zin = emb;
         a.zout = g->ws;
         const int G = choose_threads_per_row(g, opts ? opts->threads_per_row : 0, LP, (int)FSC_F32);
         if ((e = launch_step_f32(LP, G, g->w != nullptr, a, s)) != cudaSuccess) break;
+        if ((e = long_rows_power(g, LP, 0, 0, a, s)) != cudaSuccess) break;
         const float* mz = static_cast<const float*>(g->ws);
         switch (LP) {
             case 1: e = ritz_lp<1>(n, l, emb, mz, g->deg, part, (int)nb, vmat, dvals, s); break;
@@ -397,12 +399,14 @@ extern "C" fsc_status fsc_embed_orthogonal(const fsc_graph* gc, int l, int t, in
         a.w = g->w;
         a.invdeg = g->invdeg;
         a.col_off = g->col_off;
+        a.max_row = g->max_row;
         const int G = choose_threads_per_row(g, opts ? opts->threads_per_row : 0, LP, (int)FSC_F32);
         for (int it = 0; it < t && e == cudaSuccess; ++it) {
             a.zin = buf[it % 2];
             a.zout = buf[(it + 1) % 2];
             a.last = 0;
             if ((e = launch_step_f32(LP, G, g->w != nullptr, a, s)) != cudaSuccess) break;
+            if ((e = long_rows_power(g, LP, 0, 0, a, s)) != cudaSuccess) break;
             if ((it + 1) % every == 0 || it == t - 1)
                 e = orthonormalize(LP, n, l, buf[(it + 1) % 2], g->deg, part, (int)nb, rinv, s);
         }

@@ -50,16 +50,20 @@ __device__ __forceinline__ void load_z(const T* p, float (&v)[LP]) {
 // sum_j w_ij z_j of one row, computed by the G lanes `sub` = 0..G-1 of a group and reduced with
 // full-warp shuffles (every lane of the warp must call it).  `row` indexes rp; column ids are
 // shifted by col_off to index zin, which has nz rows.  After the call every lane of the group holds
-// the sum.
+// the sum.  A row with more than max_row entries is left to the long-row kernels (longrows.cu):
+// returns false for it (and for an inactive row).
 template <int LP, typename TI, int G, int U, bool W, bool NC>
-__device__ __forceinline__ void row_gather(bool active, long long row, int sub, const int64_t* __restrict__ rp,
+__device__ __forceinline__ bool row_gather(bool active, long long row, int sub, const int64_t* __restrict__ rp,
                                            const int32_t* __restrict__ col, const float* __restrict__ w,
-                                           const TI* zin, long long col_off, long long nz, float (&acc)[LP]) {
+                                           const TI* zin, long long col_off, long long nz, long long max_row,
+                                           float (&acc)[LP]) {
 #pragma unroll
     for (int c = 0; c < LP; ++c) acc[c] = 0.f;
+    bool own = false;
     if (active) {
         const int64_t s = rp[row], e = rp[row + 1];
-        for (int64_t p = s + sub; p < e; p += G * U) {
+        own = e - s <= max_row;
+        for (int64_t p = s + sub; own && p < e; p += G * U) {
             long long j[U];
             float wv[U];
 #pragma unroll
@@ -90,6 +94,7 @@ __device__ __forceinline__ void row_gather(bool active, long long row, int sub, 
     for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
         for (int c = 0; c < LP; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    return own;
 }
 
 // One output row of the power step, y = scale * (z_in[row] + (1/d) sum_j w_ij z_in[j]) / 2,
@@ -98,10 +103,11 @@ template <int LP, typename TI, typename TO, int G, int U, bool W, bool NC>
 __device__ __forceinline__ bool power_row(bool active, long long row, int sub, const int64_t* __restrict__ rp,
                                           const int32_t* __restrict__ col, const float* __restrict__ w,
                                           const float* __restrict__ invdeg, const TI* zin, TO* zout,
-                                          long long col_off, long long nz, const float (&scale)[LP], float (&y)[LP]) {
+                                          long long col_off, long long nz, long long max_row,
+                                          const float (&scale)[LP], float (&y)[LP]) {
     float acc[LP];
-    row_gather<LP, TI, G, U, W, NC>(active, row, sub, rp, col, w, zin, col_off, nz, acc);
-    if (active && sub == 0) {
+    const bool own = row_gather<LP, TI, G, U, W, NC>(active, row, sub, rp, col, w, zin, col_off, nz, max_row, acc);
+    if (own && sub == 0) {
         float self[LP];
         load_z<LP, TI, NC>(zin + (size_t)row * LP, self);
         const float id = invdeg[row];
@@ -118,7 +124,7 @@ __global__ void __launch_bounds__(256)
 k_power_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ w,
              const float* __restrict__ invdeg, const TI* __restrict__ zin, TO* __restrict__ zout,
              const unsigned* __restrict__ cm_in, unsigned* __restrict__ cm_out, unsigned* __restrict__ cm_zero,
-             int* __restrict__ expo, int last, long long col_off) {
+             int* __restrict__ expo, int last, long long col_off, long long max_row) {
     static_assert(32 % G == 0, "G must divide the warp");
     constexpr int RPW = 32 / G;
     __shared__ unsigned s_cm[LP];
@@ -147,8 +153,8 @@ k_power_step(int n, const int64_t* __restrict__ rp, const int32_t* __restrict__ 
     for (long long base = warp * RPW; base < n; base += nwarps * RPW) {
         const long long row = base + grp;
         float y[LP];
-        if (power_row<LP, TI, TO, G, U, W, true>(row < n, row, sub, rp, col, w, invdeg, zin, zout, col_off, n, scale,
-                                                  y)) {
+        if (power_row<LP, TI, TO, G, U, W, true>(row < n, row, sub, rp, col, w, invdeg, zin, zout, col_off, n, max_row,
+                                                  scale, y)) {
 #pragma unroll
             for (int c = 0; c < LP; ++c) cmx[c] = fmaxf(cmx[c], fabsf(y[c]));
         }
@@ -180,6 +186,8 @@ struct StepArgs {
     int* expo;
     int last;
     long long col_off;   // subtracted from column ids (graphs that are a slice of a larger CSR)
+    long long max_row = 0x7fffffffffffffffLL;   // rows with more entries are left to longrows.cu
+    int unroll = 0;      // neighbour rows in flight per lane: 0 = the default for the lane count, or 3 with 4 lanes
 };
 
 template <int LP, typename TI, typename TO, int G, int U, bool W>
@@ -198,14 +206,14 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, 256, 0, s>>>(a.n, a.rp, a.col, a.w, a.invdeg, static_cast<const TI*>(a.zin),
                                          static_cast<TO*>(a.zout), a.cm_in, a.cm_out, a.cm_zero, a.expo, a.last,
-                                         a.col_off);
+                                         a.col_off, a.max_row);
     return cudaGetLastError();
 }
 
 template <int LP, typename TI, typename TO, bool W>
 cudaError_t launch_step_g(int G, const StepArgs& a, cudaStream_t s) {
     switch (G) {
-        case 4: return launch_step<LP, TI, TO, 4, 4, W>(a, s);
+        case 4: return a.unroll == 3 ? launch_step<LP, TI, TO, 4, 3, W>(a, s) : launch_step<LP, TI, TO, 4, 4, W>(a, s);
         case 8: return launch_step<LP, TI, TO, 8, 4, W>(a, s);
         case 16: return launch_step<LP, TI, TO, 16, 2, W>(a, s);
         case 32: return launch_step<LP, TI, TO, 32, 2, W>(a, s);
@@ -228,5 +236,8 @@ cudaError_t launch_step_any(int LP, int G, bool weighted, const StepArgs& a, cud
 cudaError_t launch_step_f32(int LP, int G, bool weighted, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_bf16(int LP, int G, bool weighted, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_bf16_to_f32(int LP, int G, bool weighted, const StepArgs& a, cudaStream_t s);
+// The long rows of g after a row-split power step with the same arguments (longrows.cu); store_in /
+// store_out 0 = float32, 1 = bfloat16.  Nothing to do for a graph without long rows.
+cudaError_t long_rows_power(const fsc_graph* g, int LP, int store_in, int store_out, const StepArgs& a, cudaStream_t s);
 
 }  // namespace fsc
