@@ -106,6 +106,10 @@ typedef struct fsc_kmeans_stats {
  * the embedding workspace.  n must be in [1, 2^31 - 1].
  * Degrees: d(v) = sum over u != v of w(u,v) in float64; D^-1/2 of an
  * isolated vertex is taken as 0 (its embedding row is then 0).
+ * Rows with more than 1024 stored entries (hubs) are listed and cut into
+ * 1024-entry segments here; every sparse step sums a segment with one warp and
+ * a row's segments in segment order (results do not depend on scheduling), so
+ * a hub does not hold back the row-split kernels.
  * Synchronous: returns after validation; on error *out is left unchanged and
  * nothing is allocated.
  */
@@ -307,13 +311,17 @@ fsc_status fsc_cluster(const fsc_graph* g, int k, int l, int t, uint64_t seed, f
                        int32_t* labels, fsc_kmeans_stats* stats, const fsc_embed_opts* opts, void* stream);
 
 /*
- * fsc_autotune - time the lane counts of the power step (4, 8, 16, 32 lanes per row) on g.
+ * fsc_autotune - time launch shapes of the power step on g: 4 lanes per row with 4 or 3
+ * neighbour rows in flight per lane, and 8, 16, 32 lanes per row.
  *
  * No counterpart in the paper (a tuning aid).  Runs one warm-up and five timed power steps per
  * candidate on scratch iterates, records the fastest in a process-wide table keyed by (row
  * width fsc_pad_l(l), storage type, weighted or not, half-octave bucket of the average degree)
- * and returns it.  Later fsc_embed / fsc_cluster calls with threads_per_row = 0, and batch
- * plans, use the table for graphs in the same bucket.  Synchronous; allocates its scratch.
+ * and returns its lane count (*best_threads_per_row) and time.  Later fsc_embed / fsc_cluster /
+ * fsc_power_step calls with threads_per_row = 0 use the table's shape for graphs in the same
+ * bucket, batch plans its lane count.  Rows with more than 1024 entries are not timed: every
+ * sparse step splits them into 1024-entry segments summed by their own kernels (see
+ * fsc_create_graph).  Synchronous; allocates its scratch.
  */
 fsc_status fsc_autotune(const fsc_graph* g, int l, fsc_dtype store, int* best_threads_per_row, float* best_us,
                         void* stream);
