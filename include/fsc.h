@@ -57,6 +57,7 @@ typedef enum fsc_dtype {
 
 /* fsc_create_graph flags */
 #define FSC_VALIDATE_SYMMETRY 0x1u  /* also check that A is symmetric (rows must be sorted) */
+#define FSC_COPY 0x4u               /* the graph keeps its own copy of the CSR (no borrowing) */
 
 /* fsc_embed_opts.flags */
 #define FSC_EMBED_RESCALE 0x1u      /* per-column power-of-two rescale every iteration */
@@ -102,8 +103,10 @@ typedef struct fsc_kmeans_stats {
  * weights (checked only with FSC_VALIDATE_SYMMETRY, which also requires
  * increasing columns within each row).
  * The graph BORROWS row_ptr, col_idx and w: the caller keeps them alive and
- * unchanged until fsc_destroy_graph.  The library owns the degree arrays and
- * the embedding workspace.  n must be in [1, 2^31 - 1].
+ * unchanged until fsc_destroy_graph, unless flags holds FSC_COPY, in which case
+ * the graph copies them (stream-ordered, device to device) into memory it owns
+ * and the caller's arrays may be reused once the call returns.  The library owns
+ * the degree arrays and the embedding workspace.  n must be in [1, 2^31 - 1].
  * Degrees: d(v) = sum over u != v of w(u,v) in float64; D^-1/2 of an
  * isolated vertex is taken as 0 (its embedding row is then 0).
  * Rows with more than 1024 stored entries (hubs) are listed and cut into

@@ -21,7 +21,7 @@ import os
 __all__ = [
     "FscError", "Graph", "KmeansStats", "EmbedOpts", "lib", "embed", "power_step", "kmeans", "cluster",
     "default_params", "pad_l", "sync_status", "set_wait_limit_ns", "inject_barrier_stall", "status_string", "LIB_PATH",
-    "F32", "BF16", "F16", "FILTER_NO_FALLBACK", "release_cached_memory", "VALIDATE_SYMMETRY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
+    "F32", "BF16", "F16", "FILTER_NO_FALLBACK", "release_cached_memory", "VALIDATE_SYMMETRY", "COPY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "Batch", "autotune",
     "knn_graph", "embed_orthogonal", "top_eigenvectors", "kmeans_best", "partition_scores", "filter_embed", "cluster_filtered", "mlp_forward", "mlp_train_step", "load_filter_params", "NPARAM",
 ]
 
@@ -32,6 +32,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
 F32, BF16, F16 = 0, 1, 2
 FILTER_NO_FALLBACK = 0x100
 VALIDATE_SYMMETRY = 0x1
+COPY = 0x4
 EMBED_RESCALE = 0x1
 BATCH_AUTOTUNE = 0x2
 
@@ -214,22 +215,24 @@ def inject_barrier_stall(enable: bool):
 
 
 class Graph:
-    """A CSR graph on the GPU with its degrees (fsc_create_graph).  Keeps the CSR tensors alive."""
+    """A CSR graph on the GPU with its degrees (fsc_create_graph).  Keeps the CSR tensors alive, or
+    with ``copy=True`` lets the library keep its own copy (FSC_COPY) and holds no reference to them."""
 
-    def __init__(self, row_ptr, col, w=None, validate_symmetry: bool = False, stream=None):
+    def __init__(self, row_ptr, col, w=None, validate_symmetry: bool = False, stream=None, copy: bool = False):
         torch = _torch()
         _require_cuda(row_ptr, torch.int64, "row_ptr")
         _require_cuda(col, torch.int32, "col")
         if w is not None:
             _require_cuda(w, torch.float32, "w")
-        self.row_ptr, self.col, self.w = row_ptr, col, w
+        self.device = row_ptr.device
         self.n = row_ptr.numel() - 1
         self.nnz = col.numel()
         h = C.c_void_p()
-        flags = VALIDATE_SYMMETRY if validate_symmetry else 0
+        flags = (VALIDATE_SYMMETRY if validate_symmetry else 0) | (COPY if copy else 0)
         _check(lib().fsc_create_graph(self.n, self.nnz, _ptr(row_ptr), _ptr(col), _ptr(w), flags,
                                       _stream(stream), C.byref(h)), "fsc_create_graph")
         self.handle = h
+        self.row_ptr, self.col, self.w = (None, None, None) if copy else (row_ptr, col, w)
 
     @classmethod
     def from_workload(cls, g, device="cuda", **kw):
@@ -295,7 +298,7 @@ def embed(g: Graph, l: int, t: int, seed: int, store: int = F32, out=None, resca
     torch = _torch()
     lp = pad_l(l)
     if out is None:
-        out = torch.empty((g.n, max(lp, 1)), dtype=torch.float32, device=g.row_ptr.device)
+        out = torch.empty((g.n, max(lp, 1)), dtype=torch.float32, device=g.device)
     _require_cuda(out, torch.float32, "out")
     o = _opts(rescale, threads_per_row, events)
     _check(lib().fsc_embed(g.handle, int(l), int(t), int(seed) & (2**64 - 1), int(store), _ptr(out),
@@ -374,7 +377,7 @@ def embed_orthogonal(g: Graph, l: int, t: int, seed: int, every: int = 1, out=No
     returns (or fills) the n x pad_l(l) float32 embedding D^-1/2 Q."""
     torch = _torch()
     if out is None:
-        out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=g.row_ptr.device)
+        out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=g.device)
     _require_cuda(out, torch.float32, "out")
     o = _opts(False, threads_per_row, events)
     _check(lib().fsc_embed_orthogonal(g.handle, int(l), int(t), int(every), int(seed) & (2**64 - 1), _ptr(out),
@@ -388,7 +391,7 @@ def top_eigenvectors(g: Graph, l: int, t: int, seed: int, every: int = 4, out=No
     embedding n x pad_l(l) = D^-1/2 [Ritz vectors])."""
     torch = _torch()
     if out is None:
-        out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=g.row_ptr.device)
+        out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=g.device)
     _require_cuda(out, torch.float32, "out")
     vals = (C.c_double * int(l))()
     o = _opts(False, threads_per_row, events)
@@ -430,7 +433,7 @@ def cluster(g: Graph, k: int, l: int, t: int, seed: int, store: int = F32, max_i
     """fsc_cluster (Algorithm 2 end to end).  Returns (labels, stats)."""
     torch = _torch()
     if labels is None:
-        labels = torch.empty(g.n, dtype=torch.int32, device=g.row_ptr.device)
+        labels = torch.empty(g.n, dtype=torch.int32, device=g.device)
     st = KmeansStats()
     o = _opts(rescale, threads_per_row, events)
     _check(lib().fsc_cluster(g.handle, int(k), int(l), int(t), int(seed) & (2**64 - 1), int(store), int(max_iter),
@@ -557,7 +560,7 @@ def filter_embed(g: Graph, l: int, k: int, seed: int, params=None, coeffs=None, 
     """fsc_filter_embed: returns (embedding n x pad_l(l), features (16), coefficients (9)) device tensors.
     ``energy`` (optional float64 CUDA tensor of one element) receives ||p(M) X||^2 (x-space)."""
     torch = _torch()
-    dev = g.row_ptr.device
+    dev = g.device
     if out is None:
         out = torch.empty((g.n, pad_l(l)), dtype=torch.float32, device=dev)
     feats = torch.empty(16, dtype=torch.float32, device=dev)
@@ -576,7 +579,7 @@ def cluster_filtered(g: Graph, k: int, l: int, seed: int, params, store: int = F
     stats also holds the guard's report (filter_energy_ratio, filter_threshold, fallback, fallback_t)."""
     torch = _torch()
     if labels is None:
-        labels = torch.empty(g.n, dtype=torch.int32, device=g.row_ptr.device)
+        labels = torch.empty(g.n, dtype=torch.int32, device=g.device)
     st = KmeansStats()
     rep = FilterReport()
     o = _opts(False, threads_per_row, events)

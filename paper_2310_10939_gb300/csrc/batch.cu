@@ -99,6 +99,7 @@ static void batch_free(fsc_batch* b) {
 }
 
 extern "C" fsc_status fsc_batch_create(const fsc_batch_desc* d, void* stream, fsc_batch** out) {
+    NvtxRange nvtx_range("fsc_batch_create");
     if (!d || !out || d->num_graphs < 1 || !d->vertex_offset || !d->row_ptr || !d->k || !d->seed || !d->labels)
         return FSC_ERR_INVALID_ARG;
     if ((d->store != FSC_F32 && d->store != FSC_BF16) || d->max_iter < 1) return FSC_ERR_INVALID_ARG;
@@ -353,6 +354,7 @@ extern "C" fsc_status fsc_batch_create(const fsc_batch_desc* d, void* stream, fs
 }
 
 extern "C" fsc_status fsc_batch_run(fsc_batch* b, void* stream) {
+    NvtxRange nvtx_range("fsc_batch_run");
     if (!b || !b->exec) return FSC_ERR_INVALID_ARG;
     FSC_CUDA(cudaGraphLaunch(b->exec, as_stream(stream)));
     return FSC_OK;

@@ -213,6 +213,7 @@ using namespace fsc;
 
 extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed, fsc_dtype store, float* emb,
                                 const fsc_embed_opts* opts, void* stream) {
+    NvtxRange nvtx_range("fsc_embed");
     fsc_graph* g = const_cast<fsc_graph*>(gc);
     if (!g || !emb || l < 1 || l > 8 || t < 0 || (store != FSC_F32 && store != FSC_BF16)) return FSC_ERR_INVALID_ARG;
     const int LP = pad_l(l);
@@ -289,6 +290,7 @@ extern "C" fsc_status fsc_embed(const fsc_graph* gc, int l, int t, uint64_t seed
 
 extern "C" fsc_status fsc_power_step(const fsc_graph* g, int l, fsc_dtype store, const void* z_in, void* z_out,
                                      int threads_per_row, void* stream) {
+    NvtxRange nvtx_range("fsc_power_step");
     if (!g || !z_in || !z_out || z_in == z_out || l < 1 || l > 8 || (store != FSC_F32 && store != FSC_BF16))
         return FSC_ERR_INVALID_ARG;
     const int LP = pad_l(l);
@@ -316,6 +318,7 @@ extern "C" fsc_status fsc_power_step(const fsc_graph* g, int l, fsc_dtype store,
 
 extern "C" fsc_status fsc_autotune(const fsc_graph* g, int l, fsc_dtype store, int* best_threads_per_row,
                                    float* best_us, void* stream) {
+    NvtxRange nvtx_range("fsc_autotune");
     if (!g || l < 1 || l > 8 || (store != FSC_F32 && store != FSC_BF16)) return FSC_ERR_INVALID_ARG;
     return autotune_graph(const_cast<fsc_graph*>(g), l, store, best_threads_per_row, best_us, as_stream(stream));
 }

@@ -473,6 +473,7 @@ extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64
                                        const float* params, const float* coeffs_override, float* emb, float* feats_out,
                                        float* coeffs_out, double* energy_out, const fsc_embed_opts* opts,
                                        void* stream) {
+    NvtxRange nvtx_range("fsc_filter_embed");
     fsc_graph* g = const_cast<fsc_graph*>(gc);
     if (!g || !emb || l < 1 || l > 8 || k < 1 || (int64_t)k > g->n ||
         (store != FSC_F32 && store != FSC_BF16 && store != FSC_F16))
@@ -548,6 +549,7 @@ extern "C" fsc_status fsc_cluster_filtered(const fsc_graph* g, int k, int l, uin
                                            const float* params, int max_iter, int32_t* labels,
                                            fsc_kmeans_stats* stats, fsc_filter_report* report,
                                            const fsc_embed_opts* opts, void* stream) {
+    NvtxRange nvtx_range("fsc_cluster_filtered");
     if (!g || !labels || !params || l < 1 || l > 8 || k < 1 || (int64_t)k > g->n) return FSC_ERR_INVALID_ARG;
     const int LP = pad_l(l);
     cudaStream_t s = as_stream(stream);

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <cuda/atomic>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/fsc.h"
 
@@ -98,6 +99,14 @@ int kernel_occupancy(const void* fn, int threads, size_t smem);
     } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// An NVTX range for the lifetime of a C-ABI call (seen by Nsight tools; costs nothing without one).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- row vectors: LP elements of type T, loaded/stored as aligned chunks ---------------
 template <int B> struct Chunk;
@@ -285,4 +294,5 @@ struct fsc_graph {
     int64_t* seg_lo;             // per segment: first entry
     int64_t* seg_hi;             // per segment: one past its last entry
     float* seg_part;             // per segment: partial sums, 8 floats
+    void* copy_base;             // FSC_COPY: the graph's own copy of the CSR
 };

@@ -437,7 +437,8 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
                                        const float* w, uint32_t flags, void* stream, fsc_graph** out) {
     if (!out || n < 1 || n > 2147483647LL || nnz < 0 || !row_ptr || (nnz > 0 && !col_idx))
         return FSC_ERR_INVALID_ARG;
-    if (flags & ~FSC_VALIDATE_SYMMETRY) return FSC_ERR_INVALID_ARG;
+    if (flags & ~(FSC_VALIDATE_SYMMETRY | FSC_COPY)) return FSC_ERR_INVALID_ARG;
+    NvtxRange nvtx_range("fsc_create_graph");
     cudaStream_t s = as_stream(stream);
     int dev = 0;
     FSC_CUDA(cudaGetDevice(&dev));
@@ -451,6 +452,29 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     g->row_ptr = row_ptr;
     g->col = col_idx;
     g->w = w;
+    if (flags & FSC_COPY) {   // the graph's own CSR: row_ptr | col | w, each 256-byte aligned
+        const size_t brp = ((size_t)(n + 1) * 8 + 255) & ~(size_t)255, bcol = ((size_t)nnz * 4 + 255) & ~(size_t)255;
+        const size_t bw = w ? (size_t)nnz * 4 : 0;
+        char* cb = nullptr;
+        cudaError_t ce = pool_malloc(reinterpret_cast<void**>(&cb), brp + bcol + bw + 256, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(cb, row_ptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToDevice, s);
+        if (ce == cudaSuccess && nnz > 0)
+            ce = cudaMemcpyAsync(cb + brp, col_idx, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s);
+        if (ce == cudaSuccess && w && nnz > 0)
+            ce = cudaMemcpyAsync(cb + brp + bcol, w, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) {
+            if (cb) pool_free(cb, s);
+            delete g;
+            return cuda_status(ce);
+        }
+        g->copy_base = cb;
+        g->row_ptr = reinterpret_cast<const int64_t*>(cb);
+        g->col = reinterpret_cast<const int32_t*>(cb + brp);
+        g->w = w ? reinterpret_cast<const float*>(cb + brp + bcol) : nullptr;
+        row_ptr = g->row_ptr;
+        col_idx = g->col;
+        w = g->w;
+    }
     // one allocation: deg (n doubles) | header (256 B: volume, n_iso, status, sumsq, max bits,
     //                 long-row count) | dinv (n floats) | invdeg (n floats) | colmax 24 u32 | expo 8 int |
     //                 long-row triples (at most nnz / kLongRow rows can be longer than kLongRow)
@@ -460,6 +484,8 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     char* base = nullptr;
     cudaError_t e = pool_malloc(reinterpret_cast<void**>(&base), bytes, s);
     if (e != cudaSuccess) {
+        if (g->copy_base) pool_free(g->copy_base, s);
+        cudaStreamSynchronize(s);
         delete g;
         return cuda_status(e);
     }
@@ -552,6 +578,7 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     if (rc != FSC_OK) {
         pool_free(base, s);
         if (g->long_base) pool_free(g->long_base, s);
+        if (g->copy_base) pool_free(g->copy_base, s);
         cudaStreamSynchronize(s);
         delete g;
         return rc;
@@ -561,6 +588,7 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
 }
 
 extern "C" fsc_status fsc_destroy_graph(fsc_graph* g) {
+    NvtxRange nvtx_range("fsc_destroy_graph");
     if (!g) return FSC_OK;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -571,6 +599,7 @@ extern "C" fsc_status fsc_destroy_graph(fsc_graph* g) {
     pool_free(g->ws, 0);
     pool_free(g->deg, 0);
     if (g->long_base) pool_free(g->long_base, 0);
+    if (g->copy_base) pool_free(g->copy_base, 0);
     cudaSetDevice(prev);
     delete g;
     return e == cudaSuccess ? FSC_OK : cuda_status(e);

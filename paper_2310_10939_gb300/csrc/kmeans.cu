@@ -988,6 +988,7 @@ using namespace fsc;
 extern "C" fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int max_iter,
                                  int32_t* labels, double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats,
                                  void* stream) {
+    NvtxRange nvtx_range("fsc_kmeans");
     if (!emb || !labels || n < 1 || n > 2147483647LL || l < 1 || l > ld || k < 1 || (int64_t)k > n || k > 1024 ||
         max_iter < 1)
         return FSC_ERR_INVALID_ARG;
@@ -1012,6 +1013,7 @@ extern "C" fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int
 extern "C" fsc_status fsc_kmeans_best(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int n_init,
                                       int max_iter, int32_t* labels, double* centroids, int64_t* seed_idx,
                                       fsc_kmeans_stats* stats, int32_t* best_run, void* stream) {
+    NvtxRange nvtx_range("fsc_kmeans_best");
     if (n_init < 1 || n_init > 1000000 || !labels || n < 1 || n > 2147483647LL || k < 1 || l < 1 || l > 128)
         return FSC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
@@ -1064,6 +1066,7 @@ extern "C" fsc_status fsc_kmeans_best(const float* emb, int64_t n, int l, int ld
 extern "C" fsc_status fsc_cluster(const fsc_graph* g, int k, int l, int t, uint64_t seed, fsc_dtype store,
                                   int max_iter, int32_t* labels, fsc_kmeans_stats* stats, const fsc_embed_opts* opts,
                                   void* stream) {
+    NvtxRange nvtx_range("fsc_cluster");
     if (!g || !labels || l < 1 || l > 8 || k < 1 || (int64_t)k > g->n) return FSC_ERR_INVALID_ARG;
     const int LP = pad_l(l);
     cudaStream_t s = as_stream(stream);
@@ -1216,6 +1219,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
 extern "C" fsc_status fsc_kmeans_static(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed,
                                         int max_iter, int32_t* labels, double* centroids, int64_t* seed_idx,
                                         fsc_kmeans_stats* stats, void* stream) {
+    NvtxRange nvtx_range("fsc_kmeans_static");
     if (!emb || !labels || n < 1 || n > 2147483647LL || l < 1 || l > ld || k < 1 || (int64_t)k > n || k > 1024 ||
         max_iter < 1)
         return FSC_ERR_INVALID_ARG;

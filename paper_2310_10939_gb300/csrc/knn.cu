@@ -250,6 +250,7 @@ using namespace fsc;
 
 extern "C" fsc_status fsc_knn_graph(const float* points, int64_t n, int dim, int knn, int64_t* row_ptr, int32_t* col,
                                     float* w, int64_t capacity, int64_t* nnz, double* sigma, void* stream) {
+    NvtxRange nvtx_range("fsc_knn_graph");
     if (!points || !row_ptr || !col || !nnz || n < 2 || n > 2147483647LL || dim < 1 || dim > 64 || knn < 1 ||
         knn > KNN_MAX || knn >= n || capacity < 2 * n * (int64_t)knn || n * (int64_t)knn > 2147483647LL)
         return FSC_ERR_INVALID_ARG;

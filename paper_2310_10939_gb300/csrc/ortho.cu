@@ -315,6 +315,7 @@ extern "C" fsc_status fsc_embed_orthogonal(const fsc_graph* gc, int l, int t, in
 
 extern "C" fsc_status fsc_top_eigenvectors(const fsc_graph* gc, int l, int t, int every, uint64_t seed, float* emb,
                                            double* values, const fsc_embed_opts* opts, void* stream) {
+    NvtxRange nvtx_range("fsc_top_eigenvectors");
     fsc_graph* g = const_cast<fsc_graph*>(gc);
     if (!g || !emb || !values || l < 1 || l > 128 || t < 0 || every < 1) return FSC_ERR_INVALID_ARG;
     fsc_status rc = fsc_embed_orthogonal(gc, l, t, every, seed, emb, opts, stream);
@@ -366,6 +367,7 @@ extern "C" fsc_status fsc_top_eigenvectors(const fsc_graph* gc, int l, int t, in
 
 extern "C" fsc_status fsc_embed_orthogonal(const fsc_graph* gc, int l, int t, int every, uint64_t seed, float* emb,
                                            const fsc_embed_opts* opts, void* stream) {
+    NvtxRange nvtx_range("fsc_embed_orthogonal");
     fsc_graph* g = const_cast<fsc_graph*>(gc);
     if (!g || !emb || l < 1 || l > 128 || t < 0 || every < 1) return FSC_ERR_INVALID_ARG;
     if (opts && opts->flags) return FSC_ERR_INVALID_ARG;

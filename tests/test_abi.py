@@ -65,6 +65,8 @@ def test_invalid_arguments_rejected_before_any_device_work(L):
     h = ctypes.c_void_p()
     assert L.fsc_create_graph(0, 0, None, None, None, 0, None, ctypes.byref(h)) == 1
     assert L.fsc_create_graph(5, 10, None, None, None, 0, None, ctypes.byref(h)) == 1
+    rp = (ctypes.c_int64 * 6)()
+    assert L.fsc_create_graph(5, 0, rp, None, None, 0x8, None, ctypes.byref(h)) == 1   # unknown flag
     assert L.fsc_embed(None, 2, 3, 0, 0, None, None, None) == 1
     assert L.fsc_kmeans(None, 10, 2, 2, 3, 0, 10, None, None, None, None, None) == 1
     assert L.fsc_cluster(None, 2, 2, 3, 0, 0, 10, None, None, None, None) == 1
@@ -116,3 +118,12 @@ def test_c_example_recovers_disjoint_cliques(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "cliques recovered: yes" in r.stdout
+
+
+def test_binding_flags_match_the_header():
+    """The Python binding's flag constants are the header's."""
+    import re
+    text = open(os.path.join(ROOT, "include", "fsc.h")).read()
+    defs = {m.group(1): int(m.group(2), 16) for m in re.finditer(r"#define FSC_(\w+)\s+0x([0-9a-fA-F]+)u", text)}
+    for name in ("VALIDATE_SYMMETRY", "COPY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "FILTER_NO_FALLBACK"):
+        assert defs[name] == getattr(fsc, name), name

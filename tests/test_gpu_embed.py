@@ -315,3 +315,33 @@ def test_weighted_degrees_exact(torch, which):
     assert info["deg_max"] == float(ref.max())
     assert np.isclose(info["volume"], ref.sum(), rtol=1e-13)
     assert np.array_equal(G.dinv().cpu().numpy() == 0, ref == 0)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_copy_flag_graph_owns_its_csr(torch, weighted):
+    """With FSC_COPY the graph keeps its own CSR: the caller's arrays are overwritten and freed after
+    creation, and the degrees, a power step and the embedding equal those of a graph that borrows an
+    intact copy (the same kernels on the same values: bit for bit)."""
+    import paper_2310_10939_gb300 as fsc
+    g = W.knn_mixture(5000, 8, 5, 10, seed=31) if weighted else W.sbm([700] * 6, 0.03, 0.002, 31)
+    rp, col = torch.as_tensor(g.row_ptr, device="cuda"), torch.as_tensor(g.col, device="cuda")
+    w = None if g.w is None else torch.as_tensor(g.w, device="cuda")
+    Gc = fsc.Graph(rp, col, w, copy=True, validate_symmetry=True)
+    assert Gc.row_ptr is None and Gc.col is None
+    rp.fill_(0)
+    col.fill_(-1)
+    if w is not None:
+        w.fill_(float("nan"))
+    del rp, col, w
+    torch.cuda.synchronize()
+    Gb = fsc.Graph.from_workload(g)
+    assert torch.equal(Gc.degrees(), Gb.degrees())
+    assert np.array_equal(Gc.degrees().cpu().numpy(), spectral.degrees(g))
+    z = torch.randn((g.n, 4), device="cuda")
+    oc, ob = torch.empty_like(z), torch.empty_like(z)
+    fsc.power_step(Gc, 4, z, oc)
+    fsc.power_step(Gb, 4, z, ob)
+    assert torch.equal(oc, ob)
+    assert torch.equal(fsc.embed(Gc, 3, 9, 4), fsc.embed(Gb, 3, 9, 4))
+    assert rel_fro(fsc.embed(Gc, 3, 9, 4).cpu().numpy()[:, :3], spectral.embed(g, 3, 9, 4)) <= 1e-5
+    Gc.close()
