@@ -68,6 +68,7 @@ struct KppArgs {
 // its per-point state.  rho is widened when it is stored, |c - m| shrunk and sqrt(Dmax) grown by
 // KPP_EPS relative, so a carried tile is one the per-point rule would leave unchanged.
 constexpr float KPP_EPS = 1e-5f;
+constexpr int KPP_CACHE = 4;   // tile totals per thread kept in registers by the selection
 
 template <int LP>
 __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
@@ -77,12 +78,15 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     __shared__ long long s_red[KM_WARPS];
     __shared__ long long s_T, s_base, s_tile;
     __shared__ unsigned s_amax;
-    __shared__ int s_bstar, s_idx;
+    __shared__ int s_bstar, s_idx, s_src;
     __shared__ float s_tsum[KM_WARPS][LP], s_tm[LP], s_tr[KM_WARPS];
-    __shared__ int s_live[KM_THREADS], s_nlive;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
     const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
+    const long long nch = (n + KM_CHUNK - 1) / KM_CHUNK;
+    auto chunk = [&](long long sq) -> long long {   // the block's warp's sq-th chunk (see phase A)
+        return (long long)b + (long long)G * ((long long)wid + (long long)KM_WARPS * sq);
+    };
 
     // ---- phase 0: A = max |x| over the used columns (sets the fixed-point scales), and for each
     // of the block's tiles the mean of its points and their largest distance from it
@@ -193,29 +197,29 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             dcr = dc * (1.0f - KPP_EPS) - __ldcg(a.trad + t);
             return dcr > sqrtf(dmax) * (1.0f + KPP_EPS);
         };
-        // ---- phase A: D^2 update.  Tiles of KM_TILE points are dealt round-robin (block b takes
-        // b, b + G, ...): the points that cannot skip the new centre are that centre's
-        // neighbourhood, a contiguous run of vertices in a clustered graph, and dealing tiles
-        // spreads them over the blocks instead of loading one block while the others wait at the
-        // barrier.  A tile's D^2 is read from the buffer holding it and written to the other one
-        // (the selection of the previous round may still read the first).  The next tile's D^2 and
-        // nearest-centre indices load while this tile computes, and for l_pad <= 4 its points too
-        // (all of them: the skip then saves no latency, only L2 reads, and the registers of the
-        // l_pad = 8 kernel are spent).
+        // ---- phase A: D^2 update.  The points are dealt in chunks of KM_CHUNK (one warp, four
+        // consecutive points per lane): chunk c goes to block c mod G, warp (c / G) mod KM_WARPS.
+        // The points that cannot skip the new centre are its neighbourhood, a contiguous run of
+        // vertices in a clustered graph, and dealing chunks spreads them over every warp of the
+        // grid instead of loading a few blocks while the others wait at the barrier.  Each warp
+        // first tests the tiles of up to 32 of its chunks at once (one lane per chunk); the lane
+        // holding a far tile's first chunk carries the tile's state; the live chunks are then
+        // worked in order, the next one's D^2, nearest-centre indices and lower bounds (and for
+        // l_pad <= 4 its points) loading while one computes.  A tile's D^2 is read from the
+        // buffer holding it and written to the other one (the selection of the previous round
+        // may still read the first).
         constexpr bool kPre = LP <= 4;
-        // The far-tile tests of the block's tiles (b, b + G, ...) run in parallel, one tile per
-        // thread, which also carries a far tile's state; the live tiles are then worked in order
-        // from a list in shared memory.
-        const long long mytiles = (ntiles - b + G - 1) / G;
-        for (long long q0 = 0; q0 < mytiles; q0 += KM_THREADS) {
-            const long long q = q0 + tid;
+        for (long long s0 = 0; chunk(s0) < nch; s0 += 32) {
+            const long long ch_l = chunk(s0 + lane);   // this lane's chunk of the group
             bool live = false;
-            if (q < mytiles) {
-                const long long t = b + q * G;
+            int src_l = 0;                             // the buffer holding its tile's D^2
+            if (ch_l < nch) {
+                const long long t = ch_l / KM_CHUNKS_PER_TILE;
                 float dcr = 0.f;
                 if (!far_tile(t, dcr)) {
                     live = true;
-                } else {
+                    src_l = r > 1 ? __ldcg(fp + t) : 0;
+                } else if (ch_l % KM_CHUNKS_PER_TILE == 0) {
                     // every point of the tile is at least dcr from the new centre
                     a.tlb[t] = fminf(a.tlb[t], fmaxf(0.f, dcr) * (1.0f - KPP_EPS));
                     tt[t] = __ldcg(tp + t);
@@ -225,58 +229,68 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                     fl[t] = __ldcg(fp + t);
                 }
             }
-            const int incl = (int)block_scan_ll(live ? 1 : 0, s_red);
-            if (live) s_live[incl - 1] = (int)(q - q0);
-            if (tid == KM_THREADS - 1) s_nlive = incl;
-            __syncthreads();
-            const int nlive = s_nlive;
-            auto live_tile = [&](int j) -> long long { return j < nlive ? b + (q0 + s_live[j]) * G : ntiles; };
+            unsigned pend = __ballot_sync(0xffffffffu, live);
+            // loads of one live chunk's per-point state (D^2, nearest centre, lower bound)
+            auto load_state = [&](long long ch, int src, float (&old)[KM_PPT], int (&na)[KM_PPT], float (&lb)[KM_PPT],
+                                  float (&x)[KM_PPT][LP]) {
+                const long long i0 = ch * KM_CHUNK + (long long)KM_PPT * lane;
+                if (r > 1 && i0 + KM_PPT <= n) {
+                    const float4 dv = *reinterpret_cast<const float4*>(a.d2[src] + i0);
+                    const int4 nv = *reinterpret_cast<const int4*>(a.near + i0);
+                    const float4 lv = *reinterpret_cast<const float4*>(a.lb2 + i0);
+                    old[0] = dv.x; old[1] = dv.y; old[2] = dv.z; old[3] = dv.w;
+                    na[0] = nv.x; na[1] = nv.y; na[2] = nv.z; na[3] = nv.w;
+                    lb[0] = lv.x; lb[1] = lv.y; lb[2] = lv.z; lb[3] = lv.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < KM_PPT; ++u) {
+                        const bool in = r > 1 && i0 + u < n;
+                        old[u] = in ? a.d2[src][i0 + u] : 0.f;
+                        na[u] = in ? a.near[i0 + u] : 0;
+                        lb[u] = in ? a.lb2[i0 + u] : 0.f;
+                    }
+                }
+                if constexpr (kPre) {
+#pragma unroll
+                    for (int u = 0; u < KM_PPT; ++u)
+                        if (i0 + u < n) load_point<LP>(a.X, i0 + u, a.l, x[u]);
+                }
+            };
             float old_n[KM_PPT], lb_n[KM_PPT];
             int na_n[KM_PPT];
             float x_n[KM_PPT][LP];
-            long long tile = live_tile(0);
-            int src_n = (r > 1 && tile < ntiles) ? __ldcg(fp + tile) : 0;
-#pragma unroll
-            for (int u = 0; u < KM_PPT; ++u) {
-                const long long i = tile * KM_TILE + (long long)KM_PPT * tid + u;
-                old_n[u] = (r > 1 && i < n) ? a.d2[src_n][i] : 0.f;
-                na_n[u] = (r > 1 && i < n) ? a.near[i] : 0;
-                lb_n[u] = (r > 1 && i < n) ? a.lb2[i] : 0.f;
-                if constexpr (kPre) {
-                    if (i < n) load_point<LP>(a.X, i, a.l, x_n[u]);
-                }
-            }
-            for (int jl = 0; jl < nlive; ++jl) {
-                const long long nxt = live_tile(jl + 1);
+            int j = pend ? __ffs(pend) - 1 : 0;
+            int src_n = __shfl_sync(0xffffffffu, src_l, j);
+            if (pend) load_state(chunk(s0 + j), src_n, old_n, na_n, lb_n, x_n);
+            while (pend) {
+                const long long ch = chunk(s0 + j);
                 const int src = src_n;
-                src_n = (r > 1 && nxt < ntiles) ? __ldcg(fp + nxt) : 0;
-                float* d2n = a.d2[src ^ 1];
-                const long long t0 = tile * KM_TILE;
-                const long long i0 = t0 + (long long)KM_PPT * tid;
+                pend &= pend - 1;
+                const int jn = pend ? __ffs(pend) - 1 : 0;
+                src_n = __shfl_sync(0xffffffffu, src_l, jn);
                 float old[KM_PPT], lb[KM_PPT];
                 int na[KM_PPT];
-                bool need[KM_PPT];
                 float x[KM_PPT][LP];
 #pragma unroll
                 for (int u = 0; u < KM_PPT; ++u) {
                     old[u] = old_n[u];
                     na[u] = na_n[u];
                     lb[u] = lb_n[u];
-                    const long long inext = nxt * KM_TILE + (long long)KM_PPT * tid + u;
-                    old_n[u] = (r > 1 && inext < n) ? a.d2[src_n][inext] : 0.f;
-                    na_n[u] = (r > 1 && inext < n) ? a.near[inext] : 0;
-                    lb_n[u] = (r > 1 && inext < n) ? a.lb2[inext] : 0.f;
                     if constexpr (kPre) {
 #pragma unroll
                         for (int c = 0; c < LP; ++c) x[u][c] = x_n[u][c];
-                        if (inext < n) load_point<LP>(a.X, inext, a.l, x_n[u]);
                     }
                 }
+                if (pend) load_state(chunk(s0 + jn), src_n, old_n, na_n, lb_n, x_n);
+                const long long tile = ch / KM_CHUNKS_PER_TILE;
+                float* d2n = a.d2[src ^ 1];
+                const long long i0 = ch * KM_CHUNK + (long long)KM_PPT * lane;
+                bool need[KM_PPT];
 #pragma unroll
                 for (int u = 0; u < KM_PPT; ++u) {
                     const bool in = i0 + u < n;
                     const bool nok = r == 1 || !in || in_range(na[u], 0, r - 1, BS_KPP_NEAR);
-                need[u] = in && (r == 1 || !nok || old[u] * (1.0f + KPP_EPS) * (1.0f + KPP_EPS) >= s_half2[na[u]]);
+                    need[u] = in && (r == 1 || !nok || old[u] * (1.0f + KPP_EPS) * (1.0f + KPP_EPS) >= s_half2[na[u]]);
                 }
                 if constexpr (!kPre) {
 #pragma unroll
@@ -317,15 +331,14 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                 if (lane == 0) {
                     if (v) atomicAdd(reinterpret_cast<unsigned long long*>(tt + tile), (unsigned long long)v);
                     if (dmx > 0.f) atomicMax(dm + tile, __float_as_uint(dmx));
-                    if (wid == 0) {
+                    if (ch % KM_CHUNKS_PER_TILE == 0) {   // once per live tile
                         tz[tile] = 0;
                         dz[tile] = 0;
                         fl[tile] = src ^ 1;
                     }
                 }
-                tile = nxt;
+                j = jn;
             }
-            __syncthreads();   // s_live is rewritten by the next chunk
         }
         // after the last pick one more pass (r = k) folds it into D^2 and the nearest centres, which
         // Lloyd's first assignment then reads; no selection follows it
@@ -338,8 +351,19 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         // walks it.  The point: the tile's D^2 in point order, one block scan.
         const long long per = (ntiles + KM_THREADS - 1) / KM_THREADS;
         const long long q_lo = min(ntiles, per * tid), q_hi = min(ntiles, q_lo + per);
+        // the first KPP_CACHE totals of the range, and their tiles' buffer flags, stay in registers
+        // for the walk below
+        long long tcache[KPP_CACHE];
+        int fcache[KPP_CACHE];
         long long rsum = 0;
-        for (long long q = q_lo; q < q_hi; ++q) rsum += __ldcg(tt + q);
+#pragma unroll
+        for (int q = 0; q < KPP_CACHE; ++q) {
+            const bool in = q_lo + q < q_hi;
+            tcache[q] = in ? __ldcg(tt + q_lo + q) : 0;
+            fcache[q] = in ? __ldcg(fl + q_lo + q) : 0;
+            rsum += tcache[q];
+        }
+        for (long long q = q_lo + KPP_CACHE; q < q_hi; ++q) rsum += __ldcg(tt + q);
         const long long rincl = block_scan_ll(rsum, s_red);
         const long long total = s_red[KM_WARPS - 1];
         if (tid == 0) {
@@ -362,12 +386,25 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             const long long rex = rincl - rsum;
             if (rsum > 0 && rex <= T && T < rincl) {   // exactly one thread
                 long long base = rex;
-                for (long long q = q_lo; q < q_hi; ++q) {
+                bool found = false;
+#pragma unroll
+                for (int q = 0; q < KPP_CACHE; ++q) {
+                    const long long v = tcache[q];
+                    if (!found && v > 0 && base + v > T) {
+                        s_tile = q_lo + q;
+                        s_base = base;
+                        s_src = fcache[q];
+                        found = true;
+                    }
+                    if (!found) base += v;
+                }
+                for (long long q = q_lo + KPP_CACHE; !found && q < q_hi; ++q) {
                     const long long v = __ldcg(tt + q);
                     if (v > 0 && base + v > T) {
                         s_tile = q;
                         s_base = base;
-                        break;
+                        s_src = __ldcg(fl + q);
+                        found = true;
                     }
                     base += v;
                 }
@@ -375,7 +412,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             __syncthreads();
             const long long tq = s_tile;
             if (tq >= 0) {   // always (exact sums cross the target); block-uniform
-                const float* d2n = a.d2[__ldcg(fl + tq)];
+                const float* d2n = a.d2[s_src & 1];
                 const long long i0 = tq * KM_TILE + (long long)KM_PPT * tid;
                 long long qv[KM_PPT];
                 long long v = 0;
@@ -520,9 +557,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
     // a seeding that stopped on an error (a barrier timeout) left its per-point results
     // unwritten: report its status and leave
     if (*reinterpret_cast<volatile int*>(a.status) != 0) return;
-    // tiles of KM_TILE points dealt round-robin (block b takes b, b + G, ...): the points that
-    // need the k-way scan or change cluster sit where planted clusters meet, a contiguous vertex
-    // range, and dealing spreads them over the blocks
+    // tiles of KM_TILE points, dealt round-robin (block b takes b, b + G, ...) in the final
+    // inertia pass
     const long long ntl = (n + KM_TILE - 1) / KM_TILE;
     const int G = gridDim.x;
     const Scales sc = scales_for(__uint_as_float(__ldcg(a.amax)), n, a.l);
@@ -547,26 +583,33 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
         const bool pr = a.prune && it > 1;
         for (size_t q = tid; q < (size_t)ntab * rowlen; q += KM_THREADS) s_tab[q] = 0ull;
         if (pr) {
-            for (int q = tid; q < k; q += KM_THREADS) reinterpret_cast<unsigned*>(s_sep)[q] = 0x7f800000u;   // +inf
-        }
-        __syncthreads();
-        if (pr) {
-            // half the distance of each centroid to its nearest other centroid
-            for (int q = tid; q < k * k; q += KM_THREADS) {
-                const int j = q / k, jj = q % k;
-                if (jj > j) {
-                    float cj[LP];
+            // half the distance of each centroid to its nearest other centroid.  Centroid j's
+            // candidates are dealt into `parts` interleaved subsets, one thread each, whose minima
+            // one thread per centroid then combines (no shared atomics; (a - b)^2 = (b - a)^2
+            // exactly, so d(j, jj) = d(jj, j) and the result equals a scan over pairs)
+            const int parts = k >= KM_THREADS ? 1 : KM_THREADS / k;
+            float* s_part = s_qlw;   // the point queues are idle until phase A
+            for (int q = tid; q < k * parts; q += KM_THREADS) {
+                const int j = q / parts, p = q - j * parts;
+                float cj[LP];
 #pragma unroll
-                    for (int c = 0; c < LP; ++c) cj[c] = s_c[j * LP + c];
-                    const unsigned d = __float_as_uint(sqdist<LP>(cj, s_c + jj * LP));
-                    atomicMin(reinterpret_cast<unsigned*>(s_sep) + j, d);
-                    atomicMin(reinterpret_cast<unsigned*>(s_sep) + jj, d);
-                }
+                for (int c = 0; c < LP; ++c) cj[c] = s_c[j * LP + c];
+                float m = __int_as_float(0x7f800000);   // +inf: k = 1 has no other centroid
+                for (int jj = p; jj < k; jj += parts)
+                    if (jj != j) m = fminf(m, sqdist<LP>(cj, s_c + jj * LP));
+                if (parts == 1) s_sep[j] = 0.5f * sqrtf(m) * (1.0f - PRUNE_EPS);
+                else s_part[q] = m;
             }
             __syncthreads();
-            for (int q = tid; q < k; q += KM_THREADS) s_sep[q] = 0.5f * sqrtf(s_sep[q]) * (1.0f - PRUNE_EPS);
-            __syncthreads();
+            if (parts > 1) {
+                for (int j = tid; j < k; j += KM_THREADS) {
+                    float m = s_part[j * parts];
+                    for (int p = 1; p < parts; ++p) m = fminf(m, s_part[j * parts + p]);
+                    s_sep[j] = 0.5f * sqrtf(m) * (1.0f - PRUNE_EPS);
+                }
+            }
         }
+        __syncthreads();
         const float pmax = pr ? __uint_as_float(s_pmax) * (1.0f + PRUNE_EPS) : 0.f;
         long long inert = 0;
         int changed = 0;
@@ -578,6 +621,14 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
         // fails, so no lane idles behind a neighbour's scan.  Centroid sums are exact integers,
         // so which lane adds a point changes no result.  The next tile's labels and bounds load
         // while this tile is settled.
+        // Points are dealt in chunks of KM_CHUNK (one warp, four consecutive points per lane):
+        // chunk c goes to block c mod G, warp (c / G) mod KM_WARPS, so the chunks of any vertex
+        // range (a planted cluster's, whose boundary points all need the scan) spread over every
+        // block instead of loading a few
+        const long long nch = (n + KM_CHUNK - 1) / KM_CHUNK;
+        auto chunk = [&](long long sq) -> long long {
+            return (long long)b + (long long)G * ((long long)wid + (long long)KM_WARPS * sq);
+        };
         Slot<LP> sl[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -611,20 +662,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                 }
                 float best = __int_as_float(0x7f800000), sec = __int_as_float(0x7f800000);
                 int bj = 0;
-                float lbs = 0.f;
-                const bool seeded1 = it == 1 && a.seeded;
-                if (seeded1) {
-                    // k-means++ already found each point's nearest centre (strict '<' in index
-                    // order over the same float32 distances): the scan's answer, without the scan
-                    if (act) {
-                        const long long tl = i / KM_TILE;
-                        best = ((__ldcg(a.dfl + tl) & 1) ? a.d2s1 : a.d2s0)[i];
-                        bj = a.near[i];
-                        if (!in_range(bj, 0, k, BS_LLOYD_LABEL)) bj = 0;
-                        bj = min(max(bj, 0), k - 1);   // memory safety whatever the seeding left
-                        lbs = fminf(a.lb2[i], __ldcg(a.tlb + tl));
-                    }
-                } else if (__any_sync(0xffffffffu, act && !settled)) {
+                if (__any_sync(0xffffffffu, act && !settled)) {
 #pragma unroll 4
                     for (int j = 0; j < k; ++j) {
                         const float d = sqdist<LP>(xv, s_c + j * LP);
@@ -642,8 +680,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                         a.lbound[i] = lw;
                         a.ubound[i] = sqrtf(da) * (1.0f + PRUNE_EPS);
                     } else {
-                        lloyd_commit<LP>(a, i, xv, oldl, bj, best, seeded1 ? lbs : sqrtf(sec) * (1.0f - PRUNE_EPS),
-                                         it == 1, sc, sl, my_tab, inert, changed);
+                        lloyd_commit<LP>(a, i, xv, oldl, bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), it == 1, sc, sl,
+                                         my_tab, inert, changed);
                         if (a.prune) a.ubound[i] = sqrtf(best) * (1.0f + PRUNE_EPS);
                     }
                 }
@@ -651,44 +689,159 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             __syncwarp();
             qn = 0;
         };
-        int old_n[KM_PPT];
-        float lbv_n[KM_PPT], ubv_n[KM_PPT];
-        auto fetch = [&](long long tile) {
-            const long long i0 = tile * KM_TILE + (long long)KM_PPT * tid;
+        if (it == 1 && a.seeded) {
+            // The first assignment is the seeding's (near, D^2 and the lower bound come from
+            // k-means++; see LloydArgs), and every label changes (from -1, the launcher's fill).
+            // Every thread settles its own four points directly; their coordinates join the
+            // centroid sums through warp-aggregated adds (table_add_grouped: one shared add per
+            // label present in the warp), since labels alternate within a tile and per-lane run
+            // caches would evict on most points.
+            const bool lab16 = (reinterpret_cast<uintptr_t>(a.labels) & 15) == 0;
+            long long ch = chunk(0);
+            int fl_n = ch < nch ? __ldcg(a.dfl + ch / KM_CHUNKS_PER_TILE) : 0;
+            for (long long sq = 0; ch < nch; ch = chunk(++sq)) {
+                const long long i0 = ch * KM_CHUNK + (long long)KM_PPT * lane;
+                const long long tile = ch / KM_CHUNKS_PER_TILE;   // the seeding's tile
+                const bool full4 = i0 + KM_PPT <= n;
+                const float* d2s = (fl_n & 1) ? a.d2s1 : a.d2s0;
+                const float tl = __ldcg(a.tlb + tile);
+                const long long chn = chunk(sq + 1);
+                fl_n = chn < nch ? __ldcg(a.dfl + chn / KM_CHUNKS_PER_TILE) : 0;
+                int nr[KM_PPT];
+                float dd[KM_PPT], lbs[KM_PPT], x[KM_PPT][LP];
+                if (full4) {
+                    const int4 v = *reinterpret_cast<const int4*>(a.near + i0);
+                    const float4 dv = *reinterpret_cast<const float4*>(d2s + i0);
+                    const float4 lv = *reinterpret_cast<const float4*>(a.lb2 + i0);
+                    nr[0] = v.x; nr[1] = v.y; nr[2] = v.z; nr[3] = v.w;
+                    dd[0] = dv.x; dd[1] = dv.y; dd[2] = dv.z; dd[3] = dv.w;
+                    lbs[0] = lv.x; lbs[1] = lv.y; lbs[2] = lv.z; lbs[3] = lv.w;
+                } else {
 #pragma unroll
-            for (int u = 0; u < KM_PPT; ++u) {
-                const bool in = tile < ntl && i0 + u < n;
-                old_n[u] = in ? a.labels[i0 + u] : 0;
-                lbv_n[u] = in && pr ? a.lbound[i0 + u] : 0.f;
-                ubv_n[u] = in && pr ? a.ubound[i0 + u] : 0.f;
+                    for (int u = 0; u < KM_PPT; ++u) {
+                        const bool in = i0 + u < n;
+                        nr[u] = in ? a.near[i0 + u] : 0;
+                        dd[u] = in ? d2s[i0 + u] : 0.f;
+                        lbs[u] = in ? a.lb2[i0 + u] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    if (i0 + u < n) load_point<LP>(a.X, i0 + u, a.l, x[u]);
+                    else
+#pragma unroll
+                        for (int c = 0; c < LP; ++c) x[u][c] = 0.f;
+                }
+                float lbo[KM_PPT], ubo[KM_PPT];
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    const bool in = i0 + u < n;
+                    int bj = nr[u];
+                    if (in && !in_range(bj, 0, k, BS_LLOYD_LABEL)) bj = 0;
+                    bj = min(max(bj, 0), k - 1);   // memory safety whatever the seeding left
+                    nr[u] = bj;
+                    table_add_grouped<LP>(in ? bj : -1, x[u], sc.Sx, my_tab);
+                    if (in) {
+                        inert += fixq(dd[u], sc.Sd);
+                        ++changed;
+                    }
+                    lbo[u] = fminf(lbs[u], tl);
+                    ubo[u] = sqrtf(dd[u]) * (1.0f + PRUNE_EPS);
+                }
+                // lbound and ubound share the D^2 buffers: these points' D^2 were read above
+                if (full4) {
+                    if (lab16) *reinterpret_cast<int4*>(a.labels + i0) = make_int4(nr[0], nr[1], nr[2], nr[3]);
+                    else
+#pragma unroll
+                        for (int u = 0; u < KM_PPT; ++u) a.labels[i0 + u] = nr[u];
+                    if (a.prune) {
+                        *reinterpret_cast<float4*>(a.lbound + i0) = make_float4(lbo[0], lbo[1], lbo[2], lbo[3]);
+                        *reinterpret_cast<float4*>(a.ubound + i0) = make_float4(ubo[0], ubo[1], ubo[2], ubo[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < KM_PPT; ++u)
+                        if (i0 + u < n) {
+                            a.labels[i0 + u] = nr[u];
+                            if (a.prune) {
+                                a.lbound[i0 + u] = lbo[u];
+                                a.ubound[i0 + u] = ubo[u];
+                            }
+                        }
+                }
+            }
+        }
+        // labels and bounds of the chunks two steps ahead load while a chunk is settled (16-byte
+        // loads where the rows allow: workspace bounds always, labels when the caller's array is
+        // 16-byte aligned)
+        const bool lab16 = (reinterpret_cast<uintptr_t>(a.labels) & 15) == 0;
+        auto fetch = [&](long long ch, int (&o)[KM_PPT], float (&lbv)[KM_PPT], float (&ubv)[KM_PPT]) {
+            const long long i0 = ch * KM_CHUNK + (long long)KM_PPT * lane;
+            if (ch < nch && i0 + KM_PPT <= n) {
+                if (lab16) {
+                    const int4 v = *reinterpret_cast<const int4*>(a.labels + i0);
+                    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < KM_PPT; ++u) o[u] = a.labels[i0 + u];
+                }
+                if (pr) {
+                    const float4 lv = *reinterpret_cast<const float4*>(a.lbound + i0);
+                    const float4 uv = *reinterpret_cast<const float4*>(a.ubound + i0);
+                    lbv[0] = lv.x; lbv[1] = lv.y; lbv[2] = lv.z; lbv[3] = lv.w;
+                    ubv[0] = uv.x; ubv[1] = uv.y; ubv[2] = uv.z; ubv[3] = uv.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < KM_PPT; ++u) lbv[u] = ubv[u] = 0.f;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    const bool in = ch < nch && i0 + u < n;
+                    o[u] = in ? a.labels[i0 + u] : 0;
+                    lbv[u] = in && pr ? a.lbound[i0 + u] : 0.f;
+                    ubv[u] = in && pr ? a.ubound[i0 + u] : 0.f;
+                }
             }
         };
-        fetch(b);
-        for (long long tile = b; tile < ntl; tile += G) {
-            const long long t0 = tile * KM_TILE, hi = min(n, t0 + KM_TILE);
-            const long long i0 = t0 + (long long)KM_PPT * tid;
+        static_assert(KM_PPT == 4, "the 16-byte loads and stores take four points");
+        int old_a[KM_PPT], old_b[KM_PPT];
+        float lbv_a[KM_PPT], ubv_a[KM_PPT], lbv_b[KM_PPT], ubv_b[KM_PPT];
+        const long long sq0 = (it == 1 && a.seeded) ? nch : 0;   // the seeded pass settled every point
+        fetch(chunk(sq0), old_a, lbv_a, ubv_a);
+        fetch(chunk(sq0 + 1), old_b, lbv_b, ubv_b);
+        for (long long sq = sq0, ch = chunk(sq0); ch < nch; ch = chunk(++sq)) {
+            const long long i0 = ch * KM_CHUNK + (long long)KM_PPT * lane;
             int old[KM_PPT];
             float lbv[KM_PPT], ubv[KM_PPT];
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
-                old[u] = old_n[u];
-                lbv[u] = lbv_n[u];
-                ubv[u] = ubv_n[u];
+                old[u] = old_a[u];
+                lbv[u] = lbv_a[u];
+                ubv[u] = ubv_a[u];
+                old_a[u] = old_b[u];
+                lbv_a[u] = lbv_b[u];
+                ubv_a[u] = ubv_b[u];
             }
-            fetch(tile + G);
-            if (qn > KM_QUEUE - KM_PPT * 32) flush();   // room for this tile's points
+            fetch(chunk(sq + 2), old_b, lbv_b, ubv_b);
+            if (qn > KM_QUEUE - KM_PPT * 32) flush();   // room for this chunk's points
+            float lw_s[KM_PPT], ub_s[KM_PPT];
+            bool set_s[KM_PPT];
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u) {
-                bool need = i0 + u < hi;
+                bool need = i0 + u < n;
                 float lw = 0.f;
+                set_s[u] = false;
+                lw_s[u] = ub_s[u] = 0.f;
                 if (pr && need && in_range(old[u], 0, k, BS_LLOYD_LABEL)) {
                     const int ca = old[u];
                     lw = fmaxf(0.f, lbv[u] - pmax);
                     const float bnd = fmaxf(s_sep[ca], lw);
                     const float ub = (ubv[u] + s_mv[ca]) * UBOUND_GROW;
                     if (ub < bnd) {
-                        a.lbound[i0 + u] = lw;
-                        a.ubound[i0 + u] = ub;
+                        set_s[u] = true;
+                        lw_s[u] = lw;
+                        ub_s[u] = ub;
                         need = false;
                     }
                 }
@@ -700,6 +853,18 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                     qlw[pos] = lw;
                 }
                 qn += __popc(m);
+            }
+            // the bounds of the points settled without their coordinates
+            if (set_s[0] && set_s[1] && set_s[2] && set_s[3]) {
+                *reinterpret_cast<float4*>(a.lbound + i0) = make_float4(lw_s[0], lw_s[1], lw_s[2], lw_s[3]);
+                *reinterpret_cast<float4*>(a.ubound + i0) = make_float4(ub_s[0], ub_s[1], ub_s[2], ub_s[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u)
+                    if (set_s[u]) {
+                        a.lbound[i0 + u] = lw_s[u];
+                        a.ubound[i0 + u] = ub_s[u];
+                    }
             }
         }
         flush();

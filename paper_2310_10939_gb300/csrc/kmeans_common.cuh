@@ -14,6 +14,8 @@ constexpr int KM_WARPS = KM_THREADS / 32;
 constexpr int KM_MAX_BLOCKS = 1024;
 constexpr int KM_PPT = 4;                          // consecutive points per thread per tile
 constexpr int KM_TILE = KM_THREADS * KM_PPT;       // points per tile (chunks are multiples of it)
+constexpr int KM_CHUNK = 32 * KM_PPT;              // points per warp chunk (Lloyd's unit of work)
+constexpr int KM_CHUNKS_PER_TILE = KM_TILE / KM_CHUNK;
 
 struct KmDevStats {
     int iterations;
@@ -172,6 +174,35 @@ __device__ __forceinline__ void slot_add(Slot<LP> (&sl)[2], int lab, const long 
 #pragma unroll
     for (int c = 0; c < LP; ++c) sl[0].s[c] += minus ? -q[c] : q[c];
     sl[0].cnt += minus ? -1 : 1;
+}
+
+// Adds one point's exact coordinates q(x) (and a count of 1) to row `key` of the warp's table, for
+// all 32 lanes at once (key < 0: no point).  Lanes holding the same key form a group
+// (match.any); each 64-bit value is split into limbs of 21, 21 and 22 bits (two unsigned, the top
+// one signed), whose sums over at most 32 lanes fit 32 bits and are formed by one warp reduction
+// (redux.sync) per limb; the group's lowest lane recombines them, exactly (a sum of at most n
+// fixed-point terms fits 62 bits), and adds them to the table.  Cost: 3 (LP + 1) reductions per
+// call, whatever the number of distinct keys.
+template <int LP>
+__device__ __forceinline__ void table_add_grouped(int key, const float (&x)[LP], int Sx, unsigned long long* tab) {
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const bool lead = key >= 0 && lane == __ffs(grp) - 1;
+    unsigned long long* row = tab + (size_t)(key < 0 ? 0 : key) * (LP + 1);
+#pragma unroll
+    for (int c = 0; c < LP; ++c) {
+        const long long q = key >= 0 ? fixq(x[c], Sx) : 0;   // the point's exact coordinate
+        const unsigned long long u = (unsigned long long)q;
+        const unsigned lo = __reduce_add_sync(grp, (unsigned)(u & 0x1fffffu));
+        const unsigned mid = __reduce_add_sync(grp, (unsigned)((u >> 21) & 0x1fffffu));
+        const int hi = __reduce_add_sync(grp, (int)(q >> 42));
+        if (lead) {
+            const unsigned long long v = ((unsigned long long)(long long)hi << 42) + ((unsigned long long)mid << 21) +
+                                         (unsigned long long)lo;
+            atomicAdd(row + c, v);
+        }
+    }
+    if (lead) atomicAdd(row + LP, (unsigned long long)__popc(grp));
 }
 
 template <int LP>
