@@ -79,14 +79,12 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     __shared__ long long s_T, s_base, s_tile;
     __shared__ unsigned s_amax;
     __shared__ int s_bstar, s_idx, s_src;
+    __shared__ int s_live[KM_THREADS], s_nlive;   // phase A: a group's live chunks
     __shared__ float s_tsum[KM_WARPS][LP], s_tm[LP], s_tr[KM_WARPS];
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
     const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
-    const long long nch = (n + KM_CHUNK - 1) / KM_CHUNK;
-    auto chunk = [&](long long sq) -> long long {   // the block's warp's sq-th chunk (see phase A)
-        return (long long)b + (long long)G * ((long long)wid + (long long)KM_WARPS * sq);
-    };
+    const long long nch = (n + KM_CHUNK - 1) / KM_CHUNK;   // chunks of KM_CHUNK points (see phase A)
 
     // ---- phase 0: A = max |x| over the used columns (sets the fixed-point scales), and for each
     // of the block's tiles the mean of its points and their largest distance from it
@@ -198,28 +196,28 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             return dcr > sqrtf(dmax) * (1.0f + KPP_EPS);
         };
         // ---- phase A: D^2 update.  The points are dealt in chunks of KM_CHUNK (one warp, four
-        // consecutive points per lane): chunk c goes to block c mod G, warp (c / G) mod KM_WARPS.
-        // The points that cannot skip the new centre are its neighbourhood, a contiguous run of
-        // vertices in a clustered graph, and dealing chunks spreads them over every warp of the
-        // grid instead of loading a few blocks while the others wait at the barrier.  Each warp
-        // first tests the tiles of up to 32 of its chunks at once (one lane per chunk); the lane
-        // holding a far tile's first chunk carries the tile's state; the live chunks are then
-        // worked in order, the next one's D^2, nearest-centre indices and lower bounds (and for
-        // l_pad <= 4 its points) loading while one computes.  A tile's D^2 is read from the
-        // buffer holding it and written to the other one (the selection of the previous round
-        // may still read the first).
+        // consecutive points per lane): chunk c goes to block c mod G.  The points that cannot
+        // skip the new centre are its neighbourhood, a contiguous run of vertices in a clustered
+        // graph, and dealing chunks spreads them over every block instead of loading a few while
+        // the others wait at the barrier.  A block tests the tiles of up to KM_THREADS of its
+        // chunks at once (one thread per chunk; the thread holding a far tile's first chunk
+        // carries the tile's state), lists the live chunks in shared memory and deals them over
+        // its warps, each of which works its share in order, the next chunk's D^2, nearest-centre
+        // indices and lower bounds (and for l_pad <= 4 its points) loading while one computes.  A
+        // tile's D^2 is read from the buffer holding it and written to the other one (the
+        // selection of the previous round may still read the first).
         constexpr bool kPre = LP <= 4;
-        for (long long s0 = 0; chunk(s0) < nch; s0 += 32) {
-            const long long ch_l = chunk(s0 + lane);   // this lane's chunk of the group
+        for (long long m0 = 0; b + (long long)G * m0 < nch; m0 += KM_THREADS) {
+            const long long ch_t = b + (long long)G * (m0 + tid);   // this thread's chunk of the group
             bool live = false;
-            int src_l = 0;                             // the buffer holding its tile's D^2
-            if (ch_l < nch) {
-                const long long t = ch_l / KM_CHUNKS_PER_TILE;
+            int src_t = 0;                                           // the buffer holding its tile's D^2
+            if (ch_t < nch) {
+                const long long t = ch_t / KM_CHUNKS_PER_TILE;
                 float dcr = 0.f;
                 if (!far_tile(t, dcr)) {
                     live = true;
-                    src_l = r > 1 ? __ldcg(fp + t) : 0;
-                } else if (ch_l % KM_CHUNKS_PER_TILE == 0) {
+                    src_t = r > 1 ? (__ldcg(fp + t) & 1) : 0;
+                } else if (ch_t % KM_CHUNKS_PER_TILE == 0) {
                     // every point of the tile is at least dcr from the new centre
                     a.tlb[t] = fminf(a.tlb[t], fmaxf(0.f, dcr) * (1.0f - KPP_EPS));
                     tt[t] = __ldcg(tp + t);
@@ -229,7 +227,16 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                     fl[t] = __ldcg(fp + t);
                 }
             }
-            unsigned pend = __ballot_sync(0xffffffffu, live);
+            const int incl = (int)block_scan_ll(live ? 1 : 0, s_red);
+            if (live) s_live[incl - 1] = tid | (src_t << 30);
+            if (tid == KM_THREADS - 1) s_nlive = incl;
+            __syncthreads();
+            const int nlive = s_nlive;
+            auto live_chunk = [&](int e, int& src) -> long long {   // the e-th live chunk of the group
+                const int v = s_live[e];
+                src = v >> 30;
+                return b + (long long)G * (m0 + (v & 0x3fffffff));
+            };
             // loads of one live chunk's per-point state (D^2, nearest centre, lower bound)
             auto load_state = [&](long long ch, int src, float (&old)[KM_PPT], int (&na)[KM_PPT], float (&lb)[KM_PPT],
                                   float (&x)[KM_PPT][LP]) {
@@ -259,15 +266,14 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             float old_n[KM_PPT], lb_n[KM_PPT];
             int na_n[KM_PPT];
             float x_n[KM_PPT][LP];
-            int j = pend ? __ffs(pend) - 1 : 0;
-            int src_n = __shfl_sync(0xffffffffu, src_l, j);
-            if (pend) load_state(chunk(s0 + j), src_n, old_n, na_n, lb_n, x_n);
-            while (pend) {
-                const long long ch = chunk(s0 + j);
+            int src_n = 0;
+            long long ch_n = wid < nlive ? live_chunk(wid, src_n) : nch;
+            if (wid < nlive) load_state(ch_n, src_n, old_n, na_n, lb_n, x_n);
+            for (int e = wid; e < nlive; e += KM_WARPS) {
+                const long long ch = ch_n;
                 const int src = src_n;
-                pend &= pend - 1;
-                const int jn = pend ? __ffs(pend) - 1 : 0;
-                src_n = __shfl_sync(0xffffffffu, src_l, jn);
+                const bool more = e + KM_WARPS < nlive;
+                if (more) ch_n = live_chunk(e + KM_WARPS, src_n);
                 float old[KM_PPT], lb[KM_PPT];
                 int na[KM_PPT];
                 float x[KM_PPT][LP];
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                         for (int c = 0; c < LP; ++c) x[u][c] = x_n[u][c];
                     }
                 }
-                if (pend) load_state(chunk(s0 + jn), src_n, old_n, na_n, lb_n, x_n);
+                if (more) load_state(ch_n, src_n, old_n, na_n, lb_n, x_n);
                 const long long tile = ch / KM_CHUNKS_PER_TILE;
                 float* d2n = a.d2[src ^ 1];
                 const long long i0 = ch * KM_CHUNK + (long long)KM_PPT * lane;
@@ -337,8 +343,8 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                         fl[tile] = src ^ 1;
                     }
                 }
-                j = jn;
             }
+            __syncthreads();   // s_live is rewritten by the next group
         }
         // after the last pick one more pass (r = k) folds it into D^2 and the nearest centres, which
         // Lloyd's first assignment then reads; no selection follows it
