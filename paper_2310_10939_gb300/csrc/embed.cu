@@ -62,9 +62,102 @@ __global__ void __launch_bounds__(256) k_gauss_init(int n, int l, unsigned long 
     }
 }
 
+// The four normals of Philox block b (Box-Muller on its two word pairs), as k_gauss_init forms them.
+__device__ __forceinline__ void gauss_block(unsigned long long b, unsigned long long seed, float (&z)[4]) {
+    const U64x4 r = philox4x64_10(U64x4{b, 0ull, 0ull, 0ull}, seed, STREAM_X0);
+    const unsigned long long wd[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float u1 = uniform24(wd[2 * p]);
+        const float u2 = uniform24(wd[2 * p + 1]);
+        const float rad = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        z[2 * p] = rad * cs;
+        z[2 * p + 1] = rad * sn;
+    }
+}
+
+// The same start block for rows of at most 8 entries, written row-wise: a thread takes four
+// consecutive rows and every column of them (element (i, c) is draw c n + i, as above), so each
+// thread stores 4 whole rows (one contiguous run) and reads 1/sqrt(d) once.  Element c n + i0 .. +3
+// spans one Philox block, or two when n is not a multiple of 4.
+template <int LP, typename TO>
+__global__ void __launch_bounds__(256) k_gauss_init_rows(int n, int l, unsigned long long seed,
+                                                         const float* __restrict__ dinv, TO* __restrict__ out,
+                                                         unsigned* __restrict__ cm_out) {
+    __shared__ unsigned s_cm[LP];
+    if (threadIdx.x < LP) s_cm[threadIdx.x] = 0u;
+    __syncthreads();
+    const long long groups = ((long long)n + 3) / 4;
+    float cmx[LP];   // this thread's largest |value| per column
+#pragma unroll
+    for (int c = 0; c < LP; ++c) cmx[c] = 0.f;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long i0 = 4 * g;
+        float dv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dv[q] = i0 + q < n ? dinv[i0 + q] : 0.f;
+        float v[4][LP];
+#pragma unroll
+        for (int c = 0; c < LP; ++c) {
+            if (c < l) {
+                const long long e0 = (long long)c * n + i0;
+                float za[4], zb[4];
+                gauss_block((unsigned long long)(e0 >> 2), seed, za);
+                const int off = (int)(e0 & 3);
+                if (off) gauss_block((unsigned long long)(e0 >> 2) + 1, seed, zb);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    // draw e0 + q: word off + q of block e0 / 4, or of the next block (selects, not
+                    // a dynamically indexed array, which would live in local memory)
+                    const int w = off + q;
+                    float z = za[q];
+                    if (off) {
+                        z = w == 1 ? za[1] : w == 2 ? za[2] : w == 3 ? za[3] : w == 4 ? zb[0] : w == 5 ? zb[1] : zb[2];
+                    }
+                    v[q][c] = dv[q] * z;
+                    if (i0 + q < n) cmx[c] = fmaxf(cmx[c], fabsf(v[q][c]));
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q][c] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (i0 + q < n) store_row<LP, TO>(out + (size_t)(i0 + q) * LP, v[q]);
+    }
+    if (cm_out) {
+#pragma unroll
+        for (int c = 0; c < LP; ++c) {
+            float m = cmx[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&s_cm[c], __float_as_uint(m));
+        }
+        __syncthreads();
+        if (threadIdx.x < LP && s_cm[threadIdx.x]) atomicMax(cm_out + threadIdx.x, s_cm[threadIdx.x]);
+    }
+}
+
 template <typename TO>
 cudaError_t launch_init(int LP, int n, int l, unsigned long long seed, const float* dinv, TO* out,
                         unsigned* cm_out, cudaStream_t s) {
+    if (LP <= 8) {
+        long long blocks = ((long long)n + 1023) / 1024;   // 256 threads x 4 rows
+        const long long cap = (long long)device_props().num_sms * 8;
+        if (blocks > cap) blocks = cap;
+        switch (LP) {
+            case 1: k_gauss_init_rows<1, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+            case 2: k_gauss_init_rows<2, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+            case 4: k_gauss_init_rows<4, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+            case 8: k_gauss_init_rows<8, TO><<<(unsigned)blocks, 256, 0, s>>>(n, l, seed, dinv, out, cm_out); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const long long total = (long long)n * l;
     const long long work = (total + 3) / 4 > n ? (total + 3) / 4 : n;
     long long blocks = (work + 255) / 256;

@@ -279,6 +279,20 @@ __global__ void __launch_bounds__(256) k_degree_unit(int64_t n, int64_t nnz, con
                 if (vv >= v1) break;
                 const long long base = vv * VEC;
                 const bool interior = base >= P0 && base + VEC <= P1;
+                if (interior && !check_sorted) {
+                    // the common case in a few instructions: the largest column (as unsigned, so a
+                    // negative one is out of range too) against n, and the smallest offset from
+                    // the tile's first row against the tile; only a vector holding a column of a
+                    // tile row takes the per-entry self-loop test below
+                    unsigned mx = (unsigned)x[h][0], mt = (unsigned)(x[h][0] - r0i);
+#pragma unroll
+                    for (int u = 1; u < VEC; ++u) {
+                        mx = max(mx, (unsigned)x[h][u]);
+                        mt = min(mt, (unsigned)(x[h][u] - r0i));
+                    }
+                    if (mx >= (unsigned long long)n) bad |= ST_INDEX_RANGE;
+                    if (mt >= (unsigned)nr) continue;
+                }
 #pragma unroll
                 for (int u = 0; u < VEC; ++u) {
                     const long long p = base + u;

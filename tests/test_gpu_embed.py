@@ -345,3 +345,19 @@ def test_copy_flag_graph_owns_its_csr(torch, weighted):
     assert torch.equal(fsc.embed(Gc, 3, 9, 4), fsc.embed(Gb, 3, 9, 4))
     assert rel_fro(fsc.embed(Gc, 3, 9, 4).cpu().numpy()[:, :3], spectral.embed(g, 3, 9, 4)) <= 1e-5
     Gc.close()
+
+
+@pytest.mark.parametrize("n", [3, 5, 6, 7, 10, 1025, 1026, 1027, 4099])
+def test_start_block_every_row_alignment(torch, n):
+    """The start block (t = 0) on cycles whose n leaves every remainder mod 4 (a row group of four
+    then takes its draws from one Philox block or from two), for every l up to 8, in float32 and
+    bfloat16: against the oracle's D^-1/2 X0, and the padding columns zero."""
+    import paper_2310_10939_gb300 as fsc
+    g = W.cycle(n)
+    G = _graph(torch, g)
+    for l in range(1, 9):
+        ref = spectral.embed(g, l, 0, 100 + l)
+        for store, bar in ((fsc.F32, 1e-6), (fsc.BF16, 4e-3)):
+            emb = fsc.embed(G, l, 0, 100 + l, store=store, rescale=store == fsc.BF16).cpu().numpy()
+            assert rel_fro(emb[:, :l], ref) <= bar, (l, store)
+            assert np.all(emb[:, l:] == 0)
