@@ -194,6 +194,28 @@ __device__ __forceinline__ void degree_block_totals(int bad, unsigned iso, doubl
 // row.  The tile size is chosen so the grid is about one wave of resident blocks; HBM traffic
 // is row_ptr, col and the three n-vectors once.
 constexpr int kDegUnroll = 4;
+// k_degree_unit with a 16-byte aligned col streams the tile's entries through a ring of kDegRingS
+// stages in shared memory, each stage kDegRingU vectors per thread, filled by asynchronous copies
+// (cp.async, every thread copying and later reading only its own slots): kDegRingS - 1 stages are in
+// flight while one is checked, without holding them in registers.
+constexpr int kDegThreads = 256, kDegRingS = 4, kDegRingU = 2;
+constexpr size_t kDegRingBytes = (size_t)kDegRingS * kDegRingU * kDegThreads * 16;
+// dynamic shared memory of k_degree_unit: the tile's row_ptr (int64, 16-byte padded; in the lean
+// scan below it is rewritten in place as each row's entry range relative to the tile's first entry,
+// int32 pairs), then the ring
+constexpr int kDegMaxRows = 2048;   // rows per tile at most (kDegMaxRows / kDegThreads per thread)
+__host__ __device__ inline size_t deg_unit_smem(int rows) {
+    return (((size_t)rows + 1) * 8 + 15) / 16 * 16 + kDegRingBytes;
+}
+// 16-byte asynchronous copy global -> shared; bytes < 16 copies that many and zero-fills the rest
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const size_t ga = __cvta_generic_to_global(gmem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(ga), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int VEC>
 __device__ __forceinline__ void load_entries(const int32_t* __restrict__ col, long long v, long long nnz,
@@ -220,7 +242,7 @@ __global__ void __launch_bounds__(256) k_degree_unit(int64_t n, int64_t nnz, con
                                                      double* __restrict__ vol, int* __restrict__ status,
                                                      double* __restrict__ sumsq,
                                                      unsigned long long* __restrict__ dmax_bits) {
-    extern __shared__ long long s_rp[];   // rows + 1
+    extern __shared__ __align__(16) long long s_rp[];   // rows + 1, then (VEC = 4) the copy ring
     if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(status, ST_BAD_ROWPTR);
     int bad = 0;
     unsigned iso = 0;
@@ -266,6 +288,132 @@ __global__ void __launch_bounds__(256) k_degree_unit(int64_t n, int64_t nnz, con
         const long long P0 = s_rp[0], P1 = s_rp[nr];   // 0 <= P0 <= P1 <= nnz, rows non-decreasing
         const long long v0 = P0 / VEC, v1 = (P1 + VEC - 1) / VEC;
         const int r0i = (int)r0;                        // r0 < n <= 2^31 - 1
+        // the checks of one vector of entries (positions base .. base + VEC - 1) of the tile
+        auto check = [&](long long base, const int32_t (&x)[VEC]) {
+            const bool interior = base >= P0 && base + VEC <= P1;
+            if (interior && !check_sorted) {
+                // the common case in a few instructions: the largest column (as unsigned, so a
+                // negative one is out of range too) against n, and the smallest offset from the
+                // tile's first row against the tile; only a vector holding a column of a tile row
+                // takes the per-entry self-loop test below
+                unsigned mx = (unsigned)x[0], mt = (unsigned)(x[0] - r0i);
+#pragma unroll
+                for (int u = 1; u < VEC; ++u) {
+                    mx = max(mx, (unsigned)x[u]);
+                    mt = min(mt, (unsigned)(x[u] - r0i));
+                }
+                if (mx >= (unsigned long long)n) bad |= ST_INDEX_RANGE;
+                if (mt >= (unsigned)nr) return;
+            }
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) {
+                const long long p = base + u;
+                if (!interior && (p < P0 || p >= P1)) continue;
+                const int j = x[u];
+                const int jl = j - r0i;   // j's row within the tile, if it is one
+                // a self-loop (i, i) needs i in the tile: then p lies in row i's range
+                if ((unsigned)j >= (unsigned)n) bad |= ST_INDEX_RANGE;
+                else if ((unsigned)jl < (unsigned)nr && s_rp[jl] <= p && p < s_rp[jl + 1]) bad |= ST_SELF_LOOP;
+                if (check_sorted && p > P0) {
+                    // an inversion col[p-1] >= col[p] is either a row start or an unsorted row
+                    const int prev = u > 0 ? x[u > 0 ? u - 1 : 0] : __ldg(col + p - 1);
+                    if (prev >= j) {
+                        int lo = 0, hi = nr - 1;   // last row whose start is <= p (s_rp[nr] = P1 > p)
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_rp[mid] <= p) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        if (p > s_rp[lo]) bad |= ST_UNSORTED;
+                    }
+                }
+            }
+        };
+        if constexpr (VEC == 4) {
+            int4* ring = reinterpret_cast<int4*>(reinterpret_cast<char*>(s_rp) + deg_unit_smem(rows) - kDegRingBytes);
+            // Without the sortedness check, and when the tile's entries fit int32 offsets, a vector's
+            // checks run branch-free on every lane (an entry whose column is a tile row is a rare
+            // case per lane, but over 32 lanes nearly every warp meets one): the largest column
+            // against n, and per entry the own-row range test against the tile's row ranges relative
+            // to P0 (s_rng), whose row is the column's only if the column is a tile row.
+            int2* s_rng = reinterpret_cast<int2*>(s_rp);   // replaces s_rp (same bytes) in the lean scan
+            const bool lean = !check_sorted && P1 - P0 < 0x7ffffff0LL;
+            if (lean) {
+                constexpr int kPer = kDegMaxRows / kDegThreads;
+                int2 rg[kPer];
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    const int q = threadIdx.x + k * kDegThreads;
+                    if (q < nr) rg[k] = make_int2((int)(s_rp[q] - P0), (int)(s_rp[q + 1] - P0));
+                }
+                __syncthreads();   // every read of s_rp is done before it is overwritten
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    const int q = threadIdx.x + k * kDegThreads;
+                    if (q < nr) s_rng[q] = rg[k];
+                }
+                __syncthreads();
+            }
+            const int span = (int)(lean ? P1 - P0 : 0);
+            auto lean_check = [&](long long base, const int4& t) {
+                const int32_t x[4] = {t.x, t.y, t.z, t.w};
+                const int pr0 = (int)(base - P0);   // base >= P0 - 3 and base < P1: fits int
+                bool range = false, self = false;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int pr = pr0 + u;
+                    const bool valid = (unsigned)pr < (unsigned)span;   // the entry belongs to the tile
+                    const unsigned jl = (unsigned)(x[u] - r0i);
+                    const bool in = jl < (unsigned)nr;
+                    const int q = in ? (int)jl : 0;
+                    range |= valid && (unsigned)x[u] >= (unsigned long long)n;
+                    const int2 rg = s_rng[q];
+                    self |= valid && in && rg.x <= pr && pr < rg.y;
+                }
+                if (range) bad |= ST_INDEX_RANGE;
+                if (self) bad |= ST_SELF_LOOP;
+            };
+            const long long per_stage = (long long)kDegRingU * kDegThreads;
+            const long long nstages = (v1 - v0 + per_stage - 1) / per_stage;
+            auto issue = [&](long long st) {   // stage st into slot st mod kDegRingS (own slots only)
+                if (st < nstages) {
+                    const int slot = (int)(st % kDegRingS);
+#pragma unroll
+                    for (int h = 0; h < kDegRingU; ++h) {
+                        const long long vv = v0 + st * per_stage + (long long)h * kDegThreads + threadIdx.x;
+                        if (vv < v1) {
+                            const long long rem = nnz - vv * 4;   // >= 1: vv < v1 <= ceil(nnz / 4)
+                            cp_async16(ring + ((size_t)slot * kDegRingU + h) * kDegThreads + threadIdx.x,
+                                       reinterpret_cast<const int4*>(col) + vv, rem >= 4 ? 16 : (int)rem * 4);
+                        }
+                    }
+                }
+                cp_async_commit();   // every thread commits one group per stage, empty or not
+            };
+#pragma unroll
+            for (int st = 0; st < kDegRingS - 1; ++st) issue(st);
+            for (long long st = 0; st < nstages; ++st) {
+                cp_async_wait<kDegRingS - 2>();   // this thread's copies of stage st have landed
+                issue(st + kDegRingS - 1);          // into the slot of stage st - 1, already checked
+                const int slot = (int)(st % kDegRingS);
+#pragma unroll
+                for (int h = 0; h < kDegRingU; ++h) {
+                    const long long vv = v0 + st * per_stage + (long long)h * kDegThreads + threadIdx.x;
+                    if (vv < v1) {
+                        const int4 t = ring[((size_t)slot * kDegRingU + h) * kDegThreads + threadIdx.x];
+                        if (lean) {
+                            lean_check(vv * VEC, t);
+                        } else {
+                            const int32_t x[VEC] = {t.x, t.y, t.z, t.w};
+                            check(vv * VEC, x);
+                        }
+                    }
+                }
+            }
+            cp_async_wait<0>();
+            __syncthreads();
+            continue;
+        }
         for (long long v = v0 + threadIdx.x; v < v1; v += (long long)kDegUnroll * blockDim.x) {
             int32_t x[kDegUnroll][VEC];
 #pragma unroll
@@ -276,46 +424,7 @@ __global__ void __launch_bounds__(256) k_degree_unit(int64_t n, int64_t nnz, con
 #pragma unroll
             for (int h = 0; h < kDegUnroll; ++h) {
                 const long long vv = v + (long long)h * blockDim.x;
-                if (vv >= v1) break;
-                const long long base = vv * VEC;
-                const bool interior = base >= P0 && base + VEC <= P1;
-                if (interior && !check_sorted) {
-                    // the common case in a few instructions: the largest column (as unsigned, so a
-                    // negative one is out of range too) against n, and the smallest offset from
-                    // the tile's first row against the tile; only a vector holding a column of a
-                    // tile row takes the per-entry self-loop test below
-                    unsigned mx = (unsigned)x[h][0], mt = (unsigned)(x[h][0] - r0i);
-#pragma unroll
-                    for (int u = 1; u < VEC; ++u) {
-                        mx = max(mx, (unsigned)x[h][u]);
-                        mt = min(mt, (unsigned)(x[h][u] - r0i));
-                    }
-                    if (mx >= (unsigned long long)n) bad |= ST_INDEX_RANGE;
-                    if (mt >= (unsigned)nr) continue;
-                }
-#pragma unroll
-                for (int u = 0; u < VEC; ++u) {
-                    const long long p = base + u;
-                    if (!interior && (p < P0 || p >= P1)) continue;
-                    const int j = x[h][u];
-                    const int jl = j - r0i;   // j's row within the tile, if it is one
-                    // a self-loop (i, i) needs i in the tile: then p lies in row i's range
-                    if ((unsigned)j >= (unsigned)n) bad |= ST_INDEX_RANGE;
-                    else if ((unsigned)jl < (unsigned)nr && s_rp[jl] <= p && p < s_rp[jl + 1]) bad |= ST_SELF_LOOP;
-                    if (check_sorted && p > P0) {
-                        // an inversion col[p-1] >= col[p] is either a row start or an unsorted row
-                        const int prev = u > 0 ? x[h][u > 0 ? u - 1 : 0] : __ldg(col + p - 1);
-                        if (prev >= j) {
-                            int lo = 0, hi = nr - 1;   // last row whose start is <= p (s_rp[nr] = P1 > p)
-                            while (lo < hi) {
-                                const int mid = (lo + hi + 1) >> 1;
-                                if (s_rp[mid] <= p) lo = mid;
-                                else hi = mid - 1;
-                            }
-                            if (p > s_rp[lo]) bad |= ST_UNSORTED;
-                        }
-                    }
-                }
+                if (vv < v1) check(vv * VEC, x[h]);
             }
         }
         __syncthreads();
@@ -523,21 +632,21 @@ extern "C" fsc_status fsc_create_graph(int64_t n, int64_t nnz, const int64_t* ro
     do {
         if ((e = cudaMemsetAsync(base + n8, 0, 256, s)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(base + n8 + 256 + 2 * n4, 0, 256, s)) != cudaSuccess) break;
-        const int threads = 256;
+        const int threads = kDegThreads;   // the copy ring of k_degree_unit is sized for it
         const int check_sorted = (flags & FSC_VALIDATE_SYMMETRY) ? 1 : 0;
         if (w == nullptr) {
             // tiles of 64 .. 2048 rows, sized so the grid is about one wave of resident blocks
             const bool vec4 = (reinterpret_cast<uintptr_t>(col_idx) & 15) == 0;
             const void* fn = vec4 ? (const void*)k_degree_unit<4> : (const void*)k_degree_unit<1>;
-            constexpr int64_t kMaxRows = 2048, kMinRows = 64;
-            int per_sm = kernel_occupancy(fn, threads, (size_t)(kMaxRows + 1) * 8);
+            constexpr int64_t kMaxRows = kDegMaxRows, kMinRows = 64;
+            int per_sm = kernel_occupancy(fn, threads, deg_unit_smem((int)kMaxRows));
             if (per_sm < 1) per_sm = 1;
             const int64_t slots = (int64_t)device_props().num_sms * per_sm;
             int64_t rows = ((n + slots - 1) / slots + 31) / 32 * 32;
             rows = rows < kMinRows ? kMinRows : (rows > kMaxRows ? kMaxRows : rows);
             const int64_t ntiles = (n + rows - 1) / rows;
             const int blocks = (int)(ntiles < slots ? ntiles : slots);
-            const size_t smem = (size_t)(rows + 1) * 8;
+            const size_t smem = deg_unit_smem((int)rows);
             if (vec4)
                 k_degree_unit<4><<<blocks, threads, smem, s>>>(n, nnz, row_ptr, col_idx, (int)rows, check_sorted,
                                                                g->deg, g->dinv, g->invdeg, &hdr->niso, &hdr->vol,
