@@ -182,19 +182,6 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         const unsigned* dp = a.tdmax[(r + 2) % 3];
         int* fl = a.tfl[r & 1];
         const int* fp = a.tfl[(r + 1) & 1];         // after round r - 1
-        // A tile the new centre cannot reach (the rule above KPP_EPS) keeps its state.
-        // dcr receives |c - m|, shrunk, minus the tile's radius: a lower bound on the distance from
-        // any point of the tile to the new centre.
-        auto far_tile = [&](long long t, float& dcr) -> bool {
-            if (r == 1) return false;
-            float mc[LP];
-#pragma unroll
-            for (int c = 0; c < LP; ++c) mc[c] = __ldcg(a.tcen + t * LP + c);
-            const float dc = sqrtf(sqdist<LP>(mc, s_c));
-            const float dmax = __uint_as_float(__ldcg(dp + t));
-            dcr = dc * (1.0f - KPP_EPS) - __ldcg(a.trad + t);
-            return dcr > sqrtf(dmax) * (1.0f + KPP_EPS);
-        };
         // ---- phase A: D^2 update.  The points are dealt in chunks of KM_CHUNK (one warp, four
         // consecutive points per lane): chunk c goes to block c mod G.  The points that cannot
         // skip the new centre are its neighbourhood, a contiguous run of vertices in a clustered
@@ -211,20 +198,36 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             const long long ch_t = b + (long long)G * (m0 + tid);   // this thread's chunk of the group
             bool live = false;
             int src_t = 0;                                           // the buffer holding its tile's D^2
-            if (ch_t < nch) {
+            if (ch_t < nch && r == 1) {
+                live = true;   // the first centre: every point's D^2 is set
+            } else if (ch_t < nch) {
                 const long long t = ch_t / KM_CHUNKS_PER_TILE;
-                float dcr = 0.f;
-                if (!far_tile(t, dcr)) {
+                const bool first = ch_t % KM_CHUNKS_PER_TILE == 0;   // this thread carries a far tile
+                // every load of the test and of a carry issued together (one memory latency)
+                float mc[LP];
+#pragma unroll
+                for (int c = 0; c < LP; ++c) mc[c] = __ldcg(a.tcen + t * LP + c);
+                const unsigned dmb = __ldcg(dp + t);
+                const float rad = __ldcg(a.trad + t);
+                const int fpv = __ldcg(fp + t);
+                const long long tpv = first ? __ldcg(tp + t) : 0;
+                const float tlbv = first ? a.tlb[t] : 0.f;
+                const float dc = sqrtf(sqdist<LP>(mc, s_c));
+                // a tile the new centre cannot reach (the rule above KPP_EPS) keeps its state; dcr is
+                // |c - m|, shrunk, minus the tile's radius: a lower bound on the distance from any
+                // point of the tile to the new centre
+                const float dcr = dc * (1.0f - KPP_EPS) - rad;
+                if (!(dcr > sqrtf(__uint_as_float(dmb)) * (1.0f + KPP_EPS))) {
                     live = true;
-                    src_t = r > 1 ? (__ldcg(fp + t) & 1) : 0;
-                } else if (ch_t % KM_CHUNKS_PER_TILE == 0) {
+                    src_t = fpv & 1;
+                } else if (first) {
                     // every point of the tile is at least dcr from the new centre
-                    a.tlb[t] = fminf(a.tlb[t], fmaxf(0.f, dcr) * (1.0f - KPP_EPS));
-                    tt[t] = __ldcg(tp + t);
+                    a.tlb[t] = fminf(tlbv, fmaxf(0.f, dcr) * (1.0f - KPP_EPS));
+                    tt[t] = tpv;
                     tz[t] = 0;
-                    dm[t] = __ldcg(dp + t);
+                    dm[t] = dmb;
                     dz[t] = 0;
-                    fl[t] = __ldcg(fp + t);
+                    fl[t] = fpv;
                 }
             }
             const int incl = (int)block_scan_ll(live ? 1 : 0, s_red);
