@@ -100,6 +100,18 @@ int kernel_occupancy(const void* fn, int threads, size_t smem);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// ---- asynchronous copies global -> shared (cp.async): each thread's copies are visible to that
+// thread after its wait; the copies of one commit group complete together ----------------------
+// 16 bytes; bytes < 16 copies that many and zero-fills the rest
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const size_t ga = __cvta_generic_to_global(gmem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(ga), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // An NVTX range for the lifetime of a C-ABI call (seen by Nsight tools; costs nothing without one).
 struct NvtxRange {
     explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
@@ -125,6 +137,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(flo
 }
 template <> __device__ __forceinline__ __half from_f32<__half>(float x) { return __float2half_rn(x); }
 
+// p must point to global memory: the row is read through the read-only data path (__ldg)
 template <int LP, typename T>
 __device__ __forceinline__ void load_row(const T* __restrict__ p, float (&v)[LP]) {
     constexpr int BYTES = LP * (int)sizeof(T);

@@ -207,15 +207,6 @@ constexpr int kDegMaxRows = 2048;   // rows per tile at most (kDegMaxRows / kDeg
 __host__ __device__ inline size_t deg_unit_smem(int rows) {
     return (((size_t)rows + 1) * 8 + 15) / 16 * 16 + kDegRingBytes;
 }
-// 16-byte asynchronous copy global -> shared; bytes < 16 copies that many and zero-fills the rest
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    const size_t ga = __cvta_generic_to_global(gmem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(ga), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int VEC>
 __device__ __forceinline__ void load_entries(const int32_t* __restrict__ col, long long v, long long nnz,
