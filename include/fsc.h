@@ -215,14 +215,14 @@ fsc_status fsc_kmeans(const float* emb, int64_t n, int l, int ld, int k, uint64_
  * memory budget up front, or a latency-critical loop where an allocation could block or
  * fail.  Same arguments, same kernels and same results as fsc_kmeans; the scratch space
  * (16 bytes per point: two D^2 buffers, reused by Lloyd for its bounds, each point's nearest
- * chosen centre and a lower bound on its distance to the others; plus per-tile state and the
- * centroids) lives in one fixed array of
+ * chosen centre and a lower bound on its distance to the others; plus per-tile and per-chunk
+ * state and the centroids) lives in one fixed array of
  * FSC_KMEANS_STATIC_SCRATCH_BYTES compiled into the library, which every GPU that loads the
  * library keeps reserved until the process exits.
  *  - Size limit, independent of the GPU and of the launch shape: about
- *      16 n + (52 + 4 ld) ceil(n / 2048) + 24 k (ld + 1) + 12 k ld + 8 k + 1 KB  (each part
+ *      16 n + 36 ceil(n / 2048) + (40 + 4 ld) ceil(n / 128) + 24 k (ld + 1) + 12 k ld + 8 k + 1 KB  (each part
  *    rounded up to 256 bytes) must not exceed FSC_KMEANS_STATIC_SCRATCH_BYTES; larger problems
- *    return FSC_ERR_TOO_LARGE.  With k = 64 and ld = 8 that admits up to about 1.04 million points.
+ *    return FSC_ERR_TOO_LARGE.  With k = 64 and ld = 8 that admits up to about 1.01 million points.
  *  - All calls on a device share the one array, which keeps the last call's contents (the
  *    call clears what must start at zero): calls that may run at the same time on the GPU
  *    (different streams, threads or processes sharing the context) race; serialise them.

@@ -38,13 +38,15 @@ struct KppArgs {
     const float* X;
     int n, l, k;
     unsigned long long seed;
-    float* d2[2];        // D^2 per point, two buffers; tfl names the one holding a tile's current values
-    long long* ttot[3];  // per tile: exact D^2 total (warp atomics), three in rotation
-    unsigned* tdmax[3];  // per tile: largest D^2 (float bits, warp atomics), three in rotation
-    int* tfl[2];         // per tile: the d2 buffer holding its D^2 after round r is tfl[r & 1][tile]
-    float* tcen;         // per tile: centre of its points (LP floats)
-    float* trad;         // per tile: largest distance of its points from that centre, widened
-    float* tlb;          // per tile: lower bound on its points' distances to the centres it was carried past
+    float* d2[2];        // D^2 per point, two buffers; cfl names the one holding a chunk's current values
+    long long* ttot[3];  // per tile: exact D^2 total (its chunks' totals, atomics), three in rotation
+    unsigned* tmask[3];  // per tile: bit w = the d2 buffer of its chunk w (atomics), three in rotation
+    long long* ctot[2];  // per chunk: exact D^2 total after round r: ctot[r & 1]
+    unsigned* cdmax[2];  // per chunk: largest D^2 (float bits) after round r: cdmax[r & 1]
+    int* cfl[2];         // per chunk: the d2 buffer holding its D^2 after round r is cfl[r & 1][chunk]
+    float* ccen;         // per chunk: centre of its points (LP floats)
+    float* crad;         // per chunk: largest distance of its points from that centre, widened
+    float* clb;          // per chunk: lower bound on its points' distances to the centres it was carried past
     float* lb2;          // per point: lower bound on its distance to every chosen centre but its nearest
     unsigned* amax;      // max |x| (float bits), output for the Lloyd launch
     int* near;           // per point: index (selection order) of its nearest chosen centre
@@ -61,12 +63,13 @@ struct KppArgs {
 // |x - c| >= |c - c_a| - |x - c_a| > sqrt(D^2)), so its D^2 is carried over without loading
 // the point.  Both sides of the test are widened by KPP_EPS relative, far above float32
 // rounding of the distances, so a skipped point is one whose min(D^2, d) is D^2 exactly.
-// The same argument for a whole tile of points with centre m and radius rho (every point within
-// rho of m) whose largest D^2 is Dmax: if |c - m| - rho > sqrt(Dmax), then for every point x of
-// the tile |x - c| >= |c - m| - |x - m| > sqrt(Dmax) >= sqrt(D^2(x)), so no D^2 of the tile changes
-// and the tile is carried over (its D^2, nearest centres and exact total) without reading any of
-// its per-point state.  rho is widened when it is stored, |c - m| shrunk and sqrt(Dmax) grown by
-// KPP_EPS relative, so a carried tile is one the per-point rule would leave unchanged.
+// The same argument for a whole chunk of KM_CHUNK points with centre m and radius rho (every point
+// within rho of m) whose largest D^2 is Dmax: if |c - m| - rho > sqrt(Dmax), then for every point x
+// of the chunk |x - c| >= |c - m| - |x - m| > sqrt(Dmax) >= sqrt(D^2(x)), so no D^2 of the chunk
+// changes and the chunk is carried over (its D^2, nearest centres and exact total) without reading
+// any of its per-point state.  rho is widened when it is stored, |c - m| shrunk and sqrt(Dmax)
+// grown by KPP_EPS relative, so a carried chunk is one the per-point rule would leave unchanged.
+// The draw sums the chunks' totals per tile of KM_TILE points (tile totals, atomics).
 constexpr float KPP_EPS = 1e-5f;
 constexpr int KPP_CACHE = 4;   // tile totals per thread kept in registers by the selection
 
@@ -78,22 +81,23 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     __shared__ long long s_red[KM_WARPS];
     __shared__ long long s_T, s_base, s_tile;
     __shared__ unsigned s_amax;
-    __shared__ int s_bstar, s_idx, s_src;
+    __shared__ int s_bstar, s_idx;
+    __shared__ unsigned s_src;   // the drawn tile's buffer mask
     __shared__ int s_live[KM_THREADS], s_nlive;   // phase A: a group's live chunks
-    __shared__ float s_tsum[KM_WARPS][LP], s_tm[LP], s_tr[KM_WARPS];
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
     const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
     const long long nch = (n + KM_CHUNK - 1) / KM_CHUNK;   // chunks of KM_CHUNK points (see phase A)
 
     // ---- phase 0: A = max |x| over the used columns (sets the fixed-point scales), and for each
-    // of the block's tiles the mean of its points and their largest distance from it
+    // chunk (one warp each, dealt as in phase A) the mean of its points and their largest distance
+    // from it
     if (tid == 0) s_amax = 0u;
     __syncthreads();
     {
         float m = 0.f;
-        for (long long tile = b; tile < ntiles; tile += G) {
-            const long long i0 = tile * KM_TILE + (long long)KM_PPT * tid;
+        for (long long ch = b + (long long)G * wid; ch < nch; ch += (long long)G * KM_WARPS) {
+            const long long i0 = ch * KM_CHUNK + (long long)KM_PPT * lane;
             float x[KM_PPT][LP];
             float sum[LP];
 #pragma unroll
@@ -109,36 +113,29 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                     }
                 }
             }
+            const float cnt = (float)min((long long)KM_CHUNK, n - ch * KM_CHUNK);
+            float mc[LP];
 #pragma unroll
             for (int c = 0; c < LP; ++c) {
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], off);
-                if (lane == 0) s_tsum[wid][c] = sum[c];
+                mc[c] = sum[c] / cnt;
             }
-            __syncthreads();
-            if (tid < LP) {
-                float t = 0.f;
-                for (int w = 0; w < KM_WARPS; ++w) t += s_tsum[w][tid];
-                const long long cnt = min((long long)KM_TILE, n - tile * KM_TILE);
-                s_tm[tid] = t / (float)cnt;
-            }
-            __syncthreads();
             float r2 = 0.f;
 #pragma unroll
             for (int u = 0; u < KM_PPT; ++u)
-                if (i0 + u < n) r2 = fmaxf(r2, sqdist<LP>(x[u], s_tm));
+                if (i0 + u < n) r2 = fmaxf(r2, sqdist<LP>(x[u], mc));
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, off));
-            if (lane == 0) s_tr[wid] = r2;
-            __syncthreads();
-            if (tid == 0) {
-                float r = 0.f;
-                for (int w = 0; w < KM_WARPS; ++w) r = fmaxf(r, s_tr[w]);
-                a.trad[tile] = sqrtf(r) * (1.0f + KPP_EPS);
+            float mine = 0.f;   // lane c writes column c (selects: no dynamically indexed array)
+#pragma unroll
+            for (int c = 0; c < LP; ++c)
+                if (lane == c) mine = mc[c];
+            if (lane < LP) a.ccen[ch * LP + lane] = mine;
+            if (lane == 0) {
+                a.crad[ch] = sqrtf(r2) * (1.0f + KPP_EPS);
+                a.clb[ch] = __int_as_float(0x7f800000);   // +inf
             }
-            if (tid < LP) a.tcen[tile * LP + tid] = s_tm[tid];
-            if (tid == 0) a.tlb[tile] = __int_as_float(0x7f800000);   // +inf
-            __syncthreads();
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -176,58 +173,63 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         __syncthreads();
         long long* tt = a.ttot[r % 3];              // exact D^2 total per tile (atomics)
         long long* tz = a.ttot[(r + 1) % 3];        // cleared here for round r + 1
-        const long long* tp = a.ttot[(r + 2) % 3];  // round r - 1's totals
-        unsigned* dm = a.tdmax[r % 3];              // largest D^2 per tile (atomics)
-        unsigned* dz = a.tdmax[(r + 1) % 3];
-        const unsigned* dp = a.tdmax[(r + 2) % 3];
-        int* fl = a.tfl[r & 1];
-        const int* fp = a.tfl[(r + 1) & 1];         // after round r - 1
+        unsigned* tmk = a.tmask[r % 3];             // per tile: its chunks' buffer bits (atomics)
+        unsigned* tmz = a.tmask[(r + 1) % 3];       // cleared here for round r + 1
+        long long* ct = a.ctot[r & 1];              // per chunk, this round (one writer per chunk)
+        const long long* cp = a.ctot[(r + 1) & 1];  // per chunk, after round r - 1
+        unsigned* dm = a.cdmax[r & 1];
+        const unsigned* dp = a.cdmax[(r + 1) & 1];
+        int* fl = a.cfl[r & 1];
+        const int* fp = a.cfl[(r + 1) & 1];
         // ---- phase A: D^2 update.  The points are dealt in chunks of KM_CHUNK (one warp, four
         // consecutive points per lane): chunk c goes to block c mod G.  The points that cannot
         // skip the new centre are its neighbourhood, a contiguous run of vertices in a clustered
         // graph, and dealing chunks spreads them over every block instead of loading a few while
-        // the others wait at the barrier.  A block tests the tiles of up to KM_THREADS of its
-        // chunks at once (one thread per chunk; the thread holding a far tile's first chunk
-        // carries the tile's state), lists the live chunks in shared memory and deals them over
-        // its warps, each of which works its share in order, the next chunk's D^2, nearest-centre
-        // indices and lower bounds (and for l_pad <= 4 its points) loading while one computes.  A
-        // tile's D^2 is read from the buffer holding it and written to the other one (the
-        // selection of the previous round may still read the first).
+        // the others wait at the barrier.  A block tests up to KM_THREADS of its chunks at once
+        // (one thread per chunk, which also carries a far chunk's state and adds its total to its
+        // tile's), lists the live chunks in shared memory and deals them over its warps, each of
+        // which works its share in order, the next chunk's D^2, nearest-centre indices and lower
+        // bounds (and for l_pad <= 4 its points) loading while one computes.  A chunk's D^2 is read
+        // from the buffer holding it and written to the other one (the selection of the previous
+        // round may still read the first).
         constexpr bool kPre = LP <= 4;
         for (long long m0 = 0; b + (long long)G * m0 < nch; m0 += KM_THREADS) {
             const long long ch_t = b + (long long)G * (m0 + tid);   // this thread's chunk of the group
             bool live = false;
-            int src_t = 0;                                           // the buffer holding its tile's D^2
+            int src_t = 0;                                           // the buffer holding its D^2
             if (ch_t < nch && r == 1) {
                 live = true;   // the first centre: every point's D^2 is set
             } else if (ch_t < nch) {
                 const long long t = ch_t / KM_CHUNKS_PER_TILE;
-                const bool first = ch_t % KM_CHUNKS_PER_TILE == 0;   // this thread carries a far tile
                 // every load of the test and of a carry issued together (one memory latency)
                 float mc[LP];
 #pragma unroll
-                for (int c = 0; c < LP; ++c) mc[c] = __ldcg(a.tcen + t * LP + c);
-                const unsigned dmb = __ldcg(dp + t);
-                const float rad = __ldcg(a.trad + t);
-                const int fpv = __ldcg(fp + t);
-                const long long tpv = first ? __ldcg(tp + t) : 0;
-                const float tlbv = first ? a.tlb[t] : 0.f;
+                for (int c = 0; c < LP; ++c) mc[c] = __ldcg(a.ccen + ch_t * LP + c);
+                const unsigned dmb = __ldcg(dp + ch_t);
+                const float rad = __ldcg(a.crad + ch_t);
+                const int fpv = __ldcg(fp + ch_t);
+                const long long ctp = __ldcg(cp + ch_t);
+                const float clbv = a.clb[ch_t];
                 const float dc = sqrtf(sqdist<LP>(mc, s_c));
-                // a tile the new centre cannot reach (the rule above KPP_EPS) keeps its state; dcr is
-                // |c - m|, shrunk, minus the tile's radius: a lower bound on the distance from any
-                // point of the tile to the new centre
+                // a chunk the new centre cannot reach (the rule above KPP_EPS) keeps its state; dcr
+                // is |c - m|, shrunk, minus the chunk's radius: a lower bound on the distance from
+                // any point of the chunk to the new centre
                 const float dcr = dc * (1.0f - KPP_EPS) - rad;
                 if (!(dcr > sqrtf(__uint_as_float(dmb)) * (1.0f + KPP_EPS))) {
                     live = true;
                     src_t = fpv & 1;
-                } else if (first) {
-                    // every point of the tile is at least dcr from the new centre
-                    a.tlb[t] = fminf(tlbv, fmaxf(0.f, dcr) * (1.0f - KPP_EPS));
-                    tt[t] = tpv;
-                    tz[t] = 0;
-                    dm[t] = dmb;
-                    dz[t] = 0;
-                    fl[t] = fpv;
+                } else {
+                    // every point of the chunk is at least dcr from the new centre
+                    a.clb[ch_t] = fminf(clbv, fmaxf(0.f, dcr) * (1.0f - KPP_EPS));
+                    ct[ch_t] = ctp;
+                    dm[ch_t] = dmb;
+                    fl[ch_t] = fpv;
+                    if (ctp) atomicAdd(reinterpret_cast<unsigned long long*>(tt + t), (unsigned long long)ctp);
+                    if (fpv & 1) atomicOr(tmk + t, 1u << (ch_t % KM_CHUNKS_PER_TILE));
+                    if (ch_t % KM_CHUNKS_PER_TILE == 0) {
+                        tz[t] = 0;
+                        tmz[t] = 0u;
+                    }
                 }
             }
             const int incl = (int)block_scan_ll(live ? 1 : 0, s_red);
@@ -338,12 +340,14 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, off));
                 if (lane == 0) {
+                    ct[ch] = v;
+                    dm[ch] = __float_as_uint(dmx);
+                    fl[ch] = src ^ 1;
                     if (v) atomicAdd(reinterpret_cast<unsigned long long*>(tt + tile), (unsigned long long)v);
-                    if (dmx > 0.f) atomicMax(dm + tile, __float_as_uint(dmx));
-                    if (ch % KM_CHUNKS_PER_TILE == 0) {   // once per live tile
+                    if ((src ^ 1) & 1) atomicOr(tmk + tile, 1u << (ch % KM_CHUNKS_PER_TILE));
+                    if (ch % KM_CHUNKS_PER_TILE == 0) {   // once per tile (its first chunk)
                         tz[tile] = 0;
-                        dz[tile] = 0;
-                        fl[tile] = src ^ 1;
+                        tmz[tile] = 0u;
                     }
                 }
             }
@@ -360,16 +364,16 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
         // walks it.  The point: the tile's D^2 in point order, one block scan.
         const long long per = (ntiles + KM_THREADS - 1) / KM_THREADS;
         const long long q_lo = min(ntiles, per * tid), q_hi = min(ntiles, q_lo + per);
-        // the first KPP_CACHE totals of the range, and their tiles' buffer flags, stay in registers
+        // the first KPP_CACHE totals of the range, and their tiles' buffer masks, stay in registers
         // for the walk below
         long long tcache[KPP_CACHE];
-        int fcache[KPP_CACHE];
+        unsigned fcache[KPP_CACHE];
         long long rsum = 0;
 #pragma unroll
         for (int q = 0; q < KPP_CACHE; ++q) {
             const bool in = q_lo + q < q_hi;
             tcache[q] = in ? __ldcg(tt + q_lo + q) : 0;
-            fcache[q] = in ? __ldcg(fl + q_lo + q) : 0;
+            fcache[q] = in ? __ldcg(tmk + q_lo + q) : 0u;
             rsum += tcache[q];
         }
         for (long long q = q_lo + KPP_CACHE; q < q_hi; ++q) rsum += __ldcg(tt + q);
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
                     if (v > 0 && base + v > T) {
                         s_tile = q;
                         s_base = base;
-                        s_src = __ldcg(fl + q);
+                        s_src = __ldcg(tmk + q);
                         found = true;
                     }
                     base += v;
@@ -421,7 +425,9 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
             __syncthreads();
             const long long tq = s_tile;
             if (tq >= 0) {   // always (exact sums cross the target); block-uniform
-                const float* d2n = a.d2[s_src & 1];
+                // warp w's points are the tile's chunk w, whose buffer is bit w of the tile's mask
+                static_assert(KM_CHUNKS_PER_TILE == KM_WARPS, "one chunk of the drawn tile per warp");
+                const float* d2n = a.d2[(s_src >> wid) & 1];
                 const long long i0 = tq * KM_TILE + (long long)KM_PPT * tid;
                 long long qv[KM_PPT];
                 long long v = 0;
@@ -485,8 +491,9 @@ struct LloydArgs {
     int prune;           // 1: skip the k-way scan of points whose bounds prove the label unchanged
     // The first assignment from the seeding (seeded = 1): each point's nearest of the k chosen
     // centres (near),
-    // its D^2 (in the buffer dfl[tile] names) and a lower bound on the distance to every other centre
-    // (min of lb2 and the tile's tlb), instead of a k-way scan.  (d2s0 / d2s1: the two D^2 buffers.)
+    // its D^2 (in the buffer dfl[chunk] names) and a lower bound on the distance to every other centre
+    // (min of lb2 and the chunk's carried bound tlb[chunk]), instead of a k-way scan.  (d2s0 / d2s1:
+    // the two D^2 buffers; chunks of KM_CHUNK points.)
     int seeded;
     const int* near;
     const float* d2s0;
@@ -707,15 +714,14 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             // caches would evict on most points.
             const bool lab16 = (reinterpret_cast<uintptr_t>(a.labels) & 15) == 0;
             long long ch = chunk(0);
-            int fl_n = ch < nch ? __ldcg(a.dfl + ch / KM_CHUNKS_PER_TILE) : 0;
+            int fl_n = ch < nch ? __ldcg(a.dfl + ch) : 0;
             for (long long sq = 0; ch < nch; ch = chunk(++sq)) {
                 const long long i0 = ch * KM_CHUNK + (long long)KM_PPT * lane;
-                const long long tile = ch / KM_CHUNKS_PER_TILE;   // the seeding's tile
                 const bool full4 = i0 + KM_PPT <= n;
                 const float* d2s = (fl_n & 1) ? a.d2s1 : a.d2s0;
-                const float tl = __ldcg(a.tlb + tile);
+                const float tl = __ldcg(a.tlb + ch);
                 const long long chn = chunk(sq + 1);
-                fl_n = chn < nch ? __ldcg(a.dfl + chn / KM_CHUNKS_PER_TILE) : 0;
+                fl_n = chn < nch ? __ldcg(a.dfl + chn) : 0;
                 int nr[KM_PPT];
                 float dd[KM_PPT], lbs[KM_PPT], x[KM_PPT][LP];
                 if (full4) {
@@ -984,9 +990,14 @@ static size_t lloyd_smem_bytes(int k, int LP, int ntab) {
 // accumulators (zeroed together), the two D^2 buffers, the per-tile k-means++ state (zeroed:
 // exact totals x 3, largest D^2 x 3, buffer flags x 2; not zeroed: tile centres and radii), the
 // centroids (float64, float32), the k-means++ picks and each point's nearest chosen centre.
+// Workspace of one k-means call: header (stats, grid barrier, status, max |x|) and the Lloyd
+// accumulators (zeroed together), the two D^2 buffers, the per-tile k-means++ state (zeroed: exact
+// totals x 3, buffer masks x 3), the per-chunk state (zeroed: buffer flags x 2; not zeroed: totals
+// x 2, largest D^2 x 2, centres, radii, carried bounds), the centroids (float64, float32), the
+// k-means++ picks and each point's nearest chosen centre and lower bound.
 struct KmLayout {
-    size_t hdr, acc, o_d2, o_tt, tt_bytes, o_tg, o_c64, o_c32, o_seed, o_near, o_lb2, total;
-    size_t d2_stride, tt8, tt4;
+    size_t hdr, acc, o_d2, o_tt, tt_bytes, o_cs, cs_zero, o_c64, o_c32, o_seed, o_near, o_lb2, total;
+    size_t d2_stride, tt8, tt4, c8, c4, ccen;
 };
 
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -994,15 +1005,19 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 static KmLayout km_layout(long long n, int k, int LP) {
     KmLayout L{};
     const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
+    const long long nch = (n + KM_CHUNK - 1) / KM_CHUNK;
     L.hdr = up256(sizeof(KmDevStats) + sizeof(GridBarrier) + 2 * sizeof(int) + sizeof(unsigned));
     L.acc = up256((size_t)3 * k * (LP + 1) * 8 + 16 * 8);
     L.d2_stride = up256((size_t)n * 4);
     L.tt8 = up256((size_t)ntiles * 8);
     L.tt4 = up256((size_t)ntiles * 4);
+    L.c8 = up256((size_t)nch * 8);
+    L.c4 = up256((size_t)nch * 4);
+    L.ccen = up256((size_t)nch * LP * 4);
     size_t off = L.hdr + L.acc;
     L.o_d2 = off; off += 2 * L.d2_stride;
-    L.o_tt = off; L.tt_bytes = 3 * L.tt8 + 5 * L.tt4; off += L.tt_bytes;
-    L.o_tg = off; off += up256((size_t)ntiles * LP * 4) + 2 * L.tt4;
+    L.o_tt = off; L.tt_bytes = 3 * L.tt8 + 3 * L.tt4; off += L.tt_bytes;
+    L.o_cs = off; L.cs_zero = 2 * L.c4; off += 2 * L.c4 + 2 * L.c8 + 2 * L.c4 + L.ccen + 2 * L.c4;
     L.o_c64 = off; off += up256((size_t)k * LP * 8);
     L.o_c32 = off; off += up256((size_t)k * LP * 4);
     L.o_seed = off; off += up256((size_t)k * 8);
@@ -1013,18 +1028,24 @@ static KmLayout km_layout(long long n, int k, int LP) {
 }
 
 // Points the k-means++ arguments at the buffers of a workspace laid out by km_layout.
-static void kpp_buffers(KppArgs& ka, char* ws, const KmLayout& L, long long ntiles, int LP) {
+static void kpp_buffers(KppArgs& ka, char* ws, const KmLayout& L) {
     ka.d2[0] = reinterpret_cast<float*>(ws + L.o_d2);
     ka.d2[1] = reinterpret_cast<float*>(ws + L.o_d2 + L.d2_stride);
     char* t = ws + L.o_tt;
     for (int q = 0; q < 3; ++q) ka.ttot[q] = reinterpret_cast<long long*>(t + q * L.tt8);
     t += 3 * L.tt8;
-    for (int q = 0; q < 3; ++q) ka.tdmax[q] = reinterpret_cast<unsigned*>(t + q * L.tt4);
-    t += 3 * L.tt4;
-    for (int q = 0; q < 2; ++q) ka.tfl[q] = reinterpret_cast<int*>(t + q * L.tt4);
-    ka.tcen = reinterpret_cast<float*>(ws + L.o_tg);
-    ka.trad = reinterpret_cast<float*>(ws + L.o_tg + up256((size_t)ntiles * LP * 4));
-    ka.tlb = reinterpret_cast<float*>(ws + L.o_tg + up256((size_t)ntiles * LP * 4) + L.tt4);
+    for (int q = 0; q < 3; ++q) ka.tmask[q] = reinterpret_cast<unsigned*>(t + q * L.tt4);
+    char* c = ws + L.o_cs;
+    for (int q = 0; q < 2; ++q) ka.cfl[q] = reinterpret_cast<int*>(c + q * L.c4);
+    c += 2 * L.c4;
+    for (int q = 0; q < 2; ++q) ka.ctot[q] = reinterpret_cast<long long*>(c + q * L.c8);
+    c += 2 * L.c8;
+    for (int q = 0; q < 2; ++q) ka.cdmax[q] = reinterpret_cast<unsigned*>(c + q * L.c4);
+    c += 2 * L.c4;
+    ka.ccen = reinterpret_cast<float*>(c);
+    c += L.ccen;
+    ka.crad = reinterpret_cast<float*>(c);
+    ka.clb = reinterpret_cast<float*>(c + L.c4);
     ka.lb2 = reinterpret_cast<float*>(ws + L.o_lb2);
     ka.seeds = reinterpret_cast<int64_t*>(ws + L.o_seed);
     ka.near = reinterpret_cast<int*>(ws + L.o_near);
@@ -1077,8 +1098,9 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         ka.l = l;
         ka.k = k;
         ka.seed = seed;
-        kpp_buffers(ka, ws, Lw, ntiles, LP);
+        kpp_buffers(ka, ws, Lw);
         if ((e = cudaMemsetAsync(ws + Lw.o_tt, 0, Lw.tt_bytes, s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(ws + Lw.o_cs, 0, Lw.cs_zero, s)) != cudaSuccess) break;
         ka.amax = amax;
         ka.bar = bar;
         ka.status = call_status;
@@ -1107,9 +1129,9 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.near = ka.near;
         la.d2s0 = ka.d2[0];
         la.d2s1 = ka.d2[1];
-        la.dfl = ka.tfl[k & 1];   // the flags after the final pass (r = k)
+        la.dfl = ka.cfl[k & 1];   // the chunk flags after the final pass (r = k)
         la.lb2 = ka.lb2;
-        la.tlb = ka.tlb;
+        la.tlb = ka.clb;
         la.st = st;
         la.bar = bar;
         la.status = call_status;
@@ -1327,8 +1349,9 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     ka.l = l;
     ka.k = k;
     ka.seed = seed;
-    kpp_buffers(ka, ws, Lw, ntiles, LP);
+    kpp_buffers(ka, ws, Lw);
     FSC_CUDA(cudaMemsetAsync(ws + Lw.o_tt, 0, Lw.tt_bytes, s));
+    FSC_CUDA(cudaMemsetAsync(ws + Lw.o_cs, 0, Lw.cs_zero, s));
     ka.amax = amax;
     ka.bar = bar;
     ka.status = call_status;
@@ -1357,9 +1380,9 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     la.near = ka.near;
     la.d2s0 = ka.d2[0];
     la.d2s1 = ka.d2[1];
-    la.dfl = ka.tfl[k & 1];   // the flags after the final pass (r = k)
+    la.dfl = ka.cfl[k & 1];   // the chunk flags after the final pass (r = k)
     la.lb2 = ka.lb2;
-    la.tlb = ka.tlb;
+    la.tlb = ka.clb;
     la.st = st;
     la.bar = bar;
     la.status = call_status;
