@@ -24,6 +24,10 @@
  *    reads them (fsc_kmeans with non-NULL stats, fsc_cluster) or by
  *    fsc_sync_status().
  *  - Thread safety: a graph handle may be used by one stream at a time.
+ *  - Contexts: the library's per-device state (its memory pool, status word and kernel launch
+ *    attributes) is made in the CUDA context current at first use and made again when a call
+ *    finds another context current (for example after cudaDeviceReset).  Handles (graphs,
+ *    batches) are not: destroy them before resetting a device.
  */
 #ifndef FSC_H
 #define FSC_H

@@ -8,9 +8,42 @@
 #include <mutex>
 #include <tuple>
 
+#include <cuda.h>   // driver types only: the two driver calls below are fetched through the runtime
+
 #include "fsc_internal.cuh"
 
 namespace fsc {
+
+// The unique id of the calling thread's current CUDA context (0 if it cannot be had).  The
+// library's per-device caches (memory pool, status word, launch attributes) belong to one context
+// and are rebuilt when the id changes, e.g. after cudaDeviceReset replaced the primary context:
+// their old handles and addresses are dropped, never used.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) {
+        cudaFree(nullptr);   // makes the device's primary context current (no allocation)
+        if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    }
+    unsigned long long id = 0;
+    return get_id(c, &id) == CUDA_SUCCESS ? id : 0;
+}
 
 // long rows (longrows.cu)
 cudaError_t launch_long_rows(int64_t n, const int64_t* rp, int64_t cap, unsigned long long* count, int64_t* rows,
@@ -21,6 +54,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 DeviceProps g_props[kMaxDevices];
 int* g_status_word[kMaxDevices];
+unsigned long long g_status_ctx[kMaxDevices];
 std::once_flag g_props_once[kMaxDevices];
 std::mutex g_status_mu;
 std::atomic<long long> g_wait_limit{2000000000LL};
@@ -43,27 +77,46 @@ int* device_status_word() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_status_mu);
-    if (!g_status_word[dev]) {
+    bool stale = g_status_ctx[dev] != ctx;   // one of a former context
+    if (g_status_word[dev] && !stale && ctx == 0) {
+        // no context id to compare: check that the address still names device memory
+        cudaPointerAttributes pa{};
+        stale = cudaPointerGetAttributes(&pa, g_status_word[dev]) != cudaSuccess || pa.type != cudaMemoryTypeDevice;
+        cudaGetLastError();
+    }
+    if (!g_status_word[dev] || stale) {
         int* p = nullptr;
         if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
         if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
         g_status_word[dev] = p;
+        g_status_ctx[dev] = ctx;
     }
     return g_status_word[dev];
 }
 
 namespace {
 cudaMemPool_t g_pool[kMaxDevices];
+unsigned long long g_pool_ctx[kMaxDevices];
 std::mutex g_pool_mu;
 std::mutex g_occ_mu;
-std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;
-std::map<std::pair<int, const void*>, size_t> g_smem_attr;
+// keyed by context id as well: a kernel's dynamic shared-memory opt-in is per context
+std::map<std::tuple<unsigned long long, int, const void*, int, size_t>, int> g_occ;
+std::map<std::tuple<unsigned long long, int, const void*>, size_t> g_smem_attr;
 }  // namespace
 
 static cudaMemPool_t library_pool(int dev) {
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_pool_mu);
-    if (!g_pool[dev]) {
+    bool stale = g_pool_ctx[dev] != ctx;   // one of a former context
+    if (g_pool[dev] && !stale && ctx == 0) {
+        // no context id to compare: check that the pool still answers
+        unsigned long long v = 0;
+        stale = cudaMemPoolGetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &v) != cudaSuccess;
+        cudaGetLastError();
+    }
+    if (!g_pool[dev] || stale) {
         cudaMemPoolProps props{};
         props.allocType = cudaMemAllocationTypePinned;
         props.location.type = cudaMemLocationTypeDevice;
@@ -73,6 +126,7 @@ static cudaMemPool_t library_pool(int dev) {
         unsigned long long keep = ~0ull;
         cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
         g_pool[dev] = p;
+        g_pool_ctx[dev] = ctx;
     }
     return g_pool[dev];
 }
@@ -92,13 +146,14 @@ cudaError_t pool_free(void* p, cudaStream_t s) { return p ? cudaFreeAsync(p, s) 
 int kernel_occupancy(const void* fn, int threads, size_t smem) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_occ_mu);
-    const auto key = std::make_tuple(dev, fn, threads, smem);
+    const auto key = std::make_tuple(ctx, dev, fn, threads, smem);
     auto it = g_occ.find(key);
     if (it != g_occ.end()) return it->second;
     // the opt-in limit covers dynamic bytes on top of the kernel's static shared memory, so it is
     // raised for every size above the largest one set so far
-    size_t& attr = g_smem_attr[std::make_pair(dev, fn)];
+    size_t& attr = g_smem_attr[std::make_tuple(ctx, dev, fn)];
     if (smem > attr) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
         attr = smem;
@@ -727,6 +782,7 @@ extern "C" fsc_status fsc_release_cached_memory(void) {
     for (int d = 0; d < kMaxDevices; ++d) {
         if (!g_pool[d]) continue;
         cudaSetDevice(d);
+        if (g_pool_ctx[d] != current_context_id()) continue;   // a former context's pool is gone
         cudaError_t e = cudaDeviceSynchronize();
         if (e == cudaSuccess) e = cudaMemPoolTrimTo(g_pool[d], 0);
         if (first == cudaSuccess) first = e;

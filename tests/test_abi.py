@@ -82,8 +82,9 @@ def _cuda_home():
     return None
 
 
-def build_c_example(out_path):
-    """Compile the C example against include/fsc.h and link it with libfsc.so (plain C, gcc)."""
+def build_c_example(out_path, source=None):
+    """Compile the C example (or another C program) against include/fsc.h and link it with
+    libfsc.so (plain C, gcc)."""
     import shutil
     import subprocess
     cuda = _cuda_home()
@@ -97,7 +98,7 @@ def build_c_example(out_path):
                                                     "targets/x86_64-linux/lib")
                     if os.path.exists(os.path.join(cuda, d, "libcudart.so"))), os.path.join(cuda, "lib64"))
     cmd = ["gcc", "-O2", "-Wall", "-Wextra", "-Werror", "-std=c99", "-I" + os.path.join(ROOT, "include"),
-           "-I" + os.path.join(cuda, "include"), EXAMPLE, "-L" + lib_dir, "-lfsc", "-L" + cudalib, "-lcudart",
+           "-I" + os.path.join(cuda, "include"), source or EXAMPLE, "-L" + lib_dir, "-lfsc", "-L" + cudalib, "-lcudart",
            "-Wl,-rpath," + lib_dir, "-Wl,-rpath," + cudalib, "-o", str(out_path)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
@@ -127,3 +128,22 @@ def test_binding_flags_match_the_header():
     defs = {m.group(1): int(m.group(2), 16) for m in re.finditer(r"#define FSC_(\w+)\s+0x([0-9a-fA-F]+)u", text)}
     for name in ("VALIDATE_SYMMETRY", "COPY", "EMBED_RESCALE", "BATCH_AUTOTUNE", "FILTER_NO_FALLBACK"):
         assert defs[name] == getattr(fsc, name), name
+
+
+RESET = os.path.join(ROOT, "tests", "c", "reset_cycles.c")
+
+
+def test_reset_cycles_program_builds(tmp_path):
+    assert os.path.exists(build_c_example(tmp_path / "reset_cycles", RESET))
+
+
+@pytest.mark.gpu
+def test_library_state_survives_device_reset(tmp_path):
+    """Three create / embed / k-means / cluster / destroy cycles with cudaDeviceReset between them
+    (a C program, so that no other runtime state outlives the reset): the library rebuilds its
+    memory pool, status word and launch attributes in each new context."""
+    import subprocess
+    exe = build_c_example(tmp_path / "reset_cycles", RESET)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=180)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("cliques recovered") == 3
