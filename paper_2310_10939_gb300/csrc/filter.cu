@@ -565,6 +565,11 @@ extern "C" fsc_status fsc_cluster_filtered(const fsc_graph* g, int k, int l, uin
     fsc_filter_report rep{};
     rep.threshold = 1.25 + 3.0 * sqrt(2.0 / ((double)l * (double)k));
     fsc_status rc = fsc_filter_embed(g, l, k, seed, store, params, nullptr, emb, nullptr, nullptr, d_energy, &eo, stream);
+    // k-means runs on the filtered embedding straight away (no host round trip between the two);
+    // the guard's energy is read once k-means has synchronised, and in the rare case that it calls
+    // for the fallback, the plain embedding and its k-means replace the results
+    if (rc == FSC_OK)
+        rc = fsc_kmeans(emb, g->n, l, LP, k, seed, max_iter, labels, nullptr, nullptr, stats ? stats : &local, stream);
     if (rc == FSC_OK) {
         double energy = 0.0;
         if ((e = cudaMemcpyAsync(&energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -580,9 +585,10 @@ extern "C" fsc_status fsc_cluster_filtered(const fsc_graph* g, int k, int l, uin
         fsc_embed_opts po = eo;
         po.flags = store == FSC_F32 ? 0u : FSC_EMBED_RESCALE;
         rc = fsc_embed(g, l, t, seed, store == FSC_F32 ? FSC_F32 : FSC_BF16, emb, &po, stream);
+        if (rc == FSC_OK)
+            rc = fsc_kmeans(emb, g->n, l, LP, k, seed, max_iter, labels, nullptr, nullptr, stats ? stats : &local,
+                            stream);
     }
-    if (rc == FSC_OK)
-        rc = fsc_kmeans(emb, g->n, l, LP, k, seed, max_iter, labels, nullptr, nullptr, stats ? stats : &local, stream);
     cudaError_t ef = pool_free(emb, s);
     if (rc == FSC_OK && ef != cudaSuccess) rc = cuda_status(ef);
     if (rc == FSC_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_status(e);
