@@ -500,6 +500,13 @@ extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64
     char* ws = static_cast<char*>(g->ws);
     float* mom = reinterpret_cast<float*>(ws + NCOEF * blk);
     float* coeffs = reinterpret_cast<float*>(ws + NCOEF * blk + mom_bytes);
+    // the side stream that computes the coefficients once the moments are in (after the fourth
+    // step), beside the later steps; the combination waits for it
+    if (!g->side) {
+        FSC_CUDA(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+        FSC_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+        FSC_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+    }
     FSC_CUDA(launch_init_any(LP, n, l, seed, g->dinv, ws, (int)store, s));
     FSC_CUDA(cudaMemsetAsync(mom, 0, mom_bytes, s));
     if (opts && opts->ev_spmm_begin) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_begin, s));
@@ -529,11 +536,19 @@ extern "C" fsc_status fsc_filter_embed(const fsc_graph* gc, int l, int k, uint64
             FSC_CUDA(launch_cheb_any<__nv_bfloat16>(LP, G, g->w != nullptr, a, (int)blocks, s));
             FSC_CUDA(long_cheb<__nv_bfloat16>(g, LP, a, mslot, s));
         }
+        if (j == 3) {   // the moments are complete: the coefficients on the side stream
+            static_assert(FDEG > 4, "the coefficients are formed after the fourth step");
+            FSC_CUDA(cudaEventRecord(g->ev_fork, s));
+            FSC_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+            k_filter_coeffs<<<1, 256, 0, g->side>>>(mom, (int)mslots, (double)n, g->volume, g->deg_sumsq, g->deg_max,
+                                                    (double)g->n_isolated, k, l, params, coeffs_override, feats_out,
+                                                    coeffs);
+            FSC_CUDA(cudaGetLastError());
+            FSC_CUDA(cudaEventRecord(g->ev_join, g->side));
+        }
     }
     if (opts && opts->ev_spmm_end) FSC_CUDA(cudaEventRecord((cudaEvent_t)opts->ev_spmm_end, s));
-    k_filter_coeffs<<<1, 256, 0, s>>>(mom, (int)mslots, (double)n, g->volume, g->deg_sumsq, g->deg_max,
-                                      (double)g->n_isolated, k, l, params, coeffs_override, feats_out, coeffs);
-    FSC_CUDA(cudaGetLastError());
+    FSC_CUDA(cudaStreamWaitEvent(s, g->ev_join, 0));   // the coefficients
     long long cb = ((long long)n + 255) / 256;
     if (cb > cap * 2) cb = cap * 2;
     const size_t stride = blk / es;

@@ -308,4 +308,8 @@ struct fsc_graph {
     int64_t* seg_hi;             // per segment: one past its last entry
     float* seg_part;             // per segment: partial sums, 8 floats
     void* copy_base;             // FSC_COPY: the graph's own copy of the CSR
+    // the learned filter's side stream (its coefficients run beside the later sparse steps) and the
+    // two events joining it, made on first use
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
 };

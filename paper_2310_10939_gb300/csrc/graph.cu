@@ -769,6 +769,9 @@ extern "C" fsc_status fsc_destroy_graph(fsc_graph* g) {
     pool_free(g->deg, 0);
     if (g->long_base) pool_free(g->long_base, 0);
     if (g->copy_base) pool_free(g->copy_base, 0);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->side) cudaStreamDestroy(g->side);
     cudaSetDevice(prev);
     delete g;
     return e == cudaSuccess ? FSC_OK : cuda_status(e);
