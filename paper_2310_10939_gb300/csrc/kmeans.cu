@@ -561,7 +561,9 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
     int* s_qidx = reinterpret_cast<int*>(km_smem + lloyd_queue_offset(k, LP, ntab));
     int* s_qold = s_qidx + KM_WARPS * KM_QUEUE;
     float* s_qlw = reinterpret_cast<float*>(s_qold + KM_WARPS * KM_QUEUE);
-    float* s_cn = reinterpret_cast<float*>(s_tab);   // new centroids, staged in the tables once they are summed
+    // the new centroids, formed after the grid barrier in the queue indices' space (idle then; k LP
+    // floats <= KM_WARPS KM_QUEUE since k ld <= 4096)
+    float* s_cn = reinterpret_cast<float*>(s_qidx);
     __shared__ long long s_red[KM_WARPS];
     __shared__ int s_redi[KM_WARPS];
     __shared__ long long s_inert;
@@ -586,6 +588,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
         if (b == 0) a.c64[q] = (double)v;   // float64 masters of the k-means++ centres
     }
     for (size_t q = tid; q < rowlen; q += KM_THREADS) s_S[q] = 0;
+    for (size_t q = tid; q < (size_t)ntab * rowlen; q += KM_THREADS) s_tab[q] = 0ull;   // then after each push
     if (tid == 0) s_pmax = 0u;
     __syncthreads();
     // One grid barrier per iteration: blocks add the changes of their clusters' exact sums into
@@ -597,35 +600,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
         const int cur = it % 3;
         unsigned long long* T = a.tot + (size_t)cur * rowlen;
         const bool pr = a.prune && it > 1;
-        for (size_t q = tid; q < (size_t)ntab * rowlen; q += KM_THREADS) s_tab[q] = 0ull;
-        if (pr) {
-            // half the distance of each centroid to its nearest other centroid.  Centroid j's
-            // candidates are dealt into `parts` interleaved subsets, one thread each, whose minima
-            // one thread per centroid then combines (no shared atomics; (a - b)^2 = (b - a)^2
-            // exactly, so d(j, jj) = d(jj, j) and the result equals a scan over pairs)
-            const int parts = k >= KM_THREADS ? 1 : KM_THREADS / k;
-            float* s_part = s_qlw;   // the point queues are idle until phase A
-            for (int q = tid; q < k * parts; q += KM_THREADS) {
-                const int j = q / parts, p = q - j * parts;
-                float cj[LP];
-#pragma unroll
-                for (int c = 0; c < LP; ++c) cj[c] = s_c[j * LP + c];
-                float m = __int_as_float(0x7f800000);   // +inf: k = 1 has no other centroid
-                for (int jj = p; jj < k; jj += parts)
-                    if (jj != j) m = fminf(m, sqdist<LP>(cj, s_c + jj * LP));
-                if (parts == 1) s_sep[j] = 0.5f * sqrtf(m) * (1.0f - PRUNE_EPS);
-                else s_part[q] = m;
-            }
-            __syncthreads();
-            if (parts > 1) {
-                for (int j = tid; j < k; j += KM_THREADS) {
-                    float m = s_part[j * parts];
-                    for (int p = 1; p < parts; ++p) m = fminf(m, s_part[j * parts + p]);
-                    s_sep[j] = 0.5f * sqrtf(m) * (1.0f - PRUNE_EPS);
-                }
-            }
-        }
-        __syncthreads();
+        // the tables are clear and (with pruning, from the second iteration on) s_sep holds half the
+        // distance of each centroid to its nearest other one: both prepared by the previous update
         const float pmax = pr ? __uint_as_float(s_pmax) * (1.0f + PRUNE_EPS) : 0.f;
         long long inert = 0;
         int changed = 0;
@@ -898,11 +874,19 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             if (inert) atomicAdd(a.cnt3 + 4 * cur, (unsigned long long)inert);
             if (changed) atomicAdd(a.cnt3 + 4 * cur + 1, (unsigned long long)changed);
         }
+        // the tables were read before the block sums' barriers: clear them for the next iteration
+        // while the grid gathers
+        for (size_t q = tid; q < (size_t)ntab * rowlen; q += KM_THREADS) s_tab[q] = 0ull;
         if (!grid_sync(a.bar, a.status, a.limit, a.stall, epoch)) return;
         // ---- update, in every block: running totals += this iteration's changes (exact integer
         // adds, so every block holds the same totals); c_j = (exact sum of its points) / count,
         // rounded to float64 then float32; an empty cluster keeps its centroid
         for (size_t q = tid; q < rowlen; q += KM_THREADS) s_S[q] += (long long)__ldcg(T + q);
+        if (tid == 0) {
+            s_inert = (long long)__ldcg(a.cnt3 + 4 * cur);
+            s_changed = (int)__ldcg(a.cnt3 + 4 * cur + 1);
+            s_pmax = 0u;
+        }
         __syncthreads();
         for (int q = tid; q < k * LP; q += KM_THREADS) {
             const int j = q / LP, c = q - j * LP;
@@ -916,13 +900,14 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             }
             s_cn[q] = v;
         }
-        if (tid == 0) {
-            s_inert = (long long)__ldcg(a.cnt3 + 4 * cur);
-            s_changed = (int)__ldcg(a.cnt3 + 4 * cur + 1);
-            s_pmax = 0u;
-        }
         __syncthreads();
-        // how far each centroid moved (bounds of the next assignment), empty-cluster events
+        // on the last iteration s_c keeps the centroids its assignment used (for the inertia)
+        const bool stop = s_changed == 0 || it == a.max_iter;
+        // how far each centroid moved (bounds of the next assignment), empty-cluster events; and
+        // for the next assignment half the distance of each new centroid to its nearest other one:
+        // centroid j's candidates are dealt into `parts` interleaved subsets, one thread each, whose
+        // minima one thread per centroid combines below (no shared atomics; (a - b)^2 = (b - a)^2
+        // exactly, so d(j, jj) = d(jj, j) and the result equals a scan over pairs)
         for (int j = tid; j < k; j += KM_THREADS) {
             float mv = 0.f;
 #pragma unroll
@@ -933,6 +918,22 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             s_mv[j] = sqrtf(mv) * (1.0f + PRUNE_EPS);
             atomicMax(&s_pmax, __float_as_uint(s_mv[j]));
             if (b == 0 && s_S[(size_t)j * (LP + 1) + LP] == 0) atomicAdd(&a.st->empty_events, 1);
+        }
+        const bool sep_next = a.prune && !stop;
+        const int parts = k >= KM_THREADS ? 1 : KM_THREADS / k;
+        float* s_part = s_qlw;   // the point queues are idle until phase A
+        if (sep_next) {
+            for (int q = tid; q < k * parts; q += KM_THREADS) {
+                const int j = q / parts, p = q - j * parts;
+                float cj[LP];
+#pragma unroll
+                for (int c = 0; c < LP; ++c) cj[c] = s_cn[j * LP + c];
+                float m = __int_as_float(0x7f800000);   // +inf: k = 1 has no other centroid
+                for (int jj = p; jj < k; jj += parts)
+                    if (jj != j) m = fminf(m, sqdist<LP>(cj, s_cn + jj * LP));
+                if (parts == 1) s_sep[j] = 0.5f * sqrtf(m) * (1.0f - PRUNE_EPS);
+                else s_part[q] = m;
+            }
         }
         // the accumulator of iteration it+2 was last read after the previous barrier: clear it
         if (b == 0) {
@@ -946,12 +947,16 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             a.st->changed = s_changed;
         }
         __syncthreads();
-        // on the last iteration s_c keeps the centroids its assignment used (for the inertia)
-        const bool stop = s_changed == 0 || it == a.max_iter;
-        if (!stop)
-            for (int q = tid; q < k * LP; q += KM_THREADS) s_c[q] = s_cn[q];
-        __syncthreads();
         if (stop) break;
+        if (sep_next && parts > 1) {
+            for (int j = tid; j < k; j += KM_THREADS) {
+                float m = s_part[j * parts];
+                for (int p = 1; p < parts; ++p) m = fminf(m, s_part[j * parts + p]);
+                s_sep[j] = 0.5f * sqrtf(m) * (1.0f - PRUNE_EPS);
+            }
+        }
+        for (int q = tid; q < k * LP; q += KM_THREADS) s_c[q] = s_cn[q];
+        __syncthreads();
     }
     // ---- inertia of the last assignment: each point's float32 distance to the centroid it was
     // assigned to (the same value the assignment computed), summed exactly in fixed point
