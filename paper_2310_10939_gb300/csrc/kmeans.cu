@@ -1,9 +1,9 @@
 // k-means++ seeding and Lloyd iterations on the embedding rows (Sec. 2.2, last step of Algorithm 2).
 //
-// Both phases run as one cooperative (co-resident) persistent launch each.  Tiles of KM_TILE
-// points are dealt round-robin over the blocks; cross-block steps are separated by a bounded
-// grid barrier (grid_sync), after which every block reads the other blocks' partial results
-// through L2.  Lloyd keeps the exact cluster sums as running totals that only points changing
+// Both phases run as one cooperative (co-resident) persistent launch each.  Chunks of KM_CHUNK
+// points (one warp's work) are dealt round-robin over the blocks; cross-block steps are separated
+// by a bounded grid barrier (grid_sync), after which every block reads the other blocks' partial
+// results through L2.  Lloyd keeps the exact cluster sums as running totals that only points changing
 // cluster update, and skips points by Hamerly's bounds (see k_lloyd).
 //
 // Decisions follow fixed rules that a float64 CPU restatement reproduces:
@@ -605,14 +605,13 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
         const float pmax = pr ? __uint_as_float(s_pmax) * (1.0f + PRUNE_EPS) : 0.f;
         long long inert = 0;
         int changed = 0;
-        // ---- phase A.  Each thread takes KM_PPT consecutive points of a tile and settles, from
+        // ---- phase A.  Each thread takes KM_PPT consecutive points of a chunk and settles, from
         // its label and bounds alone, those whose upper bound u (carried forward by the centroid's
         // move) is below max(s(a), lower bound): Hamerly's test, without loading the point.  The
         // others go to a per-warp queue that the warp then works one point per lane: the exact
         // distance to the own centroid first (the same test, tight), the k-way scan only if that
         // fails, so no lane idles behind a neighbour's scan.  Centroid sums are exact integers,
-        // so which lane adds a point changes no result.  The next tile's labels and bounds load
-        // while this tile is settled.
+        // so which lane adds a point changes no result.
         // Points are dealt in chunks of KM_CHUNK (one warp, four consecutive points per lane):
         // chunk c goes to block c mod G, warp (c / G) mod KM_WARPS, so the chunks of any vertex
         // range (a planted cluster's, whose boundary points all need the scan) spread over every
@@ -992,10 +991,6 @@ static size_t lloyd_smem_bytes(int k, int LP, int ntab) {
 }
 
 // Workspace of one k-means call: header (stats, grid barrier, status, max |x|) and the Lloyd
-// accumulators (zeroed together), the two D^2 buffers, the per-tile k-means++ state (zeroed:
-// exact totals x 3, largest D^2 x 3, buffer flags x 2; not zeroed: tile centres and radii), the
-// centroids (float64, float32), the k-means++ picks and each point's nearest chosen centre.
-// Workspace of one k-means call: header (stats, grid barrier, status, max |x|) and the Lloyd
 // accumulators (zeroed together), the two D^2 buffers, the per-tile k-means++ state (zeroed: exact
 // totals x 3, buffer masks x 3), the per-chunk state (zeroed: buffer flags x 2; not zeroed: totals
 // x 2, largest D^2 x 2, centres, radii, carried bounds), the centroids (float64, float32), the
@@ -1081,7 +1076,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
     if (G2 < G) G = G2;
     if (G < 1) return FSC_ERR_CUDA;
     if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
-    // both kernels deal tiles of KM_TILE points round-robin: no more blocks than tiles
+    // no more blocks than tiles of KM_TILE points (the unit of the final inertia pass)
     const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;
     if (G > ntiles) G = (int)ntiles;
 
@@ -1335,7 +1330,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     if (G2 < G) G = G2;
     if (G < 1) return FSC_ERR_CUDA;
     if (G > KM_MAX_BLOCKS) G = KM_MAX_BLOCKS;
-    const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;   // both kernels deal these round-robin
+    const long long ntiles = ((long long)n + KM_TILE - 1) / KM_TILE;   // no more blocks than tiles
     if (G > ntiles) G = (int)ntiles;
 
     const KmLayout Lw = km_layout(n, k, LP);
