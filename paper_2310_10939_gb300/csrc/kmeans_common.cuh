@@ -12,8 +12,8 @@ namespace fsc {
 constexpr int KM_THREADS = 512;
 constexpr int KM_WARPS = KM_THREADS / 32;
 constexpr int KM_MAX_BLOCKS = 1024;
-constexpr int KM_PPT = 4;                          // consecutive points per thread per tile
-constexpr int KM_TILE = KM_THREADS * KM_PPT;       // points per tile (chunks are multiples of it)
+constexpr int KM_PPT = 4;                          // consecutive points per lane in a chunk or tile
+constexpr int KM_TILE = KM_THREADS * KM_PPT;       // points per tile (one block's four points per thread)
 constexpr int KM_CHUNK = 32 * KM_PPT;              // points per warp chunk (Lloyd's unit of work)
 constexpr int KM_CHUNKS_PER_TILE = KM_TILE / KM_CHUNK;
 
