@@ -684,9 +684,10 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             // The first assignment is the seeding's (near, D^2 and the lower bound come from
             // k-means++; see LloydArgs), and every label changes (from -1, the launcher's fill).
             // Every thread settles its own four points directly; their coordinates join the
-            // centroid sums through warp-aggregated adds (table_add_grouped: one shared add per
-            // label present in the warp), since labels alternate within a tile and per-lane run
-            // caches would evict on most points.
+            // centroid sums through table_add_grouped (one shared add per label where a warp's
+            // points carry few labels, per-lane adds where they carry many).  Per-lane run caches
+            // were slower (0.26 against 0.15 ms on 2^22 points): when the label changes at a chunk
+            // boundary all 32 lanes evict into the same table row at once.
             const bool lab16 = (reinterpret_cast<uintptr_t>(a.labels) & 15) == 0;
             long long ch = chunk(0);
             int fl_n = ch < nch ? __ldcg(a.dfl + ch) : 0;
@@ -725,12 +726,31 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                 float lbo[KM_PPT], ubo[KM_PPT];
 #pragma unroll
                 for (int u = 0; u < KM_PPT; ++u) {
-                    const bool in = i0 + u < n;
                     int bj = nr[u];
-                    if (in && !in_range(bj, 0, k, BS_LLOYD_LABEL)) bj = 0;
-                    bj = min(max(bj, 0), k - 1);   // memory safety whatever the seeding left
-                    nr[u] = bj;
-                    table_add_grouped<LP>(in ? bj : -1, x[u], sc.Sx, my_tab);
+                    if (i0 + u < n && !in_range(bj, 0, k, BS_LLOYD_LABEL)) bj = 0;
+                    nr[u] = min(max(bj, 0), k - 1);   // memory safety whatever the seeding left
+                }
+                // where every lane's four points share a label, a lane adds their sum (one grouped
+                // add per chunk instead of four; |sum| < 2^62 since n >= 4 here)
+                if (__all_sync(0xffffffffu, full4 && nr[0] == nr[1] && nr[1] == nr[2] && nr[2] == nr[3])) {
+                    long long q[LP];
+#pragma unroll
+                    for (int c = 0; c < LP; ++c)
+                        q[c] = fixq(x[0][c], sc.Sx) + fixq(x[1][c], sc.Sx) + fixq(x[2][c], sc.Sx) + fixq(x[3][c], sc.Sx);
+                    table_add_grouped<LP>(nr[0], q, KM_PPT, my_tab);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < KM_PPT; ++u) {
+                        const bool in = i0 + u < n;
+                        long long q[LP];
+#pragma unroll
+                        for (int c = 0; c < LP; ++c) q[c] = in ? fixq(x[u][c], sc.Sx) : 0;
+                        table_add_grouped<LP>(in ? nr[u] : -1, q, 1, my_tab);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < KM_PPT; ++u) {
+                    const bool in = i0 + u < n;
                     if (in) {
                         inert += fixq(dd[u], sc.Sd);
                         ++changed;
