@@ -439,6 +439,12 @@ static bool is_aligned(const void* p, size_t a) { return (reinterpret_cast<uintp
 
 FSC_BOUNDS_READER(filter)
 
+// kmeans.cu: fsc_kmeans (rows of <= 8 floats, no centroids or seeds) whose launches return at once
+// when the energy guard rejects the embedding
+fsc_status kmeans_guarded(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int max_iter,
+                          int32_t* labels, fsc_kmeans_stats* stats, const double* guard, double guard_thr,
+                          cudaStream_t s);
+
 }  // namespace fsc
 
 using namespace fsc;
@@ -581,10 +587,17 @@ extern "C" fsc_status fsc_cluster_filtered(const fsc_graph* g, int k, int l, uin
     rep.threshold = 1.25 + 3.0 * sqrt(2.0 / ((double)l * (double)k));
     fsc_status rc = fsc_filter_embed(g, l, k, seed, store, params, nullptr, emb, nullptr, nullptr, d_energy, &eo, stream);
     // k-means runs on the filtered embedding straight away (no host round trip between the two);
-    // the guard's energy is read once k-means has synchronised, and in the rare case that it calls
-    // for the fallback, the plain embedding and its k-means replace the results
+    // the guard's energy is read once k-means has synchronised, and when it calls for the fallback
+    // the plain embedding and its k-means replace the results.  The k-means launches read the
+    // energy themselves and return at once when the guard will reject the embedding (the same test
+    // as below), so a fallback costs the filter and the plain method, not a wasted k-means too
+    // (a graph without a spectral gap falls back on every call).
+    const bool guarded_ok = guard && g->n <= 2147483647LL && k <= 1024 && (int64_t)k * LP <= 4096 && max_iter >= 1;
     if (rc == FSC_OK)
-        rc = fsc_kmeans(emb, g->n, l, LP, k, seed, max_iter, labels, nullptr, nullptr, stats ? stats : &local, stream);
+        rc = guarded_ok ? kmeans_guarded(emb, g->n, l, LP, k, seed, max_iter, labels, stats ? stats : &local, d_energy,
+                                         rep.threshold, s)
+                        : fsc_kmeans(emb, g->n, l, LP, k, seed, max_iter, labels, nullptr, nullptr, stats ? stats : &local,
+                                     stream);
     if (rc == FSC_OK) {
         double energy = 0.0;
         if ((e = cudaMemcpyAsync(&energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||

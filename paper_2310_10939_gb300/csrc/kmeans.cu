@@ -56,7 +56,17 @@ struct KppArgs {
     int* status;
     long long limit;
     int stall;
+    // optional: the learned filter's energy guard (see fsc_cluster_filtered).  When *guard / guard_lk
+    // is not <= guard_thr the filtered embedding will be replaced by the plain one, and the launch
+    // returns at once (the same double division and comparison as the host's decision).
+    const double* guard;
+    double guard_lk, guard_thr;
 };
+
+// The guard test of KppArgs / LloydArgs: true when the clustering is not wanted.
+__device__ __forceinline__ bool guard_rejects(const double* guard, double lk, double thr) {
+    return guard && !(__ldcg(guard) / lk <= thr);
+}
 
 // A point whose D^2 = |x - c_a|^2 (c_a its nearest chosen centre) satisfies
 // sqrt(D^2) < |c - c_a| / 2 cannot move closer to a new centre c (triangle inequality:
@@ -88,6 +98,7 @@ __global__ void __launch_bounds__(KM_THREADS) k_kmeanspp(KppArgs a) {
     const long long n = a.n;
     const long long ntiles = (n + KM_TILE - 1) / KM_TILE;
     const long long nch = (n + KM_CHUNK - 1) / KM_CHUNK;   // chunks of KM_CHUNK points (see phase A)
+    if (guard_rejects(a.guard, a.guard_lk, a.guard_thr)) return;   // every block alike: before any barrier
 
     // ---- phase 0: A = max |x| over the used columns (sets the fixed-point scales), and for each
     // chunk (one warp each, dealt as in phase A) the mean of its points and their largest distance
@@ -506,6 +517,8 @@ struct LloydArgs {
     int* status;
     long long limit;
     int stall;
+    const double* guard;   // as in KppArgs
+    double guard_lk, guard_thr;
 };
 
 // Exact pruning (Hamerly's bounds): a point whose distance to its current centroid is below
@@ -575,6 +588,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
     // a seeding that stopped on an error (a barrier timeout) left its per-point results
     // unwritten: report its status and leave
     if (*reinterpret_cast<volatile int*>(a.status) != 0) return;
+    if (guard_rejects(a.guard, a.guard_lk, a.guard_thr)) return;   // every block alike: before any barrier
     // tiles of KM_TILE points, dealt round-robin (block b takes b, b + G, ...) in the final
     // inertia pass
     const long long ntl = (n + KM_TILE - 1) / KM_TILE;
@@ -1102,7 +1116,8 @@ static int coop_blocks(K kern, size_t smem) {
 
 template <int LP>
 static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed, int max_iter, int32_t* labels,
-                            double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats, cudaStream_t s) {
+                            double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats, cudaStream_t s,
+                            const double* guard = nullptr, double guard_thr = 0.0) {
     const size_t kpp_smem = (size_t)k * (sizeof(int) + sizeof(float) + LP * sizeof(float));
     // private accumulation tables: as many as fit in 64 KB (at least one, at most one per warp)
     const size_t tab_bytes = (size_t)k * (LP + 1) * 8;
@@ -1147,6 +1162,9 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         ka.status = call_status;
         ka.limit = wait_limit_ns();
         ka.stall = barrier_stall();
+        ka.guard = guard;
+        ka.guard_lk = (double)l * (double)k;
+        ka.guard_thr = guard_thr;
         void* kargs[] = {&ka};
         if ((e = cudaLaunchCooperativeKernel((const void*)kpp, dim3(G), dim3(KM_THREADS), kargs, kpp_smem, s)) != cudaSuccess) break;
         if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s)) != cudaSuccess) break;
@@ -1178,6 +1196,9 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.status = call_status;
         la.limit = ka.limit;
         la.stall = ka.stall;
+        la.guard = ka.guard;
+        la.guard_lk = ka.guard_lk;
+        la.guard_thr = ka.guard_thr;
         void* largs[] = {&la};
         if ((e = cudaLaunchCooperativeKernel((const void*)lly, dim3(G), dim3(KM_THREADS), largs, lloyd_smem, s)) != cudaSuccess) break;
         if (centroids)
@@ -1217,6 +1238,21 @@ FSC_BOUNDS_READER(kmeans)
 // rows of 16 .. 128 floats (kmeans_wide.cu)
 fsc_status kmeans_wide(const float* emb, int n, int l, int ld, int k, uint64_t seed, int max_iter, int32_t* labels,
                        double* centroids, int64_t* seed_idx, fsc_kmeans_stats* stats, cudaStream_t s);
+
+// fsc_kmeans for rows of at most 8 floats whose launches return at once when the learned filter's
+// energy guard rejects the embedding (energy / (l k) not <= thr, read on the device): the caller
+// then discards labels and stats (labels are left at -1).  guard = nullptr: plain fsc_kmeans.
+fsc_status kmeans_guarded(const float* emb, int64_t n, int l, int ld, int k, uint64_t seed, int max_iter,
+                          int32_t* labels, fsc_kmeans_stats* stats, const double* guard, double guard_thr,
+                          cudaStream_t s) {
+    switch (ld) {
+        case 1: return kmeans_lp<1>(emb, (int)n, l, k, seed, max_iter, labels, nullptr, nullptr, stats, s, guard, guard_thr);
+        case 2: return kmeans_lp<2>(emb, (int)n, l, k, seed, max_iter, labels, nullptr, nullptr, stats, s, guard, guard_thr);
+        case 4: return kmeans_lp<4>(emb, (int)n, l, k, seed, max_iter, labels, nullptr, nullptr, stats, s, guard, guard_thr);
+        case 8: return kmeans_lp<8>(emb, (int)n, l, k, seed, max_iter, labels, nullptr, nullptr, stats, s, guard, guard_thr);
+    }
+    return FSC_ERR_INVALID_ARG;
+}
 
 }  // namespace fsc
 
