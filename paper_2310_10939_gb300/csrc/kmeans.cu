@@ -507,6 +507,9 @@ struct LloydArgs {
     // the two D^2 buffers; chunks of KM_CHUNK points.)
     int seeded;
     const int* near;
+    // after the first iteration `near` is free: each block lists there the points that need the k-way
+    // scan, in its own region (see k_lloyd's phase A); pend is the same buffer, writable
+    int* pend;
     const float* d2s0;
     const float* d2s1;
     const int* dfl;
@@ -582,6 +585,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
     __shared__ long long s_inert;
     __shared__ int s_changed;
     __shared__ unsigned s_pmax;
+    __shared__ int s_pend;   // points in the block's list for the k-way scan (phase A)
 
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const long long n = a.n;
@@ -603,8 +607,20 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
     }
     for (size_t q = tid; q < rowlen; q += KM_THREADS) s_S[q] = 0;
     for (size_t q = tid; q < (size_t)ntab * rowlen; q += KM_THREADS) s_tab[q] = 0ull;   // then after each push
-    if (tid == 0) s_pmax = 0u;
+    if (tid == 0) {
+        s_pmax = 0u;
+        s_pend = 0;
+    }
     __syncthreads();
+    // The block's region of the scan list: its chunks' points, counted exactly (chunk c belongs to
+    // block c mod G; the last chunk may be partial), so the regions of all blocks tile [0, n)
+    long long pstart;
+    {
+        const long long nch0 = (n + KM_CHUNK - 1) / KM_CHUNK;
+        const long long q_ = nch0 / G, r_ = nch0 % G, owner = (nch0 - 1) % G, missing = nch0 * KM_CHUNK - n;
+        pstart = (long long)KM_CHUNK * ((long long)b * q_ + min((long long)b, r_)) - (owner < b ? missing : 0);
+    }
+    int* pend = a.pend + pstart;
     // One grid barrier per iteration: blocks add the changes of their clusters' exact sums into
     // the iteration's accumulator (one of three, used in rotation), and after the barrier every
     // block adds them to its running totals and forms all k centroids itself, so the centroids
@@ -646,16 +662,14 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
         int* qold = s_qold + wid * KM_QUEUE;
         float* qlw = s_qlw + wid * KM_QUEUE;
         int qn = 0;   // queue length (warp-uniform)
-        // works the queued points in two passes.  First, 32 at a time, the tight test (the exact
-        // distance to the own centroid); the points it does not settle are moved, in place, to the
-        // front of the queue.  Then those, 32 at a time, get the k-way scan, so every lane of a scan
-        // has a point (measured on 2^22 points, k = 100: in the heavy second iteration only 16.5 of
-        // 32 lanes had one when both steps shared a batch; the scan is bound by its float32 issue,
-        // ~6 us per batch, against 0.6 us for the rows' loads).  The rows are loaded again for the
-        // scan (from L1 or L2).  Which lane works a point changes no result.
+        // works the queued points: the tight test (the exact distance to the own centroid), 32 at a
+        // time; the points it does not settle join the block's scan list, which all warps of the block
+        // work together once the chunks are done, so a warp whose chunks hold many such points does
+        // not hold up the block (the k-way scan, bound by its float32 issue, is most of the work in
+        // the heavy iterations, and dealt by chunks the most loaded warp of a block scanned about
+        // twice the mean)
         auto flush = [&]() {
             __syncwarp();
-            int nq = 0;   // points left for the k-way scan (warp-uniform)
             for (int q0 = 0; q0 < qn; q0 += 32) {
                 const int q = q0 + lane;
                 const bool act = q < qn;
@@ -676,41 +690,12 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
                 }
                 const bool keep = act && !settled;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
-                __syncwarp();   // every lane has read its entry before any is overwritten
-                if (keep) {     // pos <= q: only entries already read are overwritten
-                    const int pos = nq + __popc(m & ((1u << lane) - 1u));
-                    qidx[pos] = (int)i;
-                    qold[pos] = oldl;
-                    qlw[pos] = lw;
-                }
-                nq += __popc(m);
-                __syncwarp();
-            }
-            for (int q0 = 0; q0 < nq; q0 += 32) {
-                const int q = q0 + lane;
-                const bool act = q < nq;
-                const long long i = act ? qidx[q] : 0;
-                const int oldl = act ? qold[q] : 0;
-                float xv[LP];
-                load_point<LP>(a.X, i, a.l, xv);
-                float best = __int_as_float(0x7f800000), sec = __int_as_float(0x7f800000);
-                int bj = 0;
-#pragma unroll 4
-                for (int j = 0; j < k; ++j) {
-                    const float d = sqdist<LP>(xv, s_c + j * LP);
-                    if (d < best) {
-                        sec = best;
-                        best = d;
-                        bj = j;
-                    } else if (d < sec) {
-                        sec = d;
-                    }
-                }
-                if (act) {
-                    lloyd_commit<LP>(a, i, xv, oldl, bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), it == 1, sc, sl,
-                                     my_tab, inert, changed);
-                    if (a.prune) a.ubound[i] = sqrtf(best) * (1.0f + PRUNE_EPS);
-                }
+                int base = 0;
+                if (lane == 0 && m) base = atomicAdd(&s_pend, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                // a point joins the list at most once per iteration, so the list stays within the
+                // block's region (its chunks' points)
+                if (keep) pend[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
             }
             __syncwarp();
             qn = 0;
@@ -913,6 +898,38 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             }
         }
         flush();
+        __syncthreads();   // the block's scan list is complete (global writes of this block: visible)
+        {
+            // the k-way scan of the listed points, 32 per warp at a time over all warps; a point's
+            // label is still the one this iteration started from (a commit writes only its own)
+            const int P = s_pend;
+            for (int q0 = wid * 32; q0 < P; q0 += KM_WARPS * 32) {
+                const int q = q0 + lane;
+                const bool act = q < P;
+                const long long i = act ? __ldcg(pend + q) : 0;
+                const int oldl = act ? a.labels[i] : 0;
+                float xv[LP];
+                load_point<LP>(a.X, i, a.l, xv);
+                float best = __int_as_float(0x7f800000), sec = __int_as_float(0x7f800000);
+                int bj = 0;
+#pragma unroll 4
+                for (int j = 0; j < k; ++j) {
+                    const float d = sqdist<LP>(xv, s_c + j * LP);
+                    if (d < best) {
+                        sec = best;
+                        best = d;
+                        bj = j;
+                    } else if (d < sec) {
+                        sec = d;
+                    }
+                }
+                if (act) {
+                    lloyd_commit<LP>(a, i, xv, oldl, bj, best, sqrtf(sec) * (1.0f - PRUNE_EPS), it == 1, sc, sl,
+                                     my_tab, inert, changed);
+                    if (a.prune) a.ubound[i] = sqrtf(best) * (1.0f + PRUNE_EPS);
+                }
+            }
+        }
         slot_flush_warp<LP>(sl[0], my_tab);
         slot_flush_warp<LP>(sl[1], my_tab);
         __syncthreads();
@@ -940,6 +957,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
             s_inert = (long long)__ldcg(a.cnt3 + 4 * cur);
             s_changed = (int)__ldcg(a.cnt3 + 4 * cur + 1);
             s_pmax = 0u;
+            s_pend = 0;   // every warp has finished phase A's scans (the barriers above)
         }
         __syncthreads();
         for (int q = tid; q < k * LP; q += KM_THREADS) {
@@ -1186,6 +1204,7 @@ static fsc_status kmeans_lp(const float* emb, int n, int l, int k, uint64_t seed
         la.prune = k <= 256 ? 1 : 0;
         la.seeded = 1;
         la.near = ka.near;
+        la.pend = ka.near;
         la.d2s0 = ka.d2[0];
         la.d2s1 = ka.d2[1];
         la.dfl = ka.cfl[k & 1];   // the chunk flags after the final pass (r = k)
@@ -1455,6 +1474,7 @@ static fsc_status kmeans_lp_static(const float* emb, int n, int l, int k, uint64
     la.prune = k <= 256 ? 1 : 0;
     la.seeded = 1;
     la.near = ka.near;
+    la.pend = ka.near;
     la.d2s0 = ka.d2[0];
     la.d2s1 = ka.d2[1];
     la.dfl = ka.cfl[k & 1];   // the chunk flags after the final pass (r = k)
