@@ -638,10 +638,10 @@ __global__ void __launch_bounds__(KM_THREADS, 1) k_lloyd(LloydArgs a) {
         // ---- phase A.  Each thread takes KM_PPT consecutive points of a chunk and settles, from
         // its label and bounds alone, those whose upper bound u (carried forward by the centroid's
         // move) is below max(s(a), lower bound): Hamerly's test, without loading the point.  The
-        // others go to a per-warp queue that the warp then works one point per lane: the exact
-        // distance to the own centroid first (the same test, tight), the k-way scan only if that
-        // fails, so no lane idles behind a neighbour's scan.  Centroid sums are exact integers,
-        // so which lane adds a point changes no result.
+        // others go to a per-warp queue that the warp then works one point per lane with the exact
+        // distance to the own centroid (the same test, tight); those it does not settle go to the
+        // block's scan list, whose k-way scans all warps of the block share after the chunk pass.
+        // Centroid sums are exact integers, so which lane adds a point changes no result.
         // Points are dealt in chunks of KM_CHUNK (one warp, four consecutive points per lane):
         // chunk c goes to block c mod G, warp (c / G) mod KM_WARPS, so the chunks of any vertex
         // range (a planted cluster's, whose boundary points all need the scan) spread over every
